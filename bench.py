@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 MDRQ scan: queries/s and scan GB/s against the HBM roofline.
+
+A step answers one batch of multidimensional range queries (Sec. 2.1) over a table
+resident on the GPU, through the C ABI (``mdrq_query_batch``), with every answer
+written to device memory as an ascending id list. The default workload is a
+100,000,000 x 8 float32 table (4 uniform columns, 4 columns of a 20-cluster Gaussian
+mixture) and a batch of 1024 partial-match queries on 2..8 dimensions with target
+selectivity log-uniform in [1e-5, 0.2]. The 3.2 GB of columns exceed the 126 MB L2,
+so steps need no cache flush between them.
+
+Prints one JSON line (rank 0). ``--impl reference`` times the CPU oracle instead.
+Launch with N > 1 through torch.distributed.run: every rank answers its own batch on
+its own GPU (independent replicas, weak scaling); the timed region is bracketed by
+barriers and the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1801_03644_gb300 import workloads as W  # noqa: E402
+
+METRIC = "MDRQ queries/s"
+UNIT = "queries/s"
+
+
+def make_workload(name: str, rank: int = 0):
+    if name == "mixed_clustered":
+        return W.mixed_clustered()
+    if name == "uniform_1M":
+        return W.uniform_small()
+    if name == "skewed_mixed":
+        return W.skewed_mixed_types()
+    raise SystemExit("unknown workload %s" % name)
+
+
+def workload_config(wl, name: str) -> dict:
+    return {"workload": wl.name, "n": wl.n, "d": wl.d, "queries_per_step": len(wl.queries),
+            "recipe": wl.recipe,
+            "cache": ("inputs larger than L2: no flush between steps"
+                      if 4 * wl.n * wl.d > 126e6 else
+                      "table fits in L2: hot cache as in Sec. 7.1.2, L2 not flushed"),
+            "answers": "ascending uint32 id lists in device memory (CSR)",
+            "parallelism": "replicas"}
+
+
+# ----------------------------------------------------------------------------- clocks
+
+CLOCK_FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+                "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+                "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+
+class ClockSampler:
+    """nvidia-smi sampling every 200 ms while the timed region runs."""
+
+    def __init__(self, gpu_id: str):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + ",".join(CLOCK_FIELDS), "--format=csv,noheader,nounits",
+                 "-i", gpu_id, "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) != len(CLOCK_FIELDS):
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def gpu_smi_id(torch, dev: int) -> str:
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev)
+
+
+# ----------------------------------------------------------------------------- peaks, traffic
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def scan_kernel_digest() -> str:
+    src = os.path.join(ROOT, "paper_1801_03644_gb300", "csrc", "scan_kernel.cuh")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def dram_traffic_per_launch(workload: str, alg_bytes_per_launch: float):
+    """DRAM bytes per scan launch from the committed ncu summary of this workload, scaled
+    to this run's average launch by the captured launches' traffic / algorithmic ratio;
+    None when the summary is missing or the kernel source changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "mdrq_scan_kernel_%s.traffic.json" % workload)
+    if not os.path.exists(p):
+        return None, None
+    d = json.load(open(p))
+    if d.get("scan_kernel_digest") != scan_kernel_digest():
+        return None, None
+    ratio = float(d["dram_bytes"]) / float(d["algorithmic_bytes"])
+    return ratio * alg_bytes_per_launch, ratio
+
+
+# ----------------------------------------------------------------------------- oracle timing
+
+def time_oracle(wl, budget_s: float, nthreads: int, min_queries: int = 2):
+    """Answer the batch's queries in order with the CPU oracle until ``budget_s`` has
+    passed; returns (queries answered, seconds)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    done = 0
+    for q in wl.queries:
+        oracle.mdrq(wl.columns, q, nthreads=nthreads)
+        done += 1
+        if done >= min_queries and time.perf_counter() - t0 > budget_s:
+            break
+    return done, time.perf_counter() - t0
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    """The CPU oracle on the host cores: each step a bounded sample of the same batch."""
+    if rank != 0:
+        return
+    wl = make_workload(args.workload)
+    nthreads = os.cpu_count() or 1
+    # size the sample so that one step takes about --cpu-seconds
+    m, secs = time_oracle(wl, args.cpu_seconds, nthreads)
+    sample = wl.queries[:m]
+    sub = W.Workload(wl.name, wl.columns, sample, wl.recipe)
+    for _ in range(max(0, args.warmup - 1)):
+        time_oracle(sub, 1e9, nthreads, min_queries=m)
+    times = []
+    for _ in range(args.steps):
+        _, s = time_oracle(sub, 1e9, nthreads, min_queries=m)
+        times.append(s)
+    total = sum(times)
+    value = m * args.steps / total
+    cfg = workload_config(wl, args.workload)
+    desc = "first %d of the %d queries per step, whole table (%d rows)" % (m, len(wl.queries), wl.n)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
+    import torch
+    import torch.distributed as dist
+    from paper_1801_03644_gb300 import mdrq
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.cuda.current_device()
+    wl = make_workload(args.workload)
+    if world > 1 and rank > 0:
+        # each rank answers its own batch: same table recipe, queries from a rank stream
+        qrng = W.rng_for(1000 + rank, 1)
+        samples = W.quantile_samples(wl.columns, W.rng_for(1000 + rank, 2))
+        dtypes = [c.dtype for c in wl.columns]
+        qs = []
+        for q0 in wl.queries:
+            dims = [p[0] for p in q0]
+            s = W.log_uniform(qrng, 1e-5, 0.2)
+            qs.append(W.target_selectivity_query(samples, dtypes, dims, s, qrng))
+        wl = W.Workload(wl.name, wl.columns, qs, wl.recipe)
+    nq = len(wl.queries)
+
+    stream = torch.cuda.current_stream()
+    table = mdrq.Table(wl.columns)  # copied to the device once (not timed)
+    enc = table.encode_batch(wl.queries)
+
+    # first call sizes the answer buffer exactly
+    probe = torch.empty(1, dtype=torch.int32, device="cuda")
+    st, off = table.query_batch_raw(enc, probe.data_ptr(), 0, True)
+    if st not in (mdrq.OK, mdrq.E_CAPACITY):
+        raise mdrq.MDRQError(st, "mdrq_query_batch")
+    total_ids = int(off[-1])
+    ids = torch.empty(max(1, total_ids), dtype=torch.int32, device="cuda")
+
+    def step():
+        st, o = table.query_batch_raw(enc, ids.data_ptr(), ids.numel(), True)
+        if st != mdrq.OK:
+            raise mdrq.MDRQError(st, "mdrq_query_batch")
+        return o
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # ---- timed region: answers stay on the device
+    sampler = ClockSampler(gpu_smi_id(torch, dev))
+    time.sleep(0.3)
+    table.scan_timing(True)
+    table.scan_timing_read(reset=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    timing = table.scan_timing_read(reset=True)
+    table.scan_timing(False)
+    clocks = sampler.stop()
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * nq * args.steps / (ms / 1e3)
+
+    # ---- end to end: host query descriptors in, host answers out (pinned)
+    e2e = None
+    if not args.no_e2e:
+        host_ids = torch.empty(max(1, total_ids), dtype=torch.int32, pin_memory=True)
+        hptr = host_ids.data_ptr()
+
+        def step_host():
+            st, o = table.query_batch_raw(enc, hptr, host_ids.numel(), False)
+            if st != mdrq.OK:
+                raise mdrq.MDRQError(st, "mdrq_query_batch")
+            return o
+
+        step_host()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step_host()
+        torch.cuda.synchronize()
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        npreds = sum(len(q) for q in wl.queries)
+        e2e = {"value": world * nq * args.steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": 16 * npreds + 16 * nq,
+               "d2h_bytes_per_step": 8 * (nq + 1) + 4 * total_ids}
+
+    # ---- roofline of the scan kernel (algorithmic bytes / event-timed duration)
+    peaks = measured_peaks()
+    launches = max(1, timing["scan_launches"])
+    alg_per_launch = timing["bytes"] / launches
+    avg_launch_s = timing["ms"] / 1e3 / launches
+    achieved = alg_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
+    traffic, ratio = dram_traffic_per_launch(args.workload, alg_per_launch)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"],
+                "traffic": traffic,
+                "peak_source": peaks["source"] + " (HBM copy bandwidth)",
+                "kernel": "mdrq_scan_kernel",
+                "alg_bytes_per_launch": alg_per_launch,
+                "avg_launch_ms": avg_launch_s * 1e3,
+                "scan_launches": timing["scan_launches"]}
+
+    # ---- CPU baseline: the oracle as it stands, on the host cores (rank 0, N = 1)
+    cpu = None
+    if world == 1 and rank == 0 and not args.no_cpu_baseline:
+        nthreads = os.cpu_count() or 1
+        m, secs = time_oracle(wl, args.cpu_seconds, nthreads)
+        cpu = {"value": m / secs, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+               "sample": "first %d of the %d queries, whole table (%d rows), %d threads over "
+                         "contiguous horizontal partitions" % (m, nq, wl.n, nthreads)}
+
+    if rank == 0:
+        cfg = workload_config(wl, args.workload)
+        cfg["mode"] = "plain scan: one fused filter+compact launch per query"
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": cfg, "clocks": clocks, "e2e": e2e,
+            "gpu_launches": timing["kernel_launches"], "roofline": roofline,
+            "cpu_baseline": cpu, "answer_ids_per_step": total_ids,
+        }), flush=True)
+    table.close()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="mixed_clustered",
+                    choices=["mixed_clustered", "uniform_1M", "skewed_mixed"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * mdrq.h — C ABI of the GB300 multidimensional range query (MDRQ) scan library.
+ *
+ * Problem (Sec. 2.1 of "Multidimensional Range Queries on Modern Hardware",
+ * arXiv 1801.03644): a table holds n objects with d attributes (dimensions). A query
+ * gives closed intervals [lo_j, hi_j] on some or all dimensions; an object qualifies
+ * iff lo_j <= x_j <= hi_j for every constrained dimension j, and a dimension the
+ * query leaves out behaves as [-inf, +inf] (partial-match query). The answer is the
+ * set of identifiers of the qualifying objects, where the identifier of an object is
+ * its row index i (Sec. 2.2.4). This library returns it as an ascending uint32 list.
+ *
+ * Layout: the table is held column-wise on the GPU, one contiguous array per
+ * dimension (the vertical layout of Sec. 3.2), so a query reads only the columns it
+ * constrains. Columns are float32 or int32 (Sec. 7.2 uses float32 throughout).
+ *
+ * Conventions for every function below:
+ *  - Return value: MDRQ_OK (0) or a negative mdrq_status. Nothing is thrown.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Work is enqueued
+ *    on it and the call returns once the status is known (it synchronises that
+ *    stream), unless the function says otherwise.
+ *  - Pointers marked "device" must be device-accessible memory of the current CUDA
+ *    device; "host" pointers are plain host memory (pinned memory copies faster).
+ *  - The caller owns every buffer it passes in; the library owns mdrq_table and the
+ *    scratch memory inside it.
+ *  - Calls on one table must not run concurrently (a table holds one scratch area).
+ *  - Floating-point data and bounds never contain NaN: mdrq_load_columns rejects NaN
+ *    data (MDRQ_E_NAN) and the query calls reject NaN bounds (MDRQ_E_INVAL). With NaN
+ *    excluded, the closed-interval test of Sec. 2.1 (ordered IEEE compare, so
+ *    -0.0 == +0.0; +-inf allowed as bounds) is the same under both of the paper's
+ *    listings (Listing 1 and Listing 2), which otherwise disagree on NaN.
+ */
+#ifndef MDRQ_H
+#define MDRQ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Column element types. */
+typedef enum { MDRQ_F32 = 0, MDRQ_I32 = 1 } mdrq_dtype;
+
+/* Status codes. */
+typedef enum {
+    MDRQ_OK = 0,
+    MDRQ_E_INVAL = -1,    /* bad argument: see each function */
+    MDRQ_E_NOMEM = -2,    /* a device or host allocation failed */
+    MDRQ_E_CUDA = -3,     /* a CUDA runtime call failed; the table may be unusable */
+    MDRQ_E_CAPACITY = -4, /* the answer is longer than the caller's id buffer */
+    MDRQ_E_TIMEOUT = -5,  /* a bounded device-side wait gave up; results are invalid */
+    MDRQ_E_NAN = -6       /* a float32 column holds a NaN */
+} mdrq_status;
+
+/* Opaque table handle (library-owned). */
+typedef struct mdrq_table mdrq_table;
+
+/* One bound, read as float32 or int32 according to the type of the column. */
+typedef union {
+    float f;
+    int32_t i;
+} mdrq_value;
+
+/*
+ * One predicate p_j = [lo, hi] on dimension `dim` (Sec. 2.1). lo > hi is valid and
+ * matches nothing. A dimension may appear in several predicates of one query; they
+ * are ANDed. `reserved` must be 0.
+ */
+typedef struct {
+    uint32_t dim;
+    uint32_t reserved;
+    mdrq_value lo;
+    mdrq_value hi;
+} mdrq_pred;
+
+/* One query of a batch: `npreds` predicates at host address `preds`. */
+typedef struct {
+    const mdrq_pred *preds;
+    uint32_t npreds;
+    uint32_t reserved;
+} mdrq_qdesc;
+
+/*
+ * mdrq_load_columns — make a table of n objects with d dimensions resident on the
+ * current CUDA device (the vertical partitioning of Sec. 3.2: one array per dimension).
+ *
+ *  cols[j]        column j: n values of type types[j] (MDRQ_F32 / MDRQ_I32).
+ *                 cols_on_device = 0: host pointers; the values are copied to the GPU.
+ *                 cols_on_device = 1: device pointers, each 16-byte aligned; the table
+ *                 refers to that memory, which must outlive the table and stay
+ *                 unchanged while it is in use.
+ *  d              number of dimensions, >= 1.
+ *  n              number of objects, <= 2^32 - 1 (identifiers are uint32). n = 0 is a
+ *                 valid empty table.
+ *  stream         stream for the copies and checks.
+ *  out            receives the handle; release it with mdrq_free.
+ *
+ * Errors: MDRQ_E_INVAL (d = 0, n >= 2^32, a null pointer where n > 0, an unknown
+ * type, a device column that is not 16-byte aligned, out == NULL); MDRQ_E_NAN (a
+ * float32 column holds a NaN; nothing is kept); MDRQ_E_NOMEM; MDRQ_E_CUDA.
+ */
+int mdrq_load_columns(const void *const *cols, const int32_t *types, uint32_t d, uint64_t n,
+                      int cols_on_device, void *stream, mdrq_table **out);
+
+/*
+ * mdrq_query — answer one MDRQ (Sec. 2.1) with a full parallel scan of the
+ * constrained columns (Sec. 5.5), returning the qualifying row indices in ascending
+ * order.
+ *
+ *  preds, npreds  host array of predicates; npreds = 0 is the full-domain query
+ *                 (all n ids). At most 128 distinct dimensions may be constrained.
+ *  ids            output, `capacity` uint32 slots; device memory when
+ *                 ids_on_device = 1, host memory when 0.
+ *  count          host; receives the length of the answer (also when it exceeds
+ *                 capacity).
+ *
+ * Errors: MDRQ_E_INVAL (t or count NULL, dim >= d, a NaN float bound, nonzero
+ * reserved field, ids NULL with capacity > 0, more than 128 constrained
+ * dimensions); MDRQ_E_CAPACITY (*count > capacity: the first `capacity` ids are
+ * written, nothing beyond); MDRQ_E_TIMEOUT; MDRQ_E_NOMEM; MDRQ_E_CUDA.
+ */
+int mdrq_query(mdrq_table *t, const mdrq_pred *preds, uint32_t npreds, uint32_t *ids,
+               uint64_t capacity, uint64_t *count, int ids_on_device, void *stream);
+
+/*
+ * mdrq_query_batch — answer nq queries; the answers are concatenated in query order
+ * into `ids` in CSR form: query q's ascending ids are ids[offsets[q] .. offsets[q+1]).
+ *
+ *  qs, nq         host array of nq query descriptors (nq = 0 is valid).
+ *  ids, capacity  output as for mdrq_query, holding the concatenation.
+ *  offsets        host, nq + 1 entries; offsets[0] = 0 and offsets[nq] is the total
+ *                 length (also when it exceeds capacity).
+ *
+ * Errors: as mdrq_query; MDRQ_E_CAPACITY when offsets[nq] > capacity (every id at a
+ * position below capacity is written, nothing beyond).
+ */
+int mdrq_query_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids,
+                     uint64_t capacity, uint64_t *offsets, int ids_on_device, void *stream);
+
+/* mdrq_free — release a table and its device memory (not caller-owned columns). NULL is
+ * a no-op. Synchronises the device work the table still has in flight. */
+void mdrq_free(mdrq_table *t);
+
+/* Short English description of a status code (static storage). */
+const char *mdrq_status_string(int status);
+
+/* Table shape: number of objects and of dimensions (0 for NULL). */
+uint64_t mdrq_table_rows(const mdrq_table *t);
+uint32_t mdrq_table_dims(const mdrq_table *t);
+
+/*
+ * mdrq_last_scan_stats — figures of the most recent query call on this table, for
+ * measurement: the number of scan-kernel launches it made and the algorithmic bytes
+ * they imply (4 bytes per row per constrained column, plus 4 bytes per id written).
+ * Either pointer may be NULL.
+ */
+void mdrq_last_scan_stats(const mdrq_table *t, uint64_t *launches, uint64_t *bytes);
+
+/*
+ * mdrq_scan_timing — measurement aid: turn per-launch timing of the scan kernel on
+ * (enable = 1) or off (0) for this table. While on, every scan launch is bracketed
+ * by two CUDA events recorded on the stream it is launched on.
+ * Errors: MDRQ_E_INVAL (t NULL).
+ */
+int mdrq_scan_timing(mdrq_table *t, int enable);
+
+/*
+ * mdrq_scan_timing_read — what the timed calls since the last reset measured:
+ *  ms               summed device time between each timed launch's two events
+ *  scan_launches    scan-kernel launches timed
+ *  bytes            their algorithmic bytes (4 per row per constrained column, plus
+ *                   4 per id written)
+ *  kernel_launches  kernels of this library launched by the timed calls, all kinds
+ * Any output pointer may be NULL. Waits for the last recorded event. reset = 1
+ * clears the counters afterwards. Errors: MDRQ_E_INVAL (t NULL); MDRQ_E_CUDA.
+ */
+int mdrq_scan_timing_read(mdrq_table *t, double *ms, uint64_t *scan_launches, uint64_t *bytes,
+                          uint64_t *kernel_launches, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MDRQ_H */

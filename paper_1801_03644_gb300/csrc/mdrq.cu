@@ -1,0 +1,620 @@
+// C ABI of the MDRQ scan library: table residency, query encoding, launches and result
+// hand-off. The operations are defined in include/mdrq.h; the scan itself is in
+// scan_kernel.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "mdrq.h"
+#include "scan_kernel.cuh"
+
+using namespace mdrq;
+
+namespace {
+
+constexpr uint32_t kSampleRows = 4096;  // per-column sample for selectivity estimates
+
+struct ColumnInfo {
+    const void *ptr = nullptr;  // device
+    int32_t type = MDRQ_F32;
+    uint32_t min_bits = 0, max_bits = 0;  // exact column minimum / maximum (n > 0)
+    std::vector<double> sample;           // sorted
+};
+
+struct EncodedQuery {
+    bool empty = false;                 // proven empty on the host
+    std::vector<ScanPred> preds;        // non-trivial predicates, most selective first
+    uint64_t scanned_columns = 0;
+};
+
+}  // namespace
+
+struct mdrq_table {
+    int device = 0;
+    uint64_t n = 0;
+    uint32_t d = 0;
+    std::vector<ColumnInfo> cols;
+    std::vector<void *> owned;  // device columns this table allocated
+
+    // scratch: [0] ticket, [1] error word, [2..] tile states
+    unsigned long long *scratch = nullptr;
+    unsigned long long *ticket = nullptr;
+    int *error = nullptr;
+    unsigned long long *tile_state = nullptr;
+    uint32_t state_words = 0;
+    unsigned long long ticket_next = 0;
+    uint32_t epoch = 0;
+
+    unsigned long long *offsets_dev = nullptr;  // nq + 1 entries
+    size_t offsets_dev_cap = 0;
+    unsigned long long *offsets_host = nullptr;  // pinned mirror
+    size_t offsets_host_cap = 0;
+    uint32_t *ids_stage = nullptr;  // device staging for host-side answers
+    size_t ids_stage_cap = 0;
+    int *error_host = nullptr;      // pinned
+
+    int sm_count = 0;
+    int blocks_per_sm[3] = {0, 0, 0};  // for U = 1, 2, 4
+
+    uint64_t last_launches = 0;
+    uint64_t last_bytes = 0;
+
+    // optional per-launch event timing of the scan kernel
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;  // pairs: [2i] before, [2i+1] after launch i
+    size_t ev_used = 0;           // pairs recorded since the last reset
+    uint64_t acc_scans = 0, acc_bytes = 0, acc_kernels = 0;
+};
+
+namespace {
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess)
+        return MDRQ_OK;
+    if (e == cudaErrorMemoryAllocation)
+        return MDRQ_E_NOMEM;
+    return MDRQ_E_CUDA;
+}
+
+#define MDRQ_TRY(expr)                         \
+    do {                                       \
+        int _s = cuda_status(expr);            \
+        if (_s != MDRQ_OK) {                   \
+            (void)cudaGetLastError();          \
+            return _s;                         \
+        }                                      \
+    } while (0)
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+double bound_value(uint32_t bits, int32_t type)
+{
+    if (type == MDRQ_F32) {
+        float f;
+        std::memcpy(&f, &bits, 4);
+        return (double)f;
+    }
+    return (double)(int32_t)bits;
+}
+
+uint32_t bits_from_key(unsigned long long key, int32_t type)
+{
+    const uint32_t k = (uint32_t)key;
+    if (type == MDRQ_F32)
+        return (k & 0x80000000u) ? (k ^ 0x80000000u) : ~k;
+    return k ^ 0x80000000u;
+}
+
+// Sec. 2.1: a predicate is kept as an interval in the column's own type; the
+// comparisons here are exact in double for both float32 and int32 values.
+int encode_query(const mdrq_table *t, const mdrq_pred *preds, uint32_t npreds, EncodedQuery &q)
+{
+    q = EncodedQuery();
+    if (npreds > 0 && !preds)
+        return MDRQ_E_INVAL;
+    std::map<uint32_t, std::pair<double, double>> iv;  // dim -> [lo, hi] intersected
+    std::map<uint32_t, std::pair<uint32_t, uint32_t>> bits;
+    for (uint32_t i = 0; i < npreds; ++i) {
+        const mdrq_pred &p = preds[i];
+        if (p.dim >= t->d || p.reserved != 0)
+            return MDRQ_E_INVAL;
+        const int32_t type = t->cols[p.dim].type;
+        uint32_t lb, hb;
+        std::memcpy(&lb, &p.lo, 4);
+        std::memcpy(&hb, &p.hi, 4);
+        const double lo = bound_value(lb, type), hi = bound_value(hb, type);
+        if (std::isnan(lo) || std::isnan(hi))
+            return MDRQ_E_INVAL;
+        auto it = iv.find(p.dim);
+        if (it == iv.end()) {
+            iv[p.dim] = {lo, hi};
+            bits[p.dim] = {lb, hb};
+        } else {
+            // a repeated dimension ANDs its predicates: intersect the intervals
+            if (lo > it->second.first) {
+                it->second.first = lo;
+                bits[p.dim].first = lb;
+            }
+            if (hi < it->second.second) {
+                it->second.second = hi;
+                bits[p.dim].second = hb;
+            }
+        }
+    }
+    struct Cand {
+        double est;
+        uint32_t dim;
+    };
+    std::vector<Cand> keep;
+    for (auto &kv : iv) {
+        const uint32_t j = kv.first;
+        const double lo = kv.second.first, hi = kv.second.second;
+        const ColumnInfo &c = t->cols[j];
+        if (lo > hi) {
+            q.empty = true;  // an empty interval matches nothing
+            continue;
+        }
+        if (t->n == 0)
+            continue;
+        const double mn = bound_value(c.min_bits, c.type), mx = bound_value(c.max_bits, c.type);
+        if (hi < mn || lo > mx) {
+            q.empty = true;  // no value of the column lies in the interval
+            continue;
+        }
+        if (lo <= mn && mx <= hi)
+            continue;  // every value lies in it: the predicate is always true
+        const auto b = std::lower_bound(c.sample.begin(), c.sample.end(), lo);
+        const auto e = std::upper_bound(c.sample.begin(), c.sample.end(), hi);
+        keep.push_back({(double)(e - b), j});
+    }
+    if (q.empty) {
+        q.preds.clear();
+        return MDRQ_OK;
+    }
+    // Sec. 2.2.4: evaluating the most selective dimension first ends rows earliest
+    std::stable_sort(keep.begin(), keep.end(),
+                     [](const Cand &a, const Cand &b) { return a.est < b.est; });
+    if (keep.size() > (size_t)kMaxPreds)
+        return MDRQ_E_INVAL;
+    for (const Cand &cd : keep) {
+        ScanPred sp;
+        sp.col = t->cols[cd.dim].ptr;
+        sp.type = (uint32_t)t->cols[cd.dim].type;
+        sp.lo = bits[cd.dim].first;
+        sp.hi = bits[cd.dim].second;
+        sp.pad = 0;
+        q.preds.push_back(sp);
+    }
+    q.scanned_columns = q.preds.size();
+    return MDRQ_OK;
+}
+
+int grow_device(void **p, size_t *cap, size_t bytes)
+{
+    if (*cap >= bytes)
+        return MDRQ_OK;
+    if (*p)
+        cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    MDRQ_TRY(cudaMalloc(p, bytes));
+    *cap = bytes;
+    return MDRQ_OK;
+}
+
+int grow_pinned(void **p, size_t *cap, size_t bytes)
+{
+    if (*cap >= bytes)
+        return MDRQ_OK;
+    if (*p)
+        cudaFreeHost(*p);
+    *p = nullptr;
+    *cap = 0;
+    MDRQ_TRY(cudaMallocHost(p, bytes));
+    *cap = bytes;
+    return MDRQ_OK;
+}
+
+template <int U>
+constexpr uint64_t tile_rows()
+{
+    return (uint64_t)kWarps * U * 128;
+}
+
+// Launch the scan of one encoded, non-empty query.
+int launch_scan(mdrq_table *t, const EncodedQuery &q, uint32_t *ids, uint64_t capacity,
+                const unsigned long long *base_in, unsigned long long *count_out, cudaStream_t s)
+{
+    // smallest tiles on small tables so that every SM gets work; 4096-row tiles otherwise
+    const uint64_t resident4 = (uint64_t)t->sm_count * t->blocks_per_sm[2];
+    int ui = 2;
+    if ((t->n + tile_rows<4>() - 1) / tile_rows<4>() < 2 * resident4)
+        ui = ((t->n + tile_rows<2>() - 1) / tile_rows<2>() < 2 * resident4) ? 0 : 1;
+    const uint64_t rows = ui == 2 ? tile_rows<4>() : ui == 1 ? tile_rows<2>() : tile_rows<1>();
+    const uint64_t n_tiles = (t->n + rows - 1) / rows;
+    if (n_tiles > t->state_words)
+        return MDRQ_E_CUDA;  // cannot happen: states are sized for the smallest tile
+    const uint64_t resident = (uint64_t)t->sm_count * t->blocks_per_sm[ui];
+    const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(resident, n_tiles));
+
+    if (t->epoch >= kEpochLimit) {
+        MDRQ_TRY(cudaMemsetAsync(t->tile_state, 0, (size_t)t->state_words * 8, s));
+        t->epoch = 0;
+    }
+    ++t->epoch;
+
+    ScanParams p;
+    std::memset(&p, 0, sizeof(p));
+    for (size_t i = 0; i < q.preds.size(); ++i)
+        p.pred[i] = q.preds[i];
+    p.npred = (uint32_t)q.preds.size();
+    p.n_tiles = (uint32_t)n_tiles;
+    p.n = t->n;
+    p.tile_state = t->tile_state;
+    p.ticket = t->ticket;
+    p.ticket_base = t->ticket_next;
+    p.epoch = t->epoch;
+    p.ids = ids;
+    p.capacity = capacity;
+    p.base_in = base_in;
+    p.count_out = count_out;
+    p.error = t->error;
+
+    cudaEvent_t *evp = nullptr;
+    if (t->timing) {
+        if (t->ev.size() < 2 * (t->ev_used + 1)) {
+            cudaEvent_t a, b;
+            MDRQ_TRY(cudaEventCreate(&a));
+            MDRQ_TRY(cudaEventCreate(&b));
+            t->ev.push_back(a);
+            t->ev.push_back(b);
+        }
+        evp = &t->ev[2 * t->ev_used];
+        ++t->ev_used;
+        MDRQ_TRY(cudaEventRecord(evp[0], s));
+    }
+    if (ui == 2)
+        mdrq_scan_kernel<4><<<grid, kBlock, 0, s>>>(p);
+    else if (ui == 1)
+        mdrq_scan_kernel<2><<<grid, kBlock, 0, s>>>(p);
+    else
+        mdrq_scan_kernel<1><<<grid, kBlock, 0, s>>>(p);
+    MDRQ_TRY(cudaGetLastError());
+    if (evp)
+        MDRQ_TRY(cudaEventRecord(evp[1], s));
+    t->ticket_next += n_tiles + grid;  // every CTA makes one claim past the last tile
+    t->last_launches += 1;
+    t->last_bytes += q.scanned_columns * 4ull * t->n;
+    if (t->timing) {
+        t->acc_scans += 1;
+        t->acc_kernels += 1;
+        t->acc_bytes += q.scanned_columns * 4ull * t->n;
+    }
+    return MDRQ_OK;
+}
+
+// After an error the claim counter and tile states may be inconsistent: reset them.
+void reset_scratch(mdrq_table *t, cudaStream_t s)
+{
+    cudaStreamSynchronize(s);
+    (void)cudaGetLastError();
+    cudaMemset(t->scratch, 0, (size_t)(2 + t->state_words) * 8);
+    cudaDeviceSynchronize();
+    (void)cudaGetLastError();
+    t->ticket_next = 0;
+    t->epoch = 0;
+}
+
+int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, uint64_t capacity,
+              uint64_t *offsets, int ids_on_device, cudaStream_t s)
+{
+    if (!t || !offsets || (nq > 0 && !qs) || (capacity > 0 && !ids))
+        return MDRQ_E_INVAL;
+    for (uint32_t q = 0; q < nq; ++q)
+        if (qs[q].reserved != 0)
+            return MDRQ_E_INVAL;
+    std::vector<EncodedQuery> enc(nq);
+    for (uint32_t q = 0; q < nq; ++q) {
+        int st = encode_query(t, qs[q].preds, qs[q].npreds, enc[q]);
+        if (st != MDRQ_OK)
+            return st;
+    }
+    t->last_launches = 0;
+    t->last_bytes = 0;
+    MDRQ_TRY(cudaSetDevice(t->device));
+
+    int st = grow_device((void **)&t->offsets_dev, &t->offsets_dev_cap, ((size_t)nq + 1) * 8);
+    if (st != MDRQ_OK)
+        return st;
+    st = grow_pinned((void **)&t->offsets_host, &t->offsets_host_cap, ((size_t)nq + 1) * 8);
+    if (st != MDRQ_OK)
+        return st;
+    uint32_t *out = ids;
+    if (!ids_on_device && capacity > 0) {
+        st = grow_device((void **)&t->ids_stage, &t->ids_stage_cap, (size_t)capacity * 4);
+        if (st != MDRQ_OK)
+            return st;
+        out = t->ids_stage;
+    }
+    MDRQ_TRY(cudaMemsetAsync(t->offsets_dev, 0, ((size_t)nq + 1) * 8, s));
+    MDRQ_TRY(cudaMemsetAsync(t->error, 0, sizeof(int), s));
+
+    for (uint32_t q = 0; q < nq; ++q) {
+        if (t->n == 0 || enc[q].empty) {
+            mdrq_copy_offset_kernel<<<1, 1, 0, s>>>(t->offsets_dev + q, t->offsets_dev + q + 1);
+            MDRQ_TRY(cudaGetLastError());
+            if (t->timing)
+                t->acc_kernels += 1;
+            continue;
+        }
+        st = launch_scan(t, enc[q], out, capacity, t->offsets_dev + q, t->offsets_dev + q + 1, s);
+        if (st != MDRQ_OK) {
+            reset_scratch(t, s);
+            return st;
+        }
+    }
+    MDRQ_TRY(cudaMemcpyAsync(t->offsets_host, t->offsets_dev, ((size_t)nq + 1) * 8,
+                             cudaMemcpyDeviceToHost, s));
+    MDRQ_TRY(cudaMemcpyAsync(t->error_host, t->error, sizeof(int), cudaMemcpyDeviceToHost, s));
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        reset_scratch(t, s);
+        return cuda_status(e);
+    }
+    if (*t->error_host != 0) {
+        reset_scratch(t, s);
+        return MDRQ_E_TIMEOUT;
+    }
+    std::memcpy(offsets, t->offsets_host, ((size_t)nq + 1) * 8);
+    const uint64_t total = offsets[nq];
+    // 4 bytes per id written
+    t->last_bytes += 4ull * std::min<uint64_t>(total, capacity);
+    if (t->timing)
+        t->acc_bytes += 4ull * std::min<uint64_t>(total, capacity);
+    if (!ids_on_device && capacity > 0 && total > 0) {
+        MDRQ_TRY(cudaMemcpyAsync(ids, t->ids_stage, (size_t)std::min<uint64_t>(total, capacity) * 4,
+                                 cudaMemcpyDeviceToHost, s));
+        MDRQ_TRY(cudaStreamSynchronize(s));
+    }
+    return total > capacity ? MDRQ_E_CAPACITY : MDRQ_OK;
+}
+
+void destroy(mdrq_table *t)
+{
+    if (!t)
+        return;
+    cudaSetDevice(t->device);
+    cudaDeviceSynchronize();
+    for (void *p : t->owned)
+        cudaFree(p);
+    cudaFree(t->scratch);
+    cudaFree(t->offsets_dev);
+    cudaFree(t->ids_stage);
+    cudaFreeHost(t->offsets_host);
+    cudaFreeHost(t->error_host);
+    for (cudaEvent_t e : t->ev)
+        cudaEventDestroy(e);
+    (void)cudaGetLastError();
+    delete t;
+}
+
+int load(const void *const *cols, const int32_t *types, uint32_t d, uint64_t n, int cols_on_device,
+         cudaStream_t s, mdrq_table *t)
+{
+    MDRQ_TRY(cudaGetDevice(&t->device));
+    MDRQ_TRY(cudaDeviceGetAttribute(&t->sm_count, cudaDevAttrMultiProcessorCount, t->device));
+    MDRQ_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->blocks_per_sm[0], mdrq_scan_kernel<1>, kBlock, 0));
+    MDRQ_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->blocks_per_sm[1], mdrq_scan_kernel<2>, kBlock, 0));
+    MDRQ_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->blocks_per_sm[2], mdrq_scan_kernel<4>, kBlock, 0));
+    for (int i = 0; i < 3; ++i)
+        t->blocks_per_sm[i] = std::max(1, t->blocks_per_sm[i]);
+    t->n = n;
+    t->d = d;
+    t->cols.resize(d);
+
+    for (uint32_t j = 0; j < d; ++j) {
+        t->cols[j].type = types[j];
+        if (n == 0)
+            continue;
+        if (cols_on_device) {
+            t->cols[j].ptr = cols[j];
+        } else {
+            void *p = nullptr;
+            MDRQ_TRY(cudaMalloc(&p, (size_t)((n * 4 + 15) & ~15ull)));
+            t->owned.push_back(p);
+            MDRQ_TRY(cudaMemcpyAsync(p, cols[j], (size_t)n * 4, cudaMemcpyHostToDevice, s));
+            t->cols[j].ptr = p;
+        }
+    }
+
+    // scratch sized for the smallest tile (1024 rows)
+    const uint64_t max_tiles = (n + tile_rows<1>() - 1) / tile_rows<1>();
+    t->state_words = (uint32_t)std::max<uint64_t>(1, max_tiles);
+    MDRQ_TRY(cudaMalloc(&t->scratch, (size_t)(2 + t->state_words) * 8));
+    t->ticket = t->scratch;
+    t->error = reinterpret_cast<int *>(t->scratch + 1);
+    t->tile_state = t->scratch + 2;
+    MDRQ_TRY(cudaMemsetAsync(t->scratch, 0, (size_t)(2 + t->state_words) * 8, s));
+    MDRQ_TRY(cudaMallocHost((void **)&t->error_host, sizeof(int)));
+
+    if (n == 0)
+        return cuda_status(cudaStreamSynchronize(s));
+
+    // exact minimum / maximum, NaN count and a strided sample of every column
+    unsigned long long *stats = nullptr;
+    uint32_t *sample = nullptr;
+    const uint32_t S = (uint32_t)std::min<uint64_t>(n, kSampleRows);
+    MDRQ_TRY(cudaMalloc(&stats, (size_t)d * 3 * 8));
+    MDRQ_TRY(cudaMalloc(&sample, (size_t)d * S * 4));
+    std::vector<unsigned long long> init(3 * (size_t)d);
+    for (uint32_t j = 0; j < d; ++j) {
+        init[3 * j] = 0;
+        init[3 * j + 1] = ~0ull;
+        init[3 * j + 2] = 0;
+    }
+    int st = MDRQ_OK;
+    std::vector<unsigned long long> h_stats(3 * (size_t)d);
+    std::vector<uint32_t> h_sample((size_t)d * S);
+    do {
+        if ((st = cuda_status(cudaMemcpyAsync(stats, init.data(), init.size() * 8, cudaMemcpyHostToDevice, s))))
+            break;
+        const uint32_t grid = (uint32_t)std::min<uint64_t>((n + kBlock - 1) / kBlock, (uint64_t)t->sm_count * 8);
+        for (uint32_t j = 0; j < d; ++j) {
+            mdrq_column_stats_kernel<<<grid, kBlock, 0, s>>>((const uint32_t *)t->cols[j].ptr, n,
+                                                             (uint32_t)types[j], stats + 3 * j);
+            mdrq_sample_kernel<<<(S + 255) / 256, 256, 0, s>>>((const uint32_t *)t->cols[j].ptr, n, S,
+                                                              sample + (size_t)j * S);
+        }
+        if ((st = cuda_status(cudaGetLastError())))
+            break;
+        if ((st = cuda_status(cudaMemcpyAsync(h_stats.data(), stats, h_stats.size() * 8, cudaMemcpyDeviceToHost, s))))
+            break;
+        if ((st = cuda_status(cudaMemcpyAsync(h_sample.data(), sample, h_sample.size() * 4, cudaMemcpyDeviceToHost, s))))
+            break;
+        st = cuda_status(cudaStreamSynchronize(s));
+    } while (0);
+    cudaFree(stats);
+    cudaFree(sample);
+    if (st != MDRQ_OK)
+        return st;
+    for (uint32_t j = 0; j < d; ++j) {
+        if (h_stats[3 * j] != 0)
+            return MDRQ_E_NAN;
+        ColumnInfo &c = t->cols[j];
+        c.min_bits = bits_from_key(h_stats[3 * j + 1], c.type);
+        c.max_bits = bits_from_key(h_stats[3 * j + 2], c.type);
+        c.sample.resize(S);
+        for (uint32_t i = 0; i < S; ++i)
+            c.sample[i] = bound_value(h_sample[(size_t)j * S + i], c.type);
+        std::sort(c.sample.begin(), c.sample.end());
+    }
+    return MDRQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mdrq_load_columns(const void *const *cols, const int32_t *types, uint32_t d, uint64_t n,
+                      int cols_on_device, void *stream, mdrq_table **out)
+{
+    if (!out)
+        return MDRQ_E_INVAL;
+    *out = nullptr;
+    if (d == 0 || n > 0xFFFFFFFFull || !types || (n > 0 && !cols))
+        return MDRQ_E_INVAL;
+    for (uint32_t j = 0; j < d; ++j) {
+        if (types[j] != MDRQ_F32 && types[j] != MDRQ_I32)
+            return MDRQ_E_INVAL;
+        if (n > 0 && !cols[j])
+            return MDRQ_E_INVAL;
+        if (n > 0 && cols_on_device && (reinterpret_cast<uintptr_t>(cols[j]) & 15u))
+            return MDRQ_E_INVAL;
+    }
+    mdrq_table *t = new (std::nothrow) mdrq_table();
+    if (!t)
+        return MDRQ_E_NOMEM;
+    int st = load(cols, types, d, n, cols_on_device, as_stream(stream), t);
+    if (st != MDRQ_OK) {
+        destroy(t);
+        return st;
+    }
+    *out = t;
+    return MDRQ_OK;
+}
+
+int mdrq_query(mdrq_table *t, const mdrq_pred *preds, uint32_t npreds, uint32_t *ids,
+               uint64_t capacity, uint64_t *count, int ids_on_device, void *stream)
+{
+    if (!t || !count)
+        return MDRQ_E_INVAL;
+    mdrq_qdesc q;
+    q.preds = preds;
+    q.npreds = npreds;
+    q.reserved = 0;
+    uint64_t off[2] = {0, 0};
+    int st = run_batch(t, &q, 1, ids, capacity, off, ids_on_device, as_stream(stream));
+    if (st == MDRQ_OK || st == MDRQ_E_CAPACITY)
+        *count = off[1];
+    return st;
+}
+
+int mdrq_query_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids,
+                     uint64_t capacity, uint64_t *offsets, int ids_on_device, void *stream)
+{
+    return run_batch(t, qs, nq, ids, capacity, offsets, ids_on_device, as_stream(stream));
+}
+
+void mdrq_free(mdrq_table *t) { destroy(t); }
+
+const char *mdrq_status_string(int status)
+{
+    switch (status) {
+    case MDRQ_OK: return "ok";
+    case MDRQ_E_INVAL: return "invalid argument";
+    case MDRQ_E_NOMEM: return "out of memory";
+    case MDRQ_E_CUDA: return "CUDA error";
+    case MDRQ_E_CAPACITY: return "answer longer than the id buffer";
+    case MDRQ_E_TIMEOUT: return "device wait timed out";
+    case MDRQ_E_NAN: return "NaN in a float32 column";
+    default: return "unknown status";
+    }
+}
+
+uint64_t mdrq_table_rows(const mdrq_table *t) { return t ? t->n : 0; }
+uint32_t mdrq_table_dims(const mdrq_table *t) { return t ? t->d : 0; }
+
+int mdrq_scan_timing(mdrq_table *t, int enable)
+{
+    if (!t)
+        return MDRQ_E_INVAL;
+    t->timing = enable != 0;
+    return MDRQ_OK;
+}
+
+int mdrq_scan_timing_read(mdrq_table *t, double *ms, uint64_t *scan_launches, uint64_t *bytes,
+                          uint64_t *kernel_launches, int reset)
+{
+    if (!t)
+        return MDRQ_E_INVAL;
+    double total = 0.0;
+    if (t->ev_used > 0) {
+        MDRQ_TRY(cudaEventSynchronize(t->ev[2 * t->ev_used - 1]));
+        for (size_t i = 0; i < t->ev_used; ++i) {
+            float x = 0.f;
+            MDRQ_TRY(cudaEventElapsedTime(&x, t->ev[2 * i], t->ev[2 * i + 1]));
+            total += x;
+        }
+    }
+    if (ms)
+        *ms = total;
+    if (scan_launches)
+        *scan_launches = t->acc_scans;
+    if (bytes)
+        *bytes = t->acc_bytes;
+    if (kernel_launches)
+        *kernel_launches = t->acc_kernels;
+    if (reset) {
+        t->ev_used = 0;
+        t->acc_scans = t->acc_bytes = t->acc_kernels = 0;
+    }
+    return MDRQ_OK;
+}
+
+void mdrq_last_scan_stats(const mdrq_table *t, uint64_t *launches, uint64_t *bytes)
+{
+    if (launches)
+        *launches = t ? t->last_launches : 0;
+    if (bytes)
+        *bytes = t ? t->last_bytes : 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,373 @@
+// Fused filter + ordered compaction scan for one multidimensional range query.
+//
+// Method (arXiv 1801.03644): an object qualifies iff lo_j <= x_j <= hi_j on every
+// constrained dimension (Sec. 2.1); the scan visits every object (Sec. 2.2.4), over a
+// column-wise layout so that only constrained columns are read (Sec. 3.2, Sec. 5.5);
+// per-dimension results are ANDed into a bitmask (Sec. 3.2) and the ids of matching
+// objects are produced in index order, which the paper gets by concatenating the
+// partial results of its partitions (Sec. 3.1).
+//
+// GB300 design:
+//  * A persistent grid claims row tiles in increasing order from a global ticket.
+//    Each warp owns U*128 consecutive rows of a tile; lane l reads rows
+//    4l..4l+3 of every 128-row group with one 128-bit load per column
+//    (512 contiguous bytes per warp instruction).
+//  * The per-row mask of U*4 bits lives in a register. Predicates are applied one
+//    column at a time; a lane whose rows have all failed issues no load for the
+//    remaining columns, so the memory system never fetches a 32-byte sector whose
+//    8 rows are already rejected (the early break of Sec. 2.2.4 at sector
+//    granularity), and a warp whose rows have all failed stops reading columns.
+//  * Matches are ranked with a packed warp scan, staged in shared memory in row
+//    order, and the tile's offset in the answer comes from a single-pass decoupled
+//    look-back over per-tile states (aggregate / inclusive prefix), so the answer is
+//    written once, coalesced and ascending, without a second pass over the columns.
+//  * Every wait on another tile's state is bounded; on expiry the kernel records
+//    an error bit and finishes, never traps.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mdrq {
+
+constexpr int kBlock = 256;
+constexpr int kWarps = kBlock / 32;
+constexpr int kMaxPreds = 128;
+
+constexpr uint32_t kTypeF32 = 0;
+constexpr uint32_t kTypeI32 = 1;
+
+// tile state word: [63:34] epoch, [33:32] flag, [31:0] value
+constexpr uint32_t kFlagAggregate = 1;
+constexpr uint32_t kFlagPrefix = 2;
+constexpr uint32_t kEpochLimit = (1u << 30) - 1;
+
+constexpr int kErrLookbackTimeout = 1;
+constexpr uint32_t kMaxPolls = 1u << 20;  // x <= 1 us backoff: bounded by about 1 s
+
+struct ScanPred {
+    const void *col;  // device column (16-byte aligned)
+    uint32_t type;    // kTypeF32 / kTypeI32
+    uint32_t lo;      // bound bits, read as the column's type
+    uint32_t hi;
+    uint32_t pad;
+};
+
+struct ScanParams {
+    ScanPred pred[kMaxPreds];
+    uint32_t npred;
+    uint32_t n_tiles;
+    uint64_t n;
+    unsigned long long *tile_state;  // n_tiles words
+    unsigned long long *ticket;      // monotone claim counter
+    unsigned long long ticket_base;  // counter value when this launch starts
+    uint32_t epoch;                  // tag of this launch in tile_state
+    uint32_t pad0;
+    uint32_t *ids;                   // answer buffer
+    uint64_t capacity;               // slots in ids
+    const unsigned long long *base_in;  // offset of this answer in ids (NULL: 0)
+    unsigned long long *count_out;   // receives base + answer length
+    int *error;                      // error bits (kErr*)
+};
+
+__device__ __forceinline__ uint4 ld_stream_v4(const void *p)
+{
+    uint4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_stream_u32(const void *p)
+{
+    uint32_t v;
+    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long pack_state(uint32_t epoch, uint32_t flag, uint32_t v)
+{
+    return ((unsigned long long)epoch << 34) | ((unsigned long long)flag << 32) | v;
+}
+
+// 4-bit mask of the rows of one 16-byte chunk that lie in [lo, hi]
+__device__ __forceinline__ uint32_t in_range4(uint4 v, uint32_t type, uint32_t lo, uint32_t hi)
+{
+    uint32_t r;
+    if (type == kTypeF32) {
+        const float l = __uint_as_float(lo), h = __uint_as_float(hi);
+        const float a = __uint_as_float(v.x), b = __uint_as_float(v.y);
+        const float c = __uint_as_float(v.z), d = __uint_as_float(v.w);
+        r = (uint32_t)((l <= a) & (a <= h)) | ((uint32_t)((l <= b) & (b <= h)) << 1) |
+            ((uint32_t)((l <= c) & (c <= h)) << 2) | ((uint32_t)((l <= d) & (d <= h)) << 3);
+    } else {
+        const int l = (int)lo, h = (int)hi;
+        const int a = (int)v.x, b = (int)v.y, c = (int)v.z, d = (int)v.w;
+        r = (uint32_t)((l <= a) & (a <= h)) | ((uint32_t)((l <= b) & (b <= h)) << 1) |
+            ((uint32_t)((l <= c) & (c <= h)) << 2) | ((uint32_t)((l <= d) & (d <= h)) << 3);
+    }
+    return r;
+}
+
+// Exclusive prefix of `total` over all earlier tiles (decoupled look-back), run by one
+// full warp. Publishes this tile's aggregate first and its inclusive prefix last.
+__device__ __forceinline__ uint32_t tile_lookback(const ScanParams &p, unsigned long long tile,
+                                                  uint32_t total, int lane)
+{
+    unsigned long long *st = p.tile_state;
+    if (tile == 0) {
+        if (lane == 0)
+            st_relaxed_u64(&st[0], pack_state(p.epoch, kFlagPrefix, total));
+        return 0;
+    }
+    if (lane == 0)
+        st_relaxed_u64(&st[tile], pack_state(p.epoch, kFlagAggregate, total));
+
+    unsigned long long excl = 0;
+    long long idx = (long long)tile - 1;  // nearest predecessor
+    uint32_t polls = 0, backoff = 32;
+    for (;;) {
+        const long long my = idx - lane;
+        uint32_t flag = kFlagPrefix, val = 0;  // before tile 0: an inclusive prefix of 0
+        if (my >= 0) {
+            const unsigned long long w = ld_relaxed_u64(&st[my]);
+            flag = (uint32_t)(w >> 34) == p.epoch ? (uint32_t)(w >> 32) & 3u : 0u;
+            val = (uint32_t)w;
+        }
+        if (__any_sync(0xffffffffu, flag == 0)) {
+            if (++polls < kMaxPolls) {
+                __nanosleep(backoff);
+                backoff = backoff < 1024 ? backoff * 2 : 1024;
+                continue;
+            }
+            // gave up: record it and treat the missing states as empty prefixes
+            if (lane == 0)
+                atomicOr(p.error, kErrLookbackTimeout);
+            if (flag == 0) {
+                flag = kFlagPrefix;
+                val = 0;
+            }
+        }
+        const uint32_t pmask = __ballot_sync(0xffffffffu, flag == kFlagPrefix);
+        const int stop = pmask ? __ffs(pmask) - 1 : 31;  // nearest lane holding a prefix
+        unsigned long long v = lane <= stop ? val : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            v += __shfl_xor_sync(0xffffffffu, v, o);
+        excl += v;
+        if (pmask)
+            break;
+        idx -= 32;
+    }
+    if (lane == 0)
+        st_relaxed_u64(&st[tile], pack_state(p.epoch, kFlagPrefix, (uint32_t)(excl + total)));
+    return (uint32_t)excl;
+}
+
+template <int U>
+__global__ void __launch_bounds__(kBlock) mdrq_scan_kernel(const __grid_constant__ ScanParams p)
+{
+    constexpr int kWarpRows = U * 128;
+    constexpr int kTileRows = kWarps * kWarpRows;
+    constexpr uint32_t kFullMask = (U * 4 == 32) ? 0xffffffffu : ((1u << (U * 4)) - 1u);
+
+    __shared__ uint32_t s_stage[kTileRows];
+    __shared__ uint32_t s_warp_total[kWarps];
+    __shared__ unsigned long long s_ticket[2];
+    __shared__ uint32_t s_prefix;
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const unsigned long long base = p.base_in ? *p.base_in : 0ull;
+
+    if (threadIdx.x == 0)
+        s_ticket[0] = atomicAdd(p.ticket, 1ull) - p.ticket_base;
+    __syncthreads();
+    unsigned long long tile = s_ticket[0];
+    int slot = 0;
+
+    while (tile < p.n_tiles) {
+        // claim the next tile now so the round trip overlaps this tile's loads
+        if (threadIdx.x == 0)
+            s_ticket[slot ^ 1] = atomicAdd(p.ticket, 1ull) - p.ticket_base;
+
+        const uint64_t row0 = tile * (uint64_t)kTileRows + (uint64_t)warp * kWarpRows;
+        const bool full = row0 + kWarpRows <= p.n;
+
+        // bit 4u+e of m: row row0 + 128u + 4*lane + e still qualifies
+        uint32_t m = 0;
+        if (full) {
+            m = kFullMask;
+        } else {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (row0 + 128u * u + 4u * lane + e < p.n)
+                        m |= 1u << (4 * u + e);
+        }
+
+        for (uint32_t i = 0; i < p.npred; ++i) {
+            if (!__any_sync(0xffffffffu, m))
+                break;  // every row of this warp's chunk failed: read no more columns
+            const ScanPred &pr = p.pred[i];
+            const uint32_t *col = (const uint32_t *)pr.col + row0 + 4 * lane;
+            uint4 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                v[u] = make_uint4(0, 0, 0, 0);
+                const uint32_t mu = (m >> (4 * u)) & 0xfu;
+                if (mu) {
+                    if (full || mu == 0xfu) {
+                        v[u] = ld_stream_v4(col + 128 * u);
+                    } else {
+                        // ragged end of the table: only rows < n may be read
+                        if (mu & 1u) v[u].x = ld_stream_u32(col + 128 * u + 0);
+                        if (mu & 2u) v[u].y = ld_stream_u32(col + 128 * u + 1);
+                        if (mu & 4u) v[u].z = ld_stream_u32(col + 128 * u + 2);
+                        if (mu & 8u) v[u].w = ld_stream_u32(col + 128 * u + 3);
+                    }
+                }
+            }
+            uint32_t keep = 0;
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                keep |= in_range4(v[u], pr.type, pr.lo, pr.hi) << (4 * u);
+            m &= keep;
+        }
+
+        // rank the matches of this warp: row order is (u, lane, e)
+        uint32_t packed = 0;  // 8-bit count per u
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            packed |= (uint32_t)__popc((m >> (4 * u)) & 0xfu) << (8 * u);
+        uint32_t incl = packed;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o)
+                incl += t;
+        }
+        const uint32_t excl_lane = incl - packed;
+        const uint32_t warp_packed = __shfl_sync(0xffffffffu, incl, 31);
+        uint32_t warp_total = 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            warp_total += (warp_packed >> (8 * u)) & 0xffu;
+        if (lane == 0)
+            s_warp_total[warp] = warp_total;
+        __syncthreads();
+
+        uint32_t tile_total = 0, warp_off = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t t = s_warp_total[w];
+            warp_off += w < warp ? t : 0u;
+            tile_total += t;
+        }
+
+        // stage the ids of this warp's matches in row order
+        uint32_t ubase = warp_off;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            uint32_t mu = (m >> (4 * u)) & 0xfu;
+            uint32_t r = ubase + ((excl_lane >> (8 * u)) & 0xffu);
+            const uint32_t id0 = (uint32_t)(row0 + 128u * u + 4u * lane);
+            while (mu) {
+                const int e = __ffs(mu) - 1;
+                s_stage[r++] = id0 + e;
+                mu &= mu - 1;
+            }
+            ubase += (warp_packed >> (8 * u)) & 0xffu;
+        }
+
+        if (warp == 0) {
+            const uint32_t prefix = tile_lookback(p, tile, tile_total, lane);
+            if (lane == 0) {
+                s_prefix = prefix;
+                if (tile == p.n_tiles - 1)
+                    *p.count_out = base + prefix + tile_total;
+            }
+        }
+        __syncthreads();
+
+        const unsigned long long out0 = base + s_prefix;
+        for (uint32_t r = threadIdx.x; r < tile_total; r += kBlock) {
+            const unsigned long long pos = out0 + r;
+            if (pos < p.capacity)
+                p.ids[pos] = s_stage[r];
+        }
+        __syncthreads();
+        tile = s_ticket[slot ^ 1];
+        slot ^= 1;
+    }
+}
+
+// offsets[q+1] = offsets[q] for a query the host proved empty
+__global__ void mdrq_copy_offset_kernel(const unsigned long long *in, unsigned long long *out)
+{
+    *out = *in;
+}
+
+// NaN count, minimum and maximum of a column. out[0] += NaNs; out[1] / out[2] hold the
+// minimum / maximum as order-preserving keys (see key_of).
+__device__ __forceinline__ unsigned long long key_of(uint32_t bits, uint32_t type)
+{
+    if (type == kTypeF32)
+        return (bits & 0x80000000u) ? (unsigned long long)(~bits) : (unsigned long long)(bits | 0x80000000u);
+    return (unsigned long long)(bits ^ 0x80000000u);
+}
+
+__global__ void __launch_bounds__(kBlock)
+    mdrq_column_stats_kernel(const uint32_t *col, uint64_t n, uint32_t type, unsigned long long *out)
+{
+    unsigned long long nan = 0, mn = ~0ull, mx = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t b = col[i];
+        if (type == kTypeF32 && (b & 0x7fffffffu) > 0x7f800000u) {
+            ++nan;
+            continue;
+        }
+        const unsigned long long k = key_of(b, type);
+        mn = k < mn ? k : mn;
+        mx = k > mx ? k : mx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nan += __shfl_xor_sync(0xffffffffu, nan, o);
+        const unsigned long long a = __shfl_xor_sync(0xffffffffu, mn, o);
+        const unsigned long long b = __shfl_xor_sync(0xffffffffu, mx, o);
+        mn = a < mn ? a : mn;
+        mx = b > mx ? b : mx;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (nan)
+            atomicAdd(&out[0], nan);
+        atomicMin(&out[1], mn);
+        atomicMax(&out[2], mx);
+    }
+}
+
+// out[s] = col[floor(s * n / S)] for s < S: a strided sample for selectivity estimates
+__global__ void mdrq_sample_kernel(const uint32_t *col, uint64_t n, uint32_t S, uint32_t *out)
+{
+    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < S)
+        out[s] = col[(uint64_t)s * n / S];
+}
+
+}  // namespace mdrq

@@ -1,0 +1,287 @@
+"""Python binding of the MDRQ scan library (``libmdrq.so``, C ABI in ``include/mdrq.h``).
+
+Argument marshalling only: every step of a query runs in the library's CUDA kernels.
+PyTorch provides device memory and streams. There is no CPU fallback: if the library
+is missing or no GPU is present, the calls raise.
+
+Ids are uint32 row indices (ascending per query). Device answers are returned in
+``torch.int32`` tensors holding the uint32 bit patterns (identical for n < 2^31); use
+``as_uint32_numpy`` to read them as uint32 on the host.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmdrq.so")
+
+F32, I32 = 0, 1
+OK, E_INVAL, E_NOMEM, E_CUDA, E_CAPACITY, E_TIMEOUT, E_NAN = 0, -1, -2, -3, -4, -5, -6
+
+
+class MDRQError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__("%s failed: %s (status %d)" % (what, status_string(status), status))
+        self.status = status
+
+
+class Pred(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("lo", ctypes.c_uint32), ("hi", ctypes.c_uint32)]
+
+
+class QDesc(ctypes.Structure):
+    _fields_ = [("preds", ctypes.POINTER(Pred)), ("npreds", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+_lib = None
+
+EXPORTS = ["mdrq_load_columns", "mdrq_query", "mdrq_query_batch", "mdrq_free",
+           "mdrq_status_string", "mdrq_table_rows", "mdrq_table_dims", "mdrq_last_scan_stats",
+           "mdrq_scan_timing", "mdrq_scan_timing_read"]
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libmdrq.so is not built (run __graft_entry__.build()): %s" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32
+        L.mdrq_load_columns.restype = ctypes.c_int
+        L.mdrq_load_columns.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(i32), u32, u64,
+                                        ctypes.c_int, vp, ctypes.POINTER(vp)]
+        L.mdrq_query.restype = ctypes.c_int
+        L.mdrq_query.argtypes = [vp, ctypes.POINTER(Pred), u32, vp, u64,
+                                 ctypes.POINTER(u64), ctypes.c_int, vp]
+        L.mdrq_query_batch.restype = ctypes.c_int
+        L.mdrq_query_batch.argtypes = [vp, ctypes.POINTER(QDesc), u32, vp, u64,
+                                       ctypes.POINTER(u64), ctypes.c_int, vp]
+        L.mdrq_free.restype = None
+        L.mdrq_free.argtypes = [vp]
+        L.mdrq_status_string.restype = ctypes.c_char_p
+        L.mdrq_status_string.argtypes = [ctypes.c_int]
+        L.mdrq_table_rows.restype = u64
+        L.mdrq_table_rows.argtypes = [vp]
+        L.mdrq_table_dims.restype = u32
+        L.mdrq_table_dims.argtypes = [vp]
+        L.mdrq_last_scan_stats.restype = None
+        L.mdrq_last_scan_stats.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]
+        L.mdrq_scan_timing.restype = ctypes.c_int
+        L.mdrq_scan_timing.argtypes = [vp, ctypes.c_int]
+        L.mdrq_scan_timing_read.restype = ctypes.c_int
+        L.mdrq_scan_timing_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64),
+                                            ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.c_int]
+        _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return lib().mdrq_status_string(int(status)).decode()
+    except RuntimeError:
+        return "status %d" % status
+
+
+def _bits(v, dtype: int) -> int:
+    if dtype == F32:
+        return int(np.array([v], dtype=np.float32).view(np.uint32)[0])
+    iv = int(v)
+    if not -2**31 <= iv < 2**31:
+        raise ValueError("int32 bound out of range: %r" % v)
+    return iv & 0xFFFFFFFF
+
+
+def encode_query(query, dtypes) -> ctypes.Array:
+    """(dim, lo, hi) predicates -> a ctypes array of mdrq_pred (bounds in column type)."""
+    arr = (Pred * max(1, len(query)))()
+    for i, (j, lo, hi) in enumerate(query):
+        j = int(j)
+        if not 0 <= j < len(dtypes):
+            raise ValueError("dimension %d out of range" % j)
+        arr[i].dim = j
+        arr[i].reserved = 0
+        arr[i].lo = _bits(lo, dtypes[j])
+        arr[i].hi = _bits(hi, dtypes[j])
+    return arr
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def as_uint32_numpy(t) -> np.ndarray:
+    return t.detach().cpu().numpy().view(np.uint32)
+
+
+class Table:
+    """A table resident on the current CUDA device (``mdrq_load_columns``).
+
+    ``columns``: d CUDA tensors (float32 / int32, 1-D, same length) referenced in place
+    (they must stay alive and unchanged), or d numpy arrays copied to the device.
+    """
+
+    def __init__(self, columns, stream=None):
+        import torch
+        L = lib()
+        if not torch.cuda.is_available():
+            raise RuntimeError("MDRQ tables need a CUDA device")
+        self._keep = []
+        on_device = all(isinstance(c, torch.Tensor) and c.is_cuda for c in columns)
+        ptrs, dtypes = [], []
+        n = None
+        for c in columns:
+            if on_device:
+                if c.dim() != 1 or not c.is_contiguous():
+                    raise ValueError("device columns must be contiguous 1-D tensors")
+                dt = {torch.float32: F32, torch.int32: I32}.get(c.dtype)
+                ptrs.append(c.data_ptr())
+                ln = c.numel()
+            else:
+                a = np.ascontiguousarray(c)
+                dt = {np.dtype(np.float32): F32, np.dtype(np.int32): I32}.get(a.dtype)
+                ptrs.append(a.ctypes.data)
+                ln = a.shape[0]
+                c = a
+            if dt is None:
+                raise TypeError("columns must be float32 or int32")
+            if n is None:
+                n = ln
+            elif n != ln:
+                raise ValueError("columns differ in length")
+            dtypes.append(dt)
+            self._keep.append(c)
+        self.n = int(n or 0)
+        self.d = len(columns)
+        self.dtypes = dtypes
+        h = ctypes.c_void_p()
+        st = L.mdrq_load_columns((ctypes.c_void_p * max(1, self.d))(*ptrs),
+                                 (ctypes.c_int32 * max(1, self.d))(*dtypes), self.d, self.n,
+                                 1 if on_device else 0, _stream_handle(stream), ctypes.byref(h))
+        if not on_device:
+            self._keep = []  # the library holds its own copy now
+        if st != OK:
+            raise MDRQError(st, "mdrq_load_columns")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mdrq_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # ------------------------------------------------------------------ queries
+
+    def query(self, query, out=None, stream=None):
+        """Answer one query; returns a device int32 tensor of ascending ids.
+
+        ``out``: optional preallocated device int32 tensor; its length is the capacity.
+        Without it the answer is sized exactly (a count call first if needed)."""
+        import torch
+        preds = encode_query(query, self.dtypes)
+        cnt = ctypes.c_uint64(0)
+        if out is None:
+            cap = min(self.n, 1 << 20)
+            out = torch.empty(max(1, cap), dtype=torch.int32, device="cuda")
+            st = lib().mdrq_query(self._h, preds, len(query), out.data_ptr(), cap,
+                                  ctypes.byref(cnt), 1, _stream_handle(stream))
+            if st == E_CAPACITY:
+                out = torch.empty(int(cnt.value), dtype=torch.int32, device="cuda")
+                st = lib().mdrq_query(self._h, preds, len(query), out.data_ptr(), out.numel(),
+                                      ctypes.byref(cnt), 1, _stream_handle(stream))
+        else:
+            st = lib().mdrq_query(self._h, preds, len(query), out.data_ptr(), out.numel(),
+                                  ctypes.byref(cnt), 1, _stream_handle(stream))
+        if st != OK:
+            raise MDRQError(st, "mdrq_query")
+        return out[: int(cnt.value)]
+
+    def query_host(self, query, capacity=None, stream=None) -> np.ndarray:
+        """Answer one query into host memory (``ids_on_device = 0``); uint32 numpy array."""
+        preds = encode_query(query, self.dtypes)
+        cap = self.n if capacity is None else int(capacity)
+        out = np.empty(max(1, cap), dtype=np.uint32)
+        cnt = ctypes.c_uint64(0)
+        st = lib().mdrq_query(self._h, preds, len(query), out.ctypes.data, cap, ctypes.byref(cnt),
+                              0, _stream_handle(stream))
+        if st != OK:
+            raise MDRQError(st, "mdrq_query")
+        return out[: int(cnt.value)]
+
+    def encode_batch(self, queries):
+        """Pre-encode a batch (the ctypes arrays must outlive the call)."""
+        keep = [encode_query(q, self.dtypes) for q in queries]
+        descs = (QDesc * max(1, len(queries)))()
+        for i, (q, a) in enumerate(zip(queries, keep)):
+            descs[i].preds = ctypes.cast(a, ctypes.POINTER(Pred))
+            descs[i].npreds = len(q)
+            descs[i].reserved = 0
+        return descs, keep, len(queries)
+
+    def query_batch_raw(self, encoded, ids_ptr: int, capacity: int, ids_on_device: bool,
+                        stream=None):
+        """One ``mdrq_query_batch`` call; returns (status, offsets uint64 numpy)."""
+        descs, _keep, nq = encoded
+        offsets = np.zeros(nq + 1, dtype=np.uint64)
+        st = lib().mdrq_query_batch(self._h, descs, nq, ids_ptr, int(capacity),
+                                    offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                    1 if ids_on_device else 0, _stream_handle(stream))
+        return st, offsets
+
+    def query_batch(self, queries, out=None, stream=None):
+        """Answer a batch; returns (device int32 ids tensor, offsets uint64 numpy)."""
+        import torch
+        enc = self.encode_batch(queries)
+        if out is None:
+            cap = min(self.n * max(1, len(queries)), 1 << 22)
+            out = torch.empty(max(1, cap), dtype=torch.int32, device="cuda")
+        st, off = self.query_batch_raw(enc, out.data_ptr(), out.numel(), True, stream)
+        if st == E_CAPACITY:
+            out = torch.empty(int(off[-1]), dtype=torch.int32, device="cuda")
+            st, off = self.query_batch_raw(enc, out.data_ptr(), out.numel(), True, stream)
+        if st != OK:
+            raise MDRQError(st, "mdrq_query_batch")
+        return out[: int(off[-1])], off
+
+    def scan_timing(self, enable: bool):
+        st = lib().mdrq_scan_timing(self._h, 1 if enable else 0)
+        if st != OK:
+            raise MDRQError(st, "mdrq_scan_timing")
+
+    def scan_timing_read(self, reset: bool = True) -> dict:
+        ms = ctypes.c_double(0)
+        a, b, c = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+        st = lib().mdrq_scan_timing_read(self._h, ctypes.byref(ms), ctypes.byref(a), ctypes.byref(b),
+                                         ctypes.byref(c), 1 if reset else 0)
+        if st != OK:
+            raise MDRQError(st, "mdrq_scan_timing_read")
+        return {"ms": ms.value, "scan_launches": int(a.value), "bytes": int(b.value),
+                "kernel_launches": int(c.value)}
+
+    def last_scan_stats(self):
+        a, b = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        lib().mdrq_last_scan_stats(self._h, ctypes.byref(a), ctypes.byref(b))
+        return int(a.value), int(b.value)

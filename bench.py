@@ -36,14 +36,23 @@ METRIC = "MDRQ queries/s"
 UNIT = "queries/s"
 
 
-def make_workload(name: str, rank: int = 0):
+def make_workload(name: str, rows=None, queries=None):
+    """The named workload at its full size, or at ``rows`` rows with the first ``queries``
+    queries (smaller cases of the same recipe, for profiling)."""
+    kw = {}
+    if rows:
+        kw["n"] = int(rows)
     if name == "mixed_clustered":
-        return W.mixed_clustered()
-    if name == "uniform_1M":
-        return W.uniform_small()
-    if name == "skewed_mixed":
-        return W.skewed_mixed_types()
-    raise SystemExit("unknown workload %s" % name)
+        wl = W.mixed_clustered(**kw)
+    elif name == "uniform_1M":
+        wl = W.uniform_small(**kw)
+    elif name == "skewed_mixed":
+        wl = W.skewed_mixed_types(**kw)
+    else:
+        raise SystemExit("unknown workload %s" % name)
+    if queries:
+        wl.queries = wl.queries[: int(queries)]
+    return wl
 
 
 def workload_config(wl, name: str) -> dict:
@@ -164,7 +173,7 @@ def run_reference(args, rank: int, world: int) -> None:
     """The CPU oracle on the host cores: each step a bounded sample of the same batch."""
     if rank != 0:
         return
-    wl = make_workload(args.workload)
+    wl = make_workload(args.workload, args.rows, args.queries)
     nthreads = os.cpu_count() or 1
     # size the sample so that one step takes about --cpu-seconds
     m, secs = time_oracle(wl, args.cpu_seconds, nthreads)
@@ -200,7 +209,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
 
     torch.cuda.set_device(local_rank)
     dev = torch.cuda.current_device()
-    wl = make_workload(args.workload)
+    wl = make_workload(args.workload, args.rows, args.queries)
     if world > 1 and rank > 0:
         # each rank answers its own batch: same table recipe, queries from a rank stream
         qrng = W.rng_for(1000 + rank, 1)
@@ -342,6 +351,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="mixed_clustered",
                     choices=["mixed_clustered", "uniform_1M", "skewed_mixed"])
+    ap.add_argument("--rows", type=int, default=None,
+                    help="smaller table of the same recipe (profiling cases)")
+    ap.add_argument("--queries", type=int, default=None, help="first Q queries of the batch only")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

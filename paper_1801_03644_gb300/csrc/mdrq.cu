@@ -282,11 +282,11 @@ int launch_scan(mdrq_table *t, const EncodedQuery &q, uint32_t *ids, uint64_t ca
         MDRQ_TRY(cudaEventRecord(evp[0], s));
     }
     if (ui == 2)
-        mdrq_scan_kernel<4><<<grid, kBlock, 0, s>>>(p);
+        mdrq_scan_kernel<4><<<grid, kScanThreads, 0, s>>>(p);
     else if (ui == 1)
-        mdrq_scan_kernel<2><<<grid, kBlock, 0, s>>>(p);
+        mdrq_scan_kernel<2><<<grid, kScanThreads, 0, s>>>(p);
     else
-        mdrq_scan_kernel<1><<<grid, kBlock, 0, s>>>(p);
+        mdrq_scan_kernel<1><<<grid, kScanThreads, 0, s>>>(p);
     MDRQ_TRY(cudaGetLastError());
     if (evp)
         MDRQ_TRY(cudaEventRecord(evp[1], s));
@@ -411,9 +411,9 @@ int load(const void *const *cols, const int32_t *types, uint32_t d, uint64_t n, 
 {
     MDRQ_TRY(cudaGetDevice(&t->device));
     MDRQ_TRY(cudaDeviceGetAttribute(&t->sm_count, cudaDevAttrMultiProcessorCount, t->device));
-    MDRQ_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->blocks_per_sm[0], mdrq_scan_kernel<1>, kBlock, 0));
-    MDRQ_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->blocks_per_sm[1], mdrq_scan_kernel<2>, kBlock, 0));
-    MDRQ_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->blocks_per_sm[2], mdrq_scan_kernel<4>, kBlock, 0));
+    MDRQ_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->blocks_per_sm[0], mdrq_scan_kernel<1>, kScanThreads, 0));
+    MDRQ_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->blocks_per_sm[1], mdrq_scan_kernel<2>, kScanThreads, 0));
+    MDRQ_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->blocks_per_sm[2], mdrq_scan_kernel<4>, kScanThreads, 0));
     for (int i = 0; i < 3; ++i)
         t->blocks_per_sm[i] = std::max(1, t->blocks_per_sm[i]);
     t->n = n;

@@ -17,12 +17,14 @@
 //    remaining columns, so the memory system never fetches a 32-byte sector whose
 //    8 rows are already rejected (the early break of Sec. 2.2.4 at sector
 //    granularity), and a warp whose rows have all failed stops reading columns.
-//  * Matches are ranked with a packed warp scan, staged in shared memory in row
-//    order, and the tile's offset in the answer comes from a single-pass decoupled
+//  * Matches are ranked with a packed warp scan and staged in shared memory in row
+//    order; the tile's offset in the answer comes from a single-pass decoupled
 //    look-back over per-tile states (aggregate / inclusive prefix), so the answer is
 //    written once, coalesced and ascending, without a second pass over the columns.
-//  * Every wait on another tile's state is bounded; on expiry the kernel records
-//    an error bit and finishes, never traps.
+//  * The look-back and the write-out run in a separate output warp that drains
+//    double-buffered stages, so the eight filter warps never stall on other tiles.
+//  * Every wait (on another tile's state or on a stage) is bounded; on expiry the
+//    kernel records an error bit and finishes, never traps.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -122,20 +124,68 @@ __device__ __forceinline__ uint32_t in_range4(uint4 v, uint32_t type, uint32_t l
     return r;
 }
 
-// Exclusive prefix of `total` over all earlier tiles (decoupled look-back), run by one
-// full warp. Publishes this tile's aggregate first and its inclusive prefix last.
+// ---------------------------------------------------------------- mbarrier helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr unsigned long long kStageWaitNs = 4000000000ull;  // 4 s: longer than a look-back
+
+// Wait for the phase of parity `parity` of `bar` to complete; false after kStageWaitNs.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity))
+        return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > kStageWaitNs)
+            return false;
+    return true;
+}
+
+__device__ __forceinline__ void named_bar_sync(uint32_t id, uint32_t count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Exclusive prefix of all tiles before `tile` (decoupled look-back), run by one full
+// warp once the tile's own aggregate is published; publishes the inclusive prefix.
 __device__ __forceinline__ uint32_t tile_lookback(const ScanParams &p, unsigned long long tile,
                                                   uint32_t total, int lane)
 {
     unsigned long long *st = p.tile_state;
-    if (tile == 0) {
-        if (lane == 0)
-            st_relaxed_u64(&st[0], pack_state(p.epoch, kFlagPrefix, total));
-        return 0;
-    }
-    if (lane == 0)
-        st_relaxed_u64(&st[tile], pack_state(p.epoch, kFlagAggregate, total));
-
     unsigned long long excl = 0;
     long long idx = (long long)tile - 1;  // nearest predecessor
     uint32_t polls = 0, backoff = 32;
@@ -177,32 +227,104 @@ __device__ __forceinline__ uint32_t tile_lookback(const ScanParams &p, unsigned 
     return (uint32_t)excl;
 }
 
+constexpr int kStages = 2;                       // staged tiles per CTA
+constexpr int kScanThreads = kBlock + 32;        // 8 filter warps + 1 output warp
+constexpr unsigned long long kStopTile = ~0ull;  // "no more tiles" marker for the output warp
+constexpr uint32_t kBarFilter = 1;               // named barrier of the 8 filter warps
+
+// Warp-specialised scan. Warps 0-7 ("filter warps") claim tiles, evaluate the
+// predicates, rank the matches and stage their row offsets in one of kStages shared
+// buffers, publish the tile's aggregate, and move on. Warp 8 (the "output warp")
+// takes staged tiles in order, resolves each tile's offset by look-back, publishes the
+// inclusive prefix and writes the ids out, so no filter warp ever waits on another
+// tile. Hand-off uses mbarriers: full[b] (256 filter-thread arrivals) and empty[b]
+// (32 output-lane arrivals); every wait is bounded.
 template <int U>
-__global__ void __launch_bounds__(kBlock) mdrq_scan_kernel(const __grid_constant__ ScanParams p)
+__global__ void __launch_bounds__(kScanThreads, 7) mdrq_scan_kernel(const __grid_constant__ ScanParams p)
 {
+    static_assert(U >= 1 && U <= 4, "8-bit packed counts hold at most 4 groups");
     constexpr int kWarpRows = U * 128;
     constexpr int kTileRows = kWarps * kWarpRows;
-    constexpr uint32_t kFullMask = (U * 4 == 32) ? 0xffffffffu : ((1u << (U * 4)) - 1u);
+    constexpr uint32_t kFullMask = (1u << (U * 4)) - 1u;
+    static_assert(kTileRows <= 65536, "row offsets are staged as 16-bit values");
 
-    __shared__ uint32_t s_stage[kTileRows];
-    __shared__ uint32_t s_warp_total[kWarps];
+    __shared__ uint16_t s_stage[kStages][kTileRows];
+    __shared__ uint32_t s_warp_total[kStages][kWarps];
+    __shared__ unsigned long long s_tile[kStages];
+    __shared__ uint32_t s_total[kStages];
     __shared__ unsigned long long s_ticket[2];
-    __shared__ uint32_t s_prefix;
+    __shared__ unsigned long long s_full[kStages], s_empty[kStages];
+    __shared__ int s_abort;
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const unsigned long long base = p.base_in ? *p.base_in : 0ull;
 
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < kStages; ++b) {
+            mbar_init(&s_full[b], kBlock);
+            mbar_init(&s_empty[b], 32);
+        }
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == kWarps) {
+        // ------------------------------------------------------------ output warp
+        const unsigned long long base = p.base_in ? *p.base_in : 0ull;
+        uint32_t full_phase = 0;  // bit b: parity to wait for on s_full[b]
+        for (uint32_t it = 0;; ++it) {
+            const int b = it % kStages;
+            // every lane waits; the warp leaves together if any lane gave up
+            if (!__all_sync(0xffffffffu, mbar_wait(&s_full[b], (full_phase >> b) & 1u))) {
+                if (lane == 0)
+                    atomicOr(p.error, kErrLookbackTimeout);
+                break;
+            }
+            full_phase ^= 1u << b;
+            const unsigned long long tile = s_tile[b];
+            if (tile == kStopTile)
+                break;
+            const uint32_t total = s_total[b];
+            const uint32_t prefix = tile == 0 ? 0u : tile_lookback(p, tile, total, lane);
+            if (lane == 0 && tile == p.n_tiles - 1)
+                *p.count_out = base + prefix + total;
+            const unsigned long long out0 = base + prefix;
+            const uint32_t row0 = (uint32_t)(tile * (unsigned long long)kTileRows);
+            for (uint32_t r = lane; r < total; r += 32) {
+                const unsigned long long pos = out0 + r;
+                if (pos < p.capacity)
+                    p.ids[pos] = row0 + s_stage[b][r];
+            }
+            __syncwarp();
+            mbar_arrive(&s_empty[b]);
+        }
+        return;
+    }
+
+    // ---------------------------------------------------------------- filter warps
+    uint32_t empty_phase = (1u << kStages) - 1u;  // bit b: parity for s_empty[b]; buffers start empty
     if (threadIdx.x == 0)
         s_ticket[0] = atomicAdd(p.ticket, 1ull) - p.ticket_base;
-    __syncthreads();
+    named_bar_sync(kBarFilter, kBlock);
     unsigned long long tile = s_ticket[0];
     int slot = 0;
+    uint32_t it = 0;
 
     while (tile < p.n_tiles) {
-        // claim the next tile now so the round trip overlaps this tile's loads
-        if (threadIdx.x == 0)
+        const int b = it % kStages;
+        if (threadIdx.x == 0) {
+            if (!mbar_wait(&s_empty[b], (empty_phase >> b) & 1u)) {
+                atomicOr(p.error, kErrLookbackTimeout);
+                s_abort = 1;
+            }
+            // claim the next tile now so the round trip overlaps this tile's loads
             s_ticket[slot ^ 1] = atomicAdd(p.ticket, 1ull) - p.ticket_base;
+        }
+        named_bar_sync(kBarFilter, kBlock);
+        if (s_abort)
+            break;
+        empty_phase ^= 1u << b;
 
         const uint64_t row0 = tile * (uint64_t)kTileRows + (uint64_t)warp * kWarpRows;
         const bool full = row0 + kWarpRows <= p.n;
@@ -268,52 +390,53 @@ __global__ void __launch_bounds__(kBlock) mdrq_scan_kernel(const __grid_constant
         for (int u = 0; u < U; ++u)
             warp_total += (warp_packed >> (8 * u)) & 0xffu;
         if (lane == 0)
-            s_warp_total[warp] = warp_total;
-        __syncthreads();
+            s_warp_total[b][warp] = warp_total;
+        named_bar_sync(kBarFilter, kBlock);
 
         uint32_t tile_total = 0, warp_off = 0;
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) {
-            const uint32_t t = s_warp_total[w];
+            const uint32_t t = s_warp_total[b][w];
             warp_off += w < warp ? t : 0u;
             tile_total += t;
         }
 
-        // stage the ids of this warp's matches in row order
+        // stage the row offsets (within the tile) of this warp's matches in row order
         uint32_t ubase = warp_off;
+        const uint32_t off0 = (uint32_t)warp * kWarpRows + 4u * lane;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             uint32_t mu = (m >> (4 * u)) & 0xfu;
             uint32_t r = ubase + ((excl_lane >> (8 * u)) & 0xffu);
-            const uint32_t id0 = (uint32_t)(row0 + 128u * u + 4u * lane);
             while (mu) {
                 const int e = __ffs(mu) - 1;
-                s_stage[r++] = id0 + e;
+                s_stage[b][r++] = (uint16_t)(off0 + 128u * u + e);
                 mu &= mu - 1;
             }
             ubase += (warp_packed >> (8 * u)) & 0xffu;
         }
 
-        if (warp == 0) {
-            const uint32_t prefix = tile_lookback(p, tile, tile_total, lane);
-            if (lane == 0) {
-                s_prefix = prefix;
-                if (tile == p.n_tiles - 1)
-                    *p.count_out = base + prefix + tile_total;
-            }
+        if (threadIdx.x == 0) {
+            s_tile[b] = tile;
+            s_total[b] = tile_total;
+            // publish the aggregate at once (tile 0: its inclusive prefix)
+            st_relaxed_u64(&p.tile_state[tile],
+                           pack_state(p.epoch, tile == 0 ? kFlagPrefix : kFlagAggregate, tile_total));
         }
-        __syncthreads();
-
-        const unsigned long long out0 = base + s_prefix;
-        for (uint32_t r = threadIdx.x; r < tile_total; r += kBlock) {
-            const unsigned long long pos = out0 + r;
-            if (pos < p.capacity)
-                p.ids[pos] = s_stage[r];
-        }
-        __syncthreads();
+        mbar_arrive(&s_full[b]);
         tile = s_ticket[slot ^ 1];
         slot ^= 1;
+        ++it;
     }
+
+    // tell the output warp that no tile follows
+    const int b = it % kStages;
+    if (threadIdx.x == 0) {
+        if (!s_abort)
+            mbar_wait(&s_empty[b], (empty_phase >> b) & 1u);
+        s_tile[b] = kStopTile;
+    }
+    mbar_arrive(&s_full[b]);
 }
 
 // offsets[q+1] = offsets[q] for a query the host proved empty

@@ -17,6 +17,66 @@
 
 using namespace mdrq;
 
+// ---------------------------------------------------------------- small helper kernels
+
+namespace mdrq {
+
+// offsets[q+1] = offsets[q] for a query the host proved empty
+__global__ void mdrq_copy_offset_kernel(const unsigned long long *in, unsigned long long *out)
+{
+    *out = *in;
+}
+
+// NaN count, minimum and maximum of a column. out[0] += NaNs; out[1] / out[2] hold the
+// minimum / maximum as order-preserving keys (see key_of).
+__device__ __forceinline__ unsigned long long key_of(uint32_t bits, uint32_t type)
+{
+    if (type == kTypeF32)
+        return (bits & 0x80000000u) ? (unsigned long long)(~bits) : (unsigned long long)(bits | 0x80000000u);
+    return (unsigned long long)(bits ^ 0x80000000u);
+}
+
+__global__ void __launch_bounds__(kBlock)
+    mdrq_column_stats_kernel(const uint32_t *col, uint64_t n, uint32_t type, unsigned long long *out)
+{
+    unsigned long long nan = 0, mn = ~0ull, mx = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t b = col[i];
+        if (type == kTypeF32 && (b & 0x7fffffffu) > 0x7f800000u) {
+            ++nan;
+            continue;
+        }
+        const unsigned long long k = key_of(b, type);
+        mn = k < mn ? k : mn;
+        mx = k > mx ? k : mx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nan += __shfl_xor_sync(0xffffffffu, nan, o);
+        const unsigned long long a = __shfl_xor_sync(0xffffffffu, mn, o);
+        const unsigned long long b = __shfl_xor_sync(0xffffffffu, mx, o);
+        mn = a < mn ? a : mn;
+        mx = b > mx ? b : mx;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (nan)
+            atomicAdd(&out[0], nan);
+        atomicMin(&out[1], mn);
+        atomicMax(&out[2], mx);
+    }
+}
+
+// out[s] = col[floor(s * n / S)] for s < S: a strided sample for selectivity estimates
+__global__ void mdrq_sample_kernel(const uint32_t *col, uint64_t n, uint32_t S, uint32_t *out)
+{
+    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < S)
+        out[s] = col[(uint64_t)s * n / S];
+}
+
+}  // namespace mdrq
+
 namespace {
 
 constexpr uint32_t kSampleRows = 4096;  // per-column sample for selectivity estimates

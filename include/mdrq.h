@@ -177,6 +177,44 @@ int mdrq_scan_timing(mdrq_table *t, int enable);
 int mdrq_scan_timing_read(mdrq_table *t, double *ms, uint64_t *scan_launches, uint64_t *bytes,
                           uint64_t *kernel_launches, int reset);
 
+/*
+ * mdrq_query_static — answer one MDRQ like mdrq_query, but without allocating any
+ * memory. The paper has no counterpart: it is an interface for callers that cannot
+ * allocate device memory when they query, such as a serving loop whose device memory
+ * belongs to another allocator's budget, a latency-critical path on which
+ * cudaMalloc's implicit device-wide synchronisation would stall other streams, or
+ * code that must not change the GPU's memory footprint after start-up.
+ *
+ * No table is made: the caller passes its device columns and receives the answer in
+ * its own device buffer. The scan's scratch lives in a fixed array in device memory
+ * inside the library, 512 KiB + 32 bytes on every GPU that loads the library, held
+ * until the process exits; it limits the table to MDRQ_STATIC_MAX_ROWS rows.
+ *
+ *  cols[j], types[j], d, n   as mdrq_load_columns with cols_on_device = 1 (device
+ *                            pointers, 16-byte aligned); n <= MDRQ_STATIC_MAX_ROWS.
+ *  preds, npreds             host predicates, as mdrq_query.
+ *  ids, capacity             device output buffer of `capacity` uint32 slots.
+ *  count                     host; receives the length of the answer.
+ *  stream                    the call synchronises it before returning.
+ *
+ * Every call on a device shares the scratch array and clears the part it uses before
+ * its launch. Calls whose GPU work overlaps (several streams or host threads at once)
+ * race on the array and give wrong answers: serialise them. The first call on a
+ * device sets up that device (it looks up the array's device address, with the
+ * device current): make it before any stream capture. Nothing in this call allocates
+ * memory; in particular it calls neither cudaMalloc nor cudaFree.
+ *
+ * Errors: MDRQ_E_INVAL (n > MDRQ_STATIC_MAX_ROWS, d = 0, a null or misaligned
+ * column, an unknown type, count NULL, ids NULL with capacity > 0, a bad predicate
+ * as for mdrq_query); MDRQ_E_CAPACITY (*count > capacity: the first `capacity` ids
+ * are written); MDRQ_E_TIMEOUT; MDRQ_E_CUDA.
+ */
+#define MDRQ_STATIC_MAX_ROWS 268435456ull /* 2^28 rows: 65536 tiles of 4096 rows */
+
+int mdrq_query_static(const void *const *cols, const int32_t *types, uint32_t d, uint64_t n,
+                      const mdrq_pred *preds, uint32_t npreds, uint32_t *ids, uint64_t capacity,
+                      uint64_t *count, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -42,7 +42,9 @@ _lib = None
 
 EXPORTS = ["mdrq_load_columns", "mdrq_query", "mdrq_query_batch", "mdrq_free",
            "mdrq_status_string", "mdrq_table_rows", "mdrq_table_dims", "mdrq_last_scan_stats",
-           "mdrq_scan_timing", "mdrq_scan_timing_read"]
+           "mdrq_scan_timing", "mdrq_scan_timing_read", "mdrq_query_static"]
+
+STATIC_MAX_ROWS = 1 << 28  # MDRQ_STATIC_MAX_ROWS
 
 
 def lib():
@@ -77,6 +79,9 @@ def lib():
         L.mdrq_scan_timing_read.restype = ctypes.c_int
         L.mdrq_scan_timing_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64),
                                             ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.c_int]
+        L.mdrq_query_static.restype = ctypes.c_int
+        L.mdrq_query_static.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(i32), u32, u64,
+                                        ctypes.POINTER(Pred), u32, vp, u64, ctypes.POINTER(u64), vp]
         _lib = L
     return _lib
 
@@ -120,6 +125,31 @@ def _stream_handle(stream) -> int:
 
 def as_uint32_numpy(t) -> np.ndarray:
     return t.detach().cpu().numpy().view(np.uint32)
+
+
+def query_static(columns, query, out, stream=None):
+    """``mdrq_query_static``: one query over caller-owned device columns with no memory
+    allocated by the library (its scratch is a fixed device array). ``columns``: d
+    contiguous 1-D CUDA tensors (float32 / int32); ``out``: device int32 tensor whose
+    length is the capacity. Returns (status, answer length)."""
+    import torch
+    dtypes = []
+    for c in columns:
+        if not (isinstance(c, torch.Tensor) and c.is_cuda and c.dim() == 1 and c.is_contiguous()):
+            raise ValueError("columns must be contiguous 1-D CUDA tensors")
+        dt = {torch.float32: F32, torch.int32: I32}.get(c.dtype)
+        if dt is None:
+            raise TypeError("columns must be float32 or int32")
+        dtypes.append(dt)
+    d = len(columns)
+    n = columns[0].numel() if d else 0
+    preds = encode_query(query, dtypes)
+    cnt = ctypes.c_uint64(0)
+    st = lib().mdrq_query_static((ctypes.c_void_p * max(1, d))(*[c.data_ptr() for c in columns]),
+                                 (ctypes.c_int32 * max(1, d))(*dtypes), d, n, preds, len(query),
+                                 out.data_ptr(), out.numel(), ctypes.byref(cnt),
+                                 _stream_handle(stream))
+    return st, int(cnt.value)
 
 
 class Table:

@@ -205,7 +205,7 @@ def run_reference(args, rank: int, world: int) -> None:
 def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     import torch
     import torch.distributed as dist
-    from paper_1801_03644_gb300 import mdrq
+    from paper_1801_03644_gb300 import mdrq, shards
 
     torch.cuda.set_device(local_rank)
     dev = torch.cuda.current_device()
@@ -268,10 +268,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     timing = table.scan_timing_read(reset=True)
     table.scan_timing(False)
     clocks = sampler.stop()
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = shards.max_over_ranks(ms)  # the slowest rank's time counts
     value = world * nq * args.steps / (ms / 1e3)
 
     # ---- end to end: host query descriptors in, host answers out (pinned)
@@ -295,10 +292,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
         torch.cuda.synchronize()
         barrier()
         e2e_s = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = shards.max_over_ranks(e2e_s)
         npreds = sum(len(q) for q in wl.queries)
         e2e = {"value": world * nq * args.steps / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": 16 * npreds + 16 * nq,

@@ -178,6 +178,23 @@ int mdrq_scan_timing_read(mdrq_table *t, double *ms, uint64_t *scan_launches, ui
                           uint64_t *kernel_launches, int reset);
 
 /*
+ * mdrq_inject_fault — test hook for failure detection; the paper has no counterpart.
+ * Arms one fault for the next query call on this table:
+ *  MDRQ_FAULT_SKIP_TILES  the next scan launch never claims its first `arg` (>= 1) row
+ *                         tiles, so the ordered compaction of the first claimed tile
+ *                         waits on predecessor states that nothing will set. The
+ *                         bounded wait runs out (about a second), the kernel records an
+ *                         error bit and finishes, and the call returns MDRQ_E_TIMEOUT;
+ *                         the table's scratch is then reset and stays usable.
+ *  MDRQ_FAULT_NOMEM       the next query call fails as if its scratch allocation had
+ *                         failed: MDRQ_E_NOMEM, nothing launched.
+ * Errors: MDRQ_E_INVAL (t NULL, unknown kind, SKIP_TILES with arg = 0).
+ */
+#define MDRQ_FAULT_SKIP_TILES 1
+#define MDRQ_FAULT_NOMEM 2
+int mdrq_inject_fault(mdrq_table *t, int kind, uint64_t arg);
+
+/*
  * mdrq_query_static — answer one MDRQ like mdrq_query, but without allocating any
  * memory. The paper has no counterpart: it is an interface for callers that cannot
  * allocate device memory when they query, such as a serving loop whose device memory

@@ -131,6 +131,10 @@ struct mdrq_table {
     std::vector<cudaEvent_t> ev;  // pairs: [2i] before, [2i+1] after launch i
     size_t ev_used = 0;           // pairs recorded since the last reset
     uint64_t acc_scans = 0, acc_bytes = 0, acc_kernels = 0;
+
+    // host-side fault injection for failure-detection tests (mdrq_inject_fault)
+    uint64_t inject_skip_tiles = 0;  // next scan launch never claims its first tiles
+    int inject_nomem = 0;            // next query call fails its scratch allocation
 };
 
 namespace {
@@ -327,6 +331,12 @@ int launch_scan(mdrq_table *t, const EncodedQuery &q, uint32_t *ids, uint64_t ca
     p.base_in = base_in;
     p.count_out = count_out;
     p.error = t->error;
+    if (t->inject_skip_tiles) {
+        // the first tiles are never claimed: the look-back of the first claimed tile
+        // waits on states nobody sets and gives up after its bound
+        p.ticket_base -= std::min<uint64_t>(t->inject_skip_tiles, n_tiles);
+        t->inject_skip_tiles = 0;
+    }
 
     cudaEvent_t *evp = nullptr;
     if (t->timing) {
@@ -391,6 +401,10 @@ int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, u
     t->last_bytes = 0;
     MDRQ_TRY(cudaSetDevice(t->device));
 
+    if (t->inject_nomem) {
+        t->inject_nomem = 0;
+        return MDRQ_E_NOMEM;
+    }
     int st = grow_device((void **)&t->offsets_dev, &t->offsets_dev_cap, ((size_t)nq + 1) * 8);
     if (st != MDRQ_OK)
         return st;
@@ -667,6 +681,24 @@ int mdrq_scan_timing_read(mdrq_table *t, double *ms, uint64_t *scan_launches, ui
         t->acc_scans = t->acc_bytes = t->acc_kernels = 0;
     }
     return MDRQ_OK;
+}
+
+int mdrq_inject_fault(mdrq_table *t, int kind, uint64_t arg)
+{
+    if (!t)
+        return MDRQ_E_INVAL;
+    switch (kind) {
+    case MDRQ_FAULT_SKIP_TILES:
+        if (arg == 0)
+            return MDRQ_E_INVAL;
+        t->inject_skip_tiles = arg;
+        return MDRQ_OK;
+    case MDRQ_FAULT_NOMEM:
+        t->inject_nomem = 1;
+        return MDRQ_OK;
+    default:
+        return MDRQ_E_INVAL;
+    }
 }
 
 void mdrq_last_scan_stats(const mdrq_table *t, uint64_t *launches, uint64_t *bytes)

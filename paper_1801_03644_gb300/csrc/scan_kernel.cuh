@@ -197,7 +197,10 @@ __device__ __forceinline__ uint32_t tile_lookback(const ScanParams &p, unsigned 
             flag = (uint32_t)(w >> 34) == p.epoch ? (uint32_t)(w >> 32) & 3u : 0u;
             val = (uint32_t)w;
         }
-        if (__any_sync(0xffffffffu, flag == 0)) {
+        uint32_t pmask = __ballot_sync(0xffffffffu, flag == kFlagPrefix);
+        int stop = pmask ? __ffs(pmask) - 1 : 31;  // nearest lane holding a prefix
+        // only the states up to the nearest inclusive prefix are needed
+        if (__any_sync(0xffffffffu, lane <= stop && flag == 0)) {
             if (++polls < kMaxPolls) {
                 __nanosleep(backoff);
                 backoff = backoff < 1024 ? backoff * 2 : 1024;
@@ -210,9 +213,9 @@ __device__ __forceinline__ uint32_t tile_lookback(const ScanParams &p, unsigned 
                 flag = kFlagPrefix;
                 val = 0;
             }
+            pmask = __ballot_sync(0xffffffffu, flag == kFlagPrefix);
+            stop = __ffs(pmask) - 1;
         }
-        const uint32_t pmask = __ballot_sync(0xffffffffu, flag == kFlagPrefix);
-        const int stop = pmask ? __ffs(pmask) - 1 : 31;  // nearest lane holding a prefix
         unsigned long long v = lane <= stop ? val : 0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)

@@ -42,7 +42,10 @@ _lib = None
 
 EXPORTS = ["mdrq_load_columns", "mdrq_query", "mdrq_query_batch", "mdrq_free",
            "mdrq_status_string", "mdrq_table_rows", "mdrq_table_dims", "mdrq_last_scan_stats",
-           "mdrq_scan_timing", "mdrq_scan_timing_read", "mdrq_query_static"]
+           "mdrq_scan_timing", "mdrq_scan_timing_read", "mdrq_query_static",
+           "mdrq_inject_fault"]
+
+FAULT_SKIP_TILES, FAULT_NOMEM = 1, 2
 
 STATIC_MAX_ROWS = 1 << 28  # MDRQ_STATIC_MAX_ROWS
 
@@ -79,6 +82,8 @@ def lib():
         L.mdrq_scan_timing_read.restype = ctypes.c_int
         L.mdrq_scan_timing_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64),
                                             ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.c_int]
+        L.mdrq_inject_fault.restype = ctypes.c_int
+        L.mdrq_inject_fault.argtypes = [vp, ctypes.c_int, u64]
         L.mdrq_query_static.restype = ctypes.c_int
         L.mdrq_query_static.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(i32), u32, u64,
                                         ctypes.POINTER(Pred), u32, vp, u64, ctypes.POINTER(u64), vp]
@@ -295,6 +300,12 @@ class Table:
         if st != OK:
             raise MDRQError(st, "mdrq_query_batch")
         return out[: int(off[-1])], off
+
+    def inject_fault(self, kind: int, arg: int = 0):
+        """Arm a test fault for the next query call (``mdrq_inject_fault``)."""
+        st = lib().mdrq_inject_fault(self._h, int(kind), int(arg))
+        if st != OK:
+            raise MDRQError(st, "mdrq_inject_fault")
 
     def scan_timing(self, enable: bool):
         st = lib().mdrq_scan_timing(self._h, 1 if enable else 0)

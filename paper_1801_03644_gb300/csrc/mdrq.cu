@@ -21,12 +21,6 @@ using namespace mdrq;
 
 namespace mdrq {
 
-// offsets[q+1] = offsets[q] for a query the host proved empty
-__global__ void mdrq_copy_offset_kernel(const unsigned long long *in, unsigned long long *out)
-{
-    *out = *in;
-}
-
 // NaN count, minimum and maximum of a column. out[0] += NaNs; out[1] / out[2] hold the
 // minimum / maximum as order-preserving keys (see key_of).
 __device__ __forceinline__ unsigned long long key_of(uint32_t bits, uint32_t type)
@@ -90,7 +84,7 @@ struct ColumnInfo {
 
 struct EncodedQuery {
     bool empty = false;                 // proven empty on the host
-    std::vector<ScanPred> preds;        // non-trivial predicates, most selective first
+    std::vector<DevPred> preds;         // non-trivial predicates, most selective first
     uint64_t scanned_columns = 0;
 };
 
@@ -103,14 +97,22 @@ struct mdrq_table {
     std::vector<ColumnInfo> cols;
     std::vector<void *> owned;  // device columns this table allocated
 
-    // scratch: [0] ticket, [1] error word, [2..] tile states
+    // scratch: [0] claim counter, [1] error word, [2..] ring of look-back states
     unsigned long long *scratch = nullptr;
     unsigned long long *ticket = nullptr;
     int *error = nullptr;
     unsigned long long *tile_state = nullptr;
-    uint32_t state_words = 0;
+    uint32_t ring_bits = 16;
     unsigned long long ticket_next = 0;
-    uint32_t epoch = 0;
+    uint32_t tag_next = 1;  // tag of the next launch's first ring lap (0: cleared slot)
+
+    // per-batch query tables: device copies and their pinned staging
+    DevQuery *dq_dev = nullptr;
+    size_t dq_dev_cap = 0;
+    DevPred *dp_dev = nullptr;
+    size_t dp_dev_cap = 0;
+    unsigned char *qstage_host = nullptr;  // pinned: DevQuery[] then DevPred[]
+    size_t qstage_host_cap = 0;
 
     unsigned long long *offsets_dev = nullptr;  // nq + 1 entries
     size_t offsets_dev_cap = 0;
@@ -249,7 +251,7 @@ int encode_query(const mdrq_table *t, const mdrq_pred *preds, uint32_t npreds, E
     if (keep.size() > (size_t)kMaxPreds)
         return MDRQ_E_INVAL;
     for (const Cand &cd : keep) {
-        ScanPred sp;
+        DevPred sp;
         sp.col = t->cols[cd.dim].ptr;
         sp.type = (uint32_t)t->cols[cd.dim].type;
         sp.lo = bits[cd.dim].first;
@@ -293,48 +295,52 @@ constexpr uint64_t tile_rows()
     return (uint64_t)kWarps * U * 128;
 }
 
-// Launch the scan of one encoded, non-empty query.
-int launch_scan(mdrq_table *t, const EncodedQuery &q, uint32_t *ids, uint64_t capacity,
-                const unsigned long long *base_in, unsigned long long *count_out, cudaStream_t s)
+// Launch one scan over the queries qs[0 .. nq) (all non-empty), whose predicates are
+// already in t->dp_dev and descriptors in t->dq_dev at offset q0.
+int launch_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t scanned_columns, uint32_t *ids,
+                uint64_t capacity, const unsigned long long *base_in, cudaStream_t s)
 {
-    // smallest tiles on small tables so that every SM gets work; 4096-row tiles otherwise
+    // 4096-row tiles unless the launch would leave SMs without work
     const uint64_t resident4 = (uint64_t)t->sm_count * t->blocks_per_sm[2];
+    auto tiles_of = [&](uint64_t rows) { return (t->n + rows - 1) / rows; };
     int ui = 2;
-    if ((t->n + tile_rows<4>() - 1) / tile_rows<4>() < 2 * resident4)
-        ui = ((t->n + tile_rows<2>() - 1) / tile_rows<2>() < 2 * resident4) ? 0 : 1;
+    if (tiles_of(tile_rows<4>()) * nq < 2 * resident4)
+        ui = tiles_of(tile_rows<2>()) * nq < 2 * resident4 ? 0 : 1;
     const uint64_t rows = ui == 2 ? tile_rows<4>() : ui == 1 ? tile_rows<2>() : tile_rows<1>();
-    const uint64_t n_tiles = (t->n + rows - 1) / rows;
-    if (n_tiles > t->state_words)
-        return MDRQ_E_CUDA;  // cannot happen: states are sized for the smallest tile
+    const uint64_t tiles_per_query = tiles_of(rows);
+    const uint64_t total_tiles = tiles_per_query * nq;
     const uint64_t resident = (uint64_t)t->sm_count * t->blocks_per_sm[ui];
-    const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(resident, n_tiles));
+    const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(resident, total_tiles));
 
-    if (t->epoch >= kEpochLimit) {
-        MDRQ_TRY(cudaMemsetAsync(t->tile_state, 0, (size_t)t->state_words * 8, s));
-        t->epoch = 0;
+    // tags: one per lap of the ring; restart from a cleared ring before they wrap
+    const uint32_t laps = (uint32_t)(total_tiles >> t->ring_bits) + 1;
+    if ((uint64_t)t->tag_next + laps > kTagLimit) {
+        MDRQ_TRY(cudaMemsetAsync(t->tile_state, 0, ((size_t)1 << t->ring_bits) * 8, s));
+        t->tag_next = 1;
     }
-    ++t->epoch;
 
     ScanParams p;
     std::memset(&p, 0, sizeof(p));
-    for (size_t i = 0; i < q.preds.size(); ++i)
-        p.pred[i] = q.preds[i];
-    p.npred = (uint32_t)q.preds.size();
-    p.n_tiles = (uint32_t)n_tiles;
+    p.queries = t->dq_dev + q0;
+    p.preds = t->dp_dev;
+    p.nq = nq;
+    p.tiles_per_query = (uint32_t)tiles_per_query;
     p.n = t->n;
+    p.total_tiles = total_tiles;
     p.tile_state = t->tile_state;
+    p.ring_bits = t->ring_bits;
+    p.tag0 = t->tag_next;
     p.ticket = t->ticket;
     p.ticket_base = t->ticket_next;
-    p.epoch = t->epoch;
     p.ids = ids;
     p.capacity = capacity;
     p.base_in = base_in;
-    p.count_out = count_out;
+    p.offsets = t->offsets_dev;
     p.error = t->error;
     if (t->inject_skip_tiles) {
         // the first tiles are never claimed: the look-back of the first claimed tile
         // waits on states nobody sets and gives up after its bound
-        p.ticket_base -= std::min<uint64_t>(t->inject_skip_tiles, n_tiles);
+        p.ticket_base -= std::min<uint64_t>(t->inject_skip_tiles, total_tiles);
         t->inject_skip_tiles = 0;
     }
 
@@ -360,27 +366,28 @@ int launch_scan(mdrq_table *t, const EncodedQuery &q, uint32_t *ids, uint64_t ca
     MDRQ_TRY(cudaGetLastError());
     if (evp)
         MDRQ_TRY(cudaEventRecord(evp[1], s));
-    t->ticket_next += n_tiles + grid;  // every CTA makes one claim past the last tile
+    t->ticket_next += total_tiles + (uint64_t)kFailingClaimsPerCta * grid;
+    t->tag_next += laps;
     t->last_launches += 1;
-    t->last_bytes += q.scanned_columns * 4ull * t->n;
+    t->last_bytes += scanned_columns * 4ull * t->n;
     if (t->timing) {
         t->acc_scans += 1;
         t->acc_kernels += 1;
-        t->acc_bytes += q.scanned_columns * 4ull * t->n;
+        t->acc_bytes += scanned_columns * 4ull * t->n;
     }
     return MDRQ_OK;
 }
 
-// After an error the claim counter and tile states may be inconsistent: reset them.
+// After an error the claim counter and ring may be inconsistent: reset them.
 void reset_scratch(mdrq_table *t, cudaStream_t s)
 {
     cudaStreamSynchronize(s);
     (void)cudaGetLastError();
-    cudaMemset(t->scratch, 0, (size_t)(2 + t->state_words) * 8);
+    cudaMemset(t->scratch, 0, (size_t)(2 + ((size_t)1 << t->ring_bits)) * 8);
     cudaDeviceSynchronize();
     (void)cudaGetLastError();
     t->ticket_next = 0;
-    t->epoch = 0;
+    t->tag_next = 1;
 }
 
 int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, uint64_t capacity,
@@ -391,24 +398,39 @@ int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, u
     for (uint32_t q = 0; q < nq; ++q)
         if (qs[q].reserved != 0)
             return MDRQ_E_INVAL;
+    // a2: encode every query first, so that a bad argument launches nothing
     std::vector<EncodedQuery> enc(nq);
+    std::vector<uint32_t> live;  // queries that need a scan, in order
+    size_t npreds = 0;
     for (uint32_t q = 0; q < nq; ++q) {
         int st = encode_query(t, qs[q].preds, qs[q].npreds, enc[q]);
         if (st != MDRQ_OK)
             return st;
+        if (t->n > 0 && !enc[q].empty) {
+            live.push_back(q);
+            npreds += enc[q].preds.size();
+        }
     }
     t->last_launches = 0;
     t->last_bytes = 0;
     MDRQ_TRY(cudaSetDevice(t->device));
-
     if (t->inject_nomem) {
         t->inject_nomem = 0;
         return MDRQ_E_NOMEM;
     }
+
+    const size_t nlive = live.size();
+    const size_t dq_bytes = std::max<size_t>(1, nlive) * sizeof(DevQuery);
+    const size_t dp_bytes = std::max<size_t>(1, npreds) * sizeof(DevPred);
     int st = grow_device((void **)&t->offsets_dev, &t->offsets_dev_cap, ((size_t)nq + 1) * 8);
-    if (st != MDRQ_OK)
-        return st;
-    st = grow_pinned((void **)&t->offsets_host, &t->offsets_host_cap, ((size_t)nq + 1) * 8);
+    if (st == MDRQ_OK)
+        st = grow_pinned((void **)&t->offsets_host, &t->offsets_host_cap, ((size_t)nq + 1) * 8);
+    if (st == MDRQ_OK)
+        st = grow_device((void **)&t->dq_dev, &t->dq_dev_cap, dq_bytes);
+    if (st == MDRQ_OK)
+        st = grow_device((void **)&t->dp_dev, &t->dp_dev_cap, dp_bytes);
+    if (st == MDRQ_OK)
+        st = grow_pinned((void **)&t->qstage_host, &t->qstage_host_cap, dq_bytes + dp_bytes);
     if (st != MDRQ_OK)
         return st;
     uint32_t *out = ids;
@@ -418,18 +440,37 @@ int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, u
             return st;
         out = t->ids_stage;
     }
+
+    // the query tables go to the device in one copy (pinned staging)
+    DevQuery *hq = reinterpret_cast<DevQuery *>(t->qstage_host);
+    DevPred *hp = reinterpret_cast<DevPred *>(t->qstage_host + dq_bytes);
+    uint64_t first = 0;
+    for (size_t i = 0; i < nlive; ++i) {
+        const EncodedQuery &e = enc[live[i]];
+        hq[i].first = (uint32_t)first;
+        hq[i].npred = (uint32_t)e.preds.size();
+        hq[i].orig = live[i];
+        hq[i].pad = 0;
+        for (const DevPred &dp : e.preds)
+            hp[first++] = dp;
+    }
+    // the offsets array and the query tables are written by this call only after the
+    // previous call's kernels (same stream) have finished reading them
+    MDRQ_TRY(cudaMemcpyAsync(t->dq_dev, hq, dq_bytes, cudaMemcpyHostToDevice, s));
+    if (npreds)
+        MDRQ_TRY(cudaMemcpyAsync(t->dp_dev, hp, npreds * sizeof(DevPred), cudaMemcpyHostToDevice, s));
     MDRQ_TRY(cudaMemsetAsync(t->offsets_dev, 0, ((size_t)nq + 1) * 8, s));
     MDRQ_TRY(cudaMemsetAsync(t->error, 0, sizeof(int), s));
 
-    for (uint32_t q = 0; q < nq; ++q) {
-        if (t->n == 0 || enc[q].empty) {
-            mdrq_copy_offset_kernel<<<1, 1, 0, s>>>(t->offsets_dev + q, t->offsets_dev + q + 1);
-            MDRQ_TRY(cudaGetLastError());
-            if (t->timing)
-                t->acc_kernels += 1;
-            continue;
-        }
-        st = launch_scan(t, enc[q], out, capacity, t->offsets_dev + q, t->offsets_dev + q + 1, s);
+    // one launch per chunk of queries whose ids fit the 40-bit state values
+    const uint64_t per_launch = std::max<uint64_t>(1, kValueMask / std::max<uint64_t>(1, t->n));
+    for (size_t c0 = 0; c0 < nlive; c0 += per_launch) {
+        const uint32_t cnt = (uint32_t)std::min<uint64_t>(per_launch, nlive - c0);
+        uint64_t cols = 0;
+        for (size_t i = c0; i < c0 + cnt; ++i)
+            cols += enc[live[i]].scanned_columns;
+        const unsigned long long *base = c0 == 0 ? nullptr : t->offsets_dev + live[c0 - 1] + 1;
+        st = launch_scan(t, (uint32_t)c0, cnt, cols, out, capacity, base, s);
         if (st != MDRQ_OK) {
             reset_scratch(t, s);
             return st;
@@ -447,7 +488,16 @@ int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, u
         reset_scratch(t, s);
         return MDRQ_E_TIMEOUT;
     }
+    // a query answered on the host (empty) ends where the previous one ends
     std::memcpy(offsets, t->offsets_host, ((size_t)nq + 1) * 8);
+    offsets[0] = 0;
+    size_t li = 0;
+    for (uint32_t q = 0; q < nq; ++q) {
+        if (li < nlive && live[li] == q)
+            ++li;
+        else
+            offsets[q + 1] = offsets[q];
+    }
     const uint64_t total = offsets[nq];
     // 4 bytes per id written
     t->last_bytes += 4ull * std::min<uint64_t>(total, capacity);
@@ -472,6 +522,9 @@ void destroy(mdrq_table *t)
     cudaFree(t->scratch);
     cudaFree(t->offsets_dev);
     cudaFree(t->ids_stage);
+    cudaFree(t->dq_dev);
+    cudaFree(t->dp_dev);
+    cudaFreeHost(t->qstage_host);
     cudaFreeHost(t->offsets_host);
     cudaFreeHost(t->error_host);
     for (cudaEvent_t e : t->ev)
@@ -509,14 +562,14 @@ int load(const void *const *cols, const int32_t *types, uint32_t d, uint64_t n, 
         }
     }
 
-    // scratch sized for the smallest tile (1024 rows)
-    const uint64_t max_tiles = (n + tile_rows<1>() - 1) / tile_rows<1>();
-    t->state_words = (uint32_t)std::max<uint64_t>(1, max_tiles);
-    MDRQ_TRY(cudaMalloc(&t->scratch, (size_t)(2 + t->state_words) * 8));
+    // scratch: claim counter, error word and a ring of 2^16 look-back states (512 KiB)
+    t->ring_bits = 16;
+    const size_t scratch_words = 2 + ((size_t)1 << t->ring_bits);
+    MDRQ_TRY(cudaMalloc(&t->scratch, scratch_words * 8));
     t->ticket = t->scratch;
     t->error = reinterpret_cast<int *>(t->scratch + 1);
     t->tile_state = t->scratch + 2;
-    MDRQ_TRY(cudaMemsetAsync(t->scratch, 0, (size_t)(2 + t->state_words) * 8, s));
+    MDRQ_TRY(cudaMemsetAsync(t->scratch, 0, scratch_words * 8, s));
     MDRQ_TRY(cudaMallocHost((void **)&t->error_host, sizeof(int)));
 
     if (n == 0)

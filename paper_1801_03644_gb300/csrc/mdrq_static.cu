@@ -38,17 +38,23 @@ constexpr uint64_t kTileRows = (uint64_t)kWarps * 4 * 128;  // 4096: the U = 4 t
 constexpr uint64_t kMaxTiles = MDRQ_STATIC_MAX_ROWS / kTileRows;
 static_assert(kMaxTiles * kTileRows == MDRQ_STATIC_MAX_ROWS, "limit is a whole number of tiles");
 
-// word layout: [0] claim counter, [1] error word, [2] answer length, [3] unused,
-// [4 .. 4 + kMaxTiles) look-back states
+// word layout: [0] claim counter, [1] error word, [2] answer start (0), [3] answer
+// length, then the look-back states (one per tile, used as a ring that never wraps
+// here), the query descriptor and its predicates
+constexpr uint32_t kRingBits = 16;
+static_assert((1ull << kRingBits) == kMaxTiles, "one state per tile of the largest table");
 constexpr uint64_t kHeadWords = 4;
-constexpr uint64_t kScratchWords = kHeadWords + kMaxTiles;
+constexpr uint64_t kQueryWord = kHeadWords + kMaxTiles;
+constexpr uint64_t kPredWord = kQueryWord + sizeof(DevQuery) / 8;
+constexpr uint64_t kScratchWords = kPredWord + (uint64_t)kMaxPreds * sizeof(DevPred) / 8;
+static_assert(sizeof(DevQuery) % 8 == 0 && sizeof(DevPred) % 8 == 0, "word-aligned tables");
 
 constexpr int kMaxDevices = 64;
 
 }  // namespace
 
-// The fixed scratch: (4 + 65536) * 8 bytes = 512 KiB + 32 B per device that loads the
-// library, held until the process exits.
+// The fixed scratch: (4 + 65536 + 2 + 384) * 8 bytes = 515.1 KiB per device that loads
+// the library, held until the process exits.
 static __device__ __align__(256) unsigned long long g_scan_scratch[kScratchWords];
 
 __global__ void __launch_bounds__(kScanThreads, 7) mdrq_scan_static_kernel(const __grid_constant__ ScanParams p)
@@ -131,8 +137,7 @@ extern "C" int mdrq_query_static(const void *const *cols, const int32_t *types, 
 
     // Sec. 2.1: AND of closed intervals; a repeated dimension intersects its intervals.
     // Fixed storage: at most kMaxPreds distinct dimensions.
-    ScanParams p;
-    std::memset(&p, 0, sizeof(p));
+    DevPred pred[kMaxPreds];
     double lo_v[kMaxPreds], hi_v[kMaxPreds];
     uint32_t dim_of[kMaxPreds];
     uint32_t k = 0;
@@ -157,19 +162,20 @@ extern "C" int mdrq_query_static(const void *const *cols, const int32_t *types, 
             dim_of[k] = q.dim;
             lo_v[k] = lo;
             hi_v[k] = hi;
-            p.pred[k].col = n > 0 ? cols[q.dim] : nullptr;
-            p.pred[k].type = (uint32_t)types[q.dim];
-            p.pred[k].lo = lb;
-            p.pred[k].hi = hb;
+            pred[k].col = n > 0 ? cols[q.dim] : nullptr;
+            pred[k].type = (uint32_t)types[q.dim];
+            pred[k].lo = lb;
+            pred[k].hi = hb;
+            pred[k].pad = 0;
             ++k;
         } else {
             if (lo > lo_v[slot]) {
                 lo_v[slot] = lo;
-                p.pred[slot].lo = lb;
+                pred[slot].lo = lb;
             }
             if (hi < hi_v[slot]) {
                 hi_v[slot] = hi;
-                p.pred[slot].hi = hb;
+                pred[slot].hi = hb;
             }
         }
     }
@@ -194,33 +200,50 @@ extern "C" int mdrq_query_static(const void *const *cols, const int32_t *types, 
     const uint32_t grid = (uint32_t)(resident < n_tiles ? resident : n_tiles);
     unsigned long long *scratch = ds->scratch;
 
-    // clear the header and the states this launch uses (the array keeps old contents)
+    // clear the header and the states this launch uses (the array keeps old contents),
+    // then copy the query in (from host stack memory: no staging buffer is allocated)
+    DevQuery qd;
+    qd.first = 0;
+    qd.npred = k;
+    qd.orig = 0;
+    qd.pad = 0;
     if ((st = status_of(cudaMemsetAsync(scratch, 0, (size_t)(kHeadWords + n_tiles) * 8, s))))
         return st;
+    if ((st = status_of(cudaMemcpyAsync(scratch + kQueryWord, &qd, sizeof(qd), cudaMemcpyHostToDevice, s))))
+        return st;
+    if (k > 0 && (st = status_of(cudaMemcpyAsync(scratch + kPredWord, pred, k * sizeof(DevPred),
+                                                 cudaMemcpyHostToDevice, s))))
+        return st;
 
-    p.npred = k;
-    p.n_tiles = (uint32_t)n_tiles;
+    ScanParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.queries = reinterpret_cast<const DevQuery *>(scratch + kQueryWord);
+    p.preds = reinterpret_cast<const DevPred *>(scratch + kPredWord);
+    p.nq = 1;
+    p.tiles_per_query = (uint32_t)n_tiles;
     p.n = n;
+    p.total_tiles = n_tiles;
     p.tile_state = scratch + kHeadWords;
+    p.ring_bits = kRingBits;
+    p.tag0 = 1;  // cleared states carry tag 0
     p.ticket = scratch;
     p.ticket_base = 0;
-    p.epoch = 1;
     p.ids = ids;
     p.capacity = capacity;
     p.base_in = nullptr;
-    p.count_out = scratch + 2;
+    p.offsets = scratch + 2;  // offsets[1], the answer length, lands in word 3
     p.error = reinterpret_cast<int *>(scratch + 1);
     mdrq_scan_static_kernel<<<grid, kScanThreads, 0, s>>>(p);
     if ((st = status_of(cudaGetLastError())))
         return st;
 
-    unsigned long long head[3] = {0, 0, 0};  // claim counter, error word, answer length
+    unsigned long long head[4] = {0, 0, 0, 0};  // claim counter, error word, 0, answer length
     if ((st = status_of(cudaMemcpyAsync(head, scratch, sizeof(head), cudaMemcpyDeviceToHost, s))))
         return st;
     if ((st = status_of(cudaStreamSynchronize(s))))
         return st;
     if ((int)head[1] != 0)
         return MDRQ_E_TIMEOUT;
-    *count = head[2];
-    return head[2] > capacity ? MDRQ_E_CAPACITY : MDRQ_OK;
+    *count = head[3];
+    return head[3] > capacity ? MDRQ_E_CAPACITY : MDRQ_OK;
 }

@@ -1,4 +1,5 @@
-// Fused filter + ordered compaction scan for one multidimensional range query.
+// Fused filter + ordered compaction scan: a batch of multidimensional range queries
+// over one column-wise table, in a single persistent launch.
 //
 // Method (arXiv 1801.03644): an object qualifies iff lo_j <= x_j <= hi_j on every
 // constrained dimension (Sec. 2.1); the scan visits every object (Sec. 2.2.4), over a
@@ -8,21 +9,29 @@
 // partial results of its partitions (Sec. 3.1).
 //
 // GB300 design:
-//  * A persistent grid claims row tiles in increasing order from a global ticket.
-//    Each warp owns U*128 consecutive rows of a tile; lane l reads rows
-//    4l..4l+3 of every 128-row group with one 128-bit load per column
-//    (512 contiguous bytes per warp instruction).
+//  * Work unit: a row tile of one query. The tiles of all queries of a launch form one
+//    sequence (query-major); a persistent grid claims them in increasing order from a
+//    global ticket. Each query is still scanned on its own (no column load is shared
+//    between queries): one launch merely removes the per-query launch ramp and tail.
+//  * Each filter warp owns U*128 consecutive rows of a tile; lane l reads rows
+//    4l..4l+3 of every 128-row group with one 128-bit load per column (512 contiguous
+//    bytes per warp instruction).
 //  * The per-row mask of U*4 bits lives in a register. Predicates are applied one
 //    column at a time; a lane whose rows have all failed issues no load for the
-//    remaining columns, so the memory system never fetches a 32-byte sector whose
-//    8 rows are already rejected (the early break of Sec. 2.2.4 at sector
-//    granularity), and a warp whose rows have all failed stops reading columns.
-//  * Matches are ranked with a packed warp scan and staged in shared memory in row
-//    order; the tile's offset in the answer comes from a single-pass decoupled
-//    look-back over per-tile states (aggregate / inclusive prefix), so the answer is
-//    written once, coalesced and ascending, without a second pass over the columns.
-//  * The look-back and the write-out run in a separate output warp that drains
-//    double-buffered stages, so the eight filter warps never stall on other tiles.
+//    remaining columns, so the memory system never fetches a 32-byte sector whose 8
+//    rows are already rejected (the early break of Sec. 2.2.4 at sector granularity),
+//    and a warp whose rows have all failed stops reading columns.
+//  * Matches are ranked with a packed warp scan and staged (16-bit row offsets) in
+//    shared memory, each warp in its own segment. The offset of a tile in the launch's
+//    output comes from a single-pass decoupled look-back over per-tile states
+//    (aggregate / inclusive prefix) kept in a ring; because the sequence runs over all
+//    queries, the inclusive prefix at a query's last tile is that query's end offset in
+//    the CSR answer, so the whole batch is written once, coalesced, ascending per query.
+//  * Warp roles: eight filter warps per CTA claim tiles (one tile ahead), evaluate them
+//    into kStages shared stages and publish each tile's aggregate (the last warp to
+//    finish does it); one output warp drains the stages in order, resolves each tile's
+//    offset by look-back and writes the ids. The filter warps never wait on another
+//    tile or on each other.
 //  * Every wait (on another tile's state or on a stage) is bounded; on expiry the
 //    kernel records an error bit and finishes, never traps.
 #pragma once
@@ -32,22 +41,25 @@
 
 namespace mdrq {
 
-constexpr int kBlock = 256;
+constexpr int kBlock = 256;     // filter threads per CTA
 constexpr int kWarps = kBlock / 32;
-constexpr int kMaxPreds = 128;
+constexpr int kMaxPreds = 128;  // distinct constrained dimensions per query
 
 constexpr uint32_t kTypeF32 = 0;
 constexpr uint32_t kTypeI32 = 1;
 
-// tile state word: [63:34] epoch, [33:32] flag, [31:0] value
+// tile state word: [63:62] flag, [61:40] tag, [39:0] value (ids, relative to the launch)
 constexpr uint32_t kFlagAggregate = 1;
 constexpr uint32_t kFlagPrefix = 2;
-constexpr uint32_t kEpochLimit = (1u << 30) - 1;
+constexpr uint32_t kTagLimit = (1u << 22) - 1;
+constexpr unsigned long long kValueMask = (1ull << 40) - 1;  // a launch outputs < 2^40 ids
 
 constexpr int kErrLookbackTimeout = 1;
+constexpr int kErrStageTimeout = 2;
 constexpr uint32_t kMaxPolls = 1u << 20;  // x <= 1 us backoff: bounded by about 1 s
 
-struct ScanPred {
+// One predicate of one query, as the kernel reads it.
+struct DevPred {
     const void *col;  // device column (16-byte aligned)
     uint32_t type;    // kTypeF32 / kTypeI32
     uint32_t lo;      // bound bits, read as the column's type
@@ -55,20 +67,30 @@ struct ScanPred {
     uint32_t pad;
 };
 
-struct ScanParams {
-    ScanPred pred[kMaxPreds];
+// One query of a launch: predicates preds[first .. first + npred), answer slot `orig`.
+struct DevQuery {
+    uint32_t first;
     uint32_t npred;
-    uint32_t n_tiles;
-    uint64_t n;
-    unsigned long long *tile_state;  // n_tiles words
+    uint32_t orig;
+    uint32_t pad;
+};
+
+struct ScanParams {
+    const DevQuery *queries;         // nq queries (device)
+    const DevPred *preds;            // their predicates (device)
+    uint32_t nq;
+    uint32_t tiles_per_query;        // row tiles of the table
+    uint64_t n;                      // rows
+    uint64_t total_tiles;            // nq * tiles_per_query
+    unsigned long long *tile_state;  // ring of look-back states
+    uint32_t ring_bits;              // ring size = 2^ring_bits
+    uint32_t tag0;                   // tag of this launch's first ring lap
     unsigned long long *ticket;      // monotone claim counter
     unsigned long long ticket_base;  // counter value when this launch starts
-    uint32_t epoch;                  // tag of this launch in tile_state
-    uint32_t pad0;
-    uint32_t *ids;                   // answer buffer
+    uint32_t *ids;                   // answer buffer (CSR over the queries)
     uint64_t capacity;               // slots in ids
-    const unsigned long long *base_in;  // offset of this answer in ids (NULL: 0)
-    unsigned long long *count_out;   // receives base + answer length
+    const unsigned long long *base_in;  // where this launch's output starts in ids
+    unsigned long long *offsets;     // offsets[orig + 1] <- end of query orig's answer
     int *error;                      // error bits (kErr*)
 };
 
@@ -100,9 +122,20 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned l
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__device__ __forceinline__ unsigned long long pack_state(uint32_t epoch, uint32_t flag, uint32_t v)
+// ring slot and tag of tile t of the launch
+__device__ __forceinline__ unsigned long long *state_slot(const ScanParams &p, unsigned long long t)
 {
-    return ((unsigned long long)epoch << 34) | ((unsigned long long)flag << 32) | v;
+    return p.tile_state + (t & ((1ull << p.ring_bits) - 1));
+}
+
+__device__ __forceinline__ uint32_t state_tag(const ScanParams &p, unsigned long long t)
+{
+    return (p.tag0 + (uint32_t)(t >> p.ring_bits)) & kTagLimit;
+}
+
+__device__ __forceinline__ unsigned long long pack_state(uint32_t tag, uint32_t flag, unsigned long long v)
+{
+    return ((unsigned long long)flag << 62) | ((unsigned long long)tag << 40) | (v & kValueMask);
 }
 
 // 4-bit mask of the rows of one 16-byte chunk that lie in [lo, hi]
@@ -175,27 +208,23 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t pari
     return true;
 }
 
-__device__ __forceinline__ void named_bar_sync(uint32_t id, uint32_t count)
+// Exclusive prefix of all tiles before tile `t` of the launch (decoupled look-back),
+// run by one full warp once t's aggregate is published; publishes t's inclusive prefix.
+__device__ __forceinline__ unsigned long long tile_lookback(const ScanParams &p, unsigned long long t,
+                                                            uint32_t total, int lane)
 {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
-
-// Exclusive prefix of all tiles before `tile` (decoupled look-back), run by one full
-// warp once the tile's own aggregate is published; publishes the inclusive prefix.
-__device__ __forceinline__ uint32_t tile_lookback(const ScanParams &p, unsigned long long tile,
-                                                  uint32_t total, int lane)
-{
-    unsigned long long *st = p.tile_state;
     unsigned long long excl = 0;
-    long long idx = (long long)tile - 1;  // nearest predecessor
+    long long idx = (long long)t - 1;  // nearest predecessor
     uint32_t polls = 0, backoff = 32;
     for (;;) {
         const long long my = idx - lane;
-        uint32_t flag = kFlagPrefix, val = 0;  // before tile 0: an inclusive prefix of 0
+        uint32_t flag = kFlagPrefix;  // before tile 0: an inclusive prefix of 0
+        unsigned long long val = 0;
         if (my >= 0) {
-            const unsigned long long w = ld_relaxed_u64(&st[my]);
-            flag = (uint32_t)(w >> 34) == p.epoch ? (uint32_t)(w >> 32) & 3u : 0u;
-            val = (uint32_t)w;
+            const unsigned long long w = ld_relaxed_u64(state_slot(p, (unsigned long long)my));
+            const bool mine = (uint32_t)((w >> 40) & kTagLimit) == state_tag(p, (unsigned long long)my);
+            flag = mine ? (uint32_t)(w >> 62) : 0u;
+            val = w & kValueMask;
         }
         uint32_t pmask = __ballot_sync(0xffffffffu, flag == kFlagPrefix);
         int stop = pmask ? __ffs(pmask) - 1 : 31;  // nearest lane holding a prefix
@@ -226,22 +255,25 @@ __device__ __forceinline__ uint32_t tile_lookback(const ScanParams &p, unsigned 
         idx -= 32;
     }
     if (lane == 0)
-        st_relaxed_u64(&st[tile], pack_state(p.epoch, kFlagPrefix, (uint32_t)(excl + total)));
-    return (uint32_t)excl;
+        st_relaxed_u64(state_slot(p, t), pack_state(state_tag(p, t), kFlagPrefix, excl + total));
+    return excl;
 }
 
-constexpr int kStages = 2;                       // staged tiles per CTA
+constexpr int kStages = 3;                       // staged tiles per CTA
+constexpr int kClaimSlots = kStages + 1;         // claimed-tile queue (see scan_cta)
 constexpr int kScanThreads = kBlock + 32;        // 8 filter warps + 1 output warp
-constexpr unsigned long long kStopTile = ~0ull;  // "no more tiles" marker for the output warp
-constexpr uint32_t kBarFilter = 1;               // named barrier of the 8 filter warps
+constexpr unsigned long long kStopTile = ~0ull;  // "no more tiles" marker
 
-// Warp-specialised scan. Warps 0-7 ("filter warps") claim tiles, evaluate the
-// predicates, rank the matches and stage their row offsets in one of kStages shared
-// buffers, publish the tile's aggregate, and move on. Warp 8 (the "output warp")
-// takes staged tiles in order, resolves each tile's offset by look-back, publishes the
-// inclusive prefix and writes the ids out, so no filter warp ever waits on another
-// tile. Hand-off uses mbarriers: full[b] (256 filter-thread arrivals) and empty[b]
-// (32 output-lane arrivals); every wait is bounded.
+// Claims every CTA makes past the last tile: the host advances its ticket base by
+// total_tiles + kFailingClaimsPerCta * grid per launch.
+constexpr int kFailingClaimsPerCta = 1;
+
+// The filter warps of a CTA run iterations 0, 1, 2, ... in lock-free step: iteration i
+// fills stage i % kStages with the tile held in claim slot i % kClaimSlots. The first
+// filter warp to start iteration i claims the tile of iteration i + 1, so a tile is
+// claimed about one tile before it is processed and tiles are finished close to claim
+// order, which keeps look-back waits short. Slot reuse is safe with kStages + 1 slots:
+// a warp can run at most kStages iterations ahead of the output warp.
 template <int U>
 __device__ __forceinline__ void scan_cta(const ScanParams &p)
 {
@@ -251,24 +283,34 @@ __device__ __forceinline__ void scan_cta(const ScanParams &p)
     constexpr uint32_t kFullMask = (1u << (U * 4)) - 1u;
     static_assert(kTileRows <= 65536, "row offsets are staged as 16-bit values");
 
-    __shared__ uint16_t s_stage[kStages][kTileRows];
+    __shared__ uint16_t s_stage[kStages][kTileRows];  // warp w: [w*kWarpRows, ...)
     __shared__ uint32_t s_warp_total[kStages][kWarps];
-    __shared__ unsigned long long s_tile[kStages];
-    __shared__ uint32_t s_total[kStages];
-    __shared__ unsigned long long s_ticket[2];
-    __shared__ unsigned long long s_full[kStages], s_empty[kStages];
-    __shared__ int s_abort;
+    __shared__ unsigned long long s_stage_tile[kStages];  // tile held by the stage
+    __shared__ uint32_t s_done[kStages];                  // filter warps finished with it
+    __shared__ uint32_t s_first[kStages];                 // filter warps that started it
+    __shared__ unsigned long long s_claim[kClaimSlots];   // claimed tile of an iteration
+    __shared__ unsigned long long s_ready[kStages], s_full[kStages], s_claimed[kClaimSlots];
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
 
+    auto claim = [&]() -> unsigned long long {
+        const unsigned long long t = atomicAdd(p.ticket, 1ull) - p.ticket_base;
+        return t < p.total_tiles ? t : kStopTile;
+    };
+
     if (threadIdx.x == 0) {
         for (int b = 0; b < kStages; ++b) {
-            mbar_init(&s_full[b], kBlock);
-            mbar_init(&s_empty[b], 32);
+            mbar_init(&s_ready[b], 1);
+            mbar_init(&s_full[b], kWarps);
+            s_done[b] = 0;
+            s_first[b] = 0;
         }
-        s_abort = 0;
+        for (int c = 0; c < kClaimSlots; ++c)
+            mbar_init(&s_claimed[c], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_claim[0] = claim();  // the tile of iteration 0
+        mbar_arrive(&s_claimed[0]);
     }
     __syncthreads();
 
@@ -278,168 +320,174 @@ __device__ __forceinline__ void scan_cta(const ScanParams &p)
         uint32_t full_phase = 0;  // bit b: parity to wait for on s_full[b]
         for (uint32_t it = 0;; ++it) {
             const int b = it % kStages;
-            // every lane waits; the warp leaves together if any lane gave up
             if (!__all_sync(0xffffffffu, mbar_wait(&s_full[b], (full_phase >> b) & 1u))) {
                 if (lane == 0)
-                    atomicOr(p.error, kErrLookbackTimeout);
+                    atomicOr(p.error, kErrStageTimeout);
                 break;
             }
             full_phase ^= 1u << b;
-            const unsigned long long tile = s_tile[b];
-            if (tile == kStopTile)
+            const unsigned long long t = s_stage_tile[b];
+            if (t == kStopTile)
                 break;
-            const uint32_t total = s_total[b];
-            const uint32_t prefix = tile == 0 ? 0u : tile_lookback(p, tile, total, lane);
-            if (lane == 0 && tile == p.n_tiles - 1)
-                *p.count_out = base + prefix + total;
-            const unsigned long long out0 = base + prefix;
-            const uint32_t row0 = (uint32_t)(tile * (unsigned long long)kTileRows);
-            for (uint32_t r = lane; r < total; r += 32) {
-                const unsigned long long pos = out0 + r;
-                if (pos < p.capacity)
-                    p.ids[pos] = row0 + s_stage[b][r];
+            // per-warp counts of the stage and their inclusive prefix
+            const uint32_t wt = lane < kWarps ? s_warp_total[b][lane] : 0u;
+            uint32_t wincl = wt;
+#pragma unroll
+            for (int o = 1; o < kWarps; o <<= 1) {
+                const uint32_t x = __shfl_up_sync(0xffffffffu, wincl, o);
+                if (lane >= o)
+                    wincl += x;
+            }
+            const uint32_t total = __shfl_sync(0xffffffffu, wincl, kWarps - 1);
+            const unsigned long long excl = t == 0 ? 0ull : tile_lookback(p, t, total, lane);
+            const uint32_t q = (uint32_t)(t / p.tiles_per_query);
+            const unsigned long long rt = t - (unsigned long long)q * p.tiles_per_query;
+            if (lane == 0 && rt == p.tiles_per_query - 1)
+                p.offsets[p.queries[q].orig + 1] = base + excl + total;
+            const uint32_t row0 = (uint32_t)(rt * (unsigned long long)kTileRows);
+#pragma unroll 1
+            for (int w = 0; w < kWarps; ++w) {
+                const uint32_t cnt = __shfl_sync(0xffffffffu, wt, w);
+                const unsigned long long out0 = base + excl + __shfl_sync(0xffffffffu, wincl - wt, w);
+                const uint16_t *seg = &s_stage[b][w * kWarpRows];
+                for (uint32_t r = lane; r < cnt; r += 32) {
+                    const unsigned long long pos = out0 + r;
+                    if (pos < p.capacity)
+                        p.ids[pos] = row0 + seg[r];
+                }
             }
             __syncwarp();
-            mbar_arrive(&s_empty[b]);
+            if (lane == 0)
+                mbar_arrive(&s_ready[b]);
         }
         return;
     }
 
     // ---------------------------------------------------------------- filter warps
-    uint32_t empty_phase = (1u << kStages) - 1u;  // bit b: parity for s_empty[b]; buffers start empty
-    if (threadIdx.x == 0)
-        s_ticket[0] = atomicAdd(p.ticket, 1ull) - p.ticket_base;
-    named_bar_sync(kBarFilter, kBlock);
-    unsigned long long tile = s_ticket[0];
-    int slot = 0;
-    uint32_t it = 0;
-
-    while (tile < p.n_tiles) {
+    uint32_t ready_phase = (1u << kStages) - 1u;  // bit b: parity for s_ready[b]; stages start free
+    for (uint32_t it = 0;; ++it) {
         const int b = it % kStages;
-        if (threadIdx.x == 0) {
-            if (!mbar_wait(&s_empty[b], (empty_phase >> b) & 1u)) {
-                atomicOr(p.error, kErrLookbackTimeout);
-                s_abort = 1;
-            }
-            // claim the next tile now so the round trip overlaps this tile's loads
-            s_ticket[slot ^ 1] = atomicAdd(p.ticket, 1ull) - p.ticket_base;
-        }
-        named_bar_sync(kBarFilter, kBlock);
-        if (s_abort)
+        const int c = it % kClaimSlots;
+        const bool ok = mbar_wait(&s_ready[b], (ready_phase >> b) & 1u) &&
+                        mbar_wait(&s_claimed[c], (it / kClaimSlots) & 1u);
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0)
+                atomicOr(p.error, kErrStageTimeout);
             break;
-        empty_phase ^= 1u << b;
-
-        const uint64_t row0 = tile * (uint64_t)kTileRows + (uint64_t)warp * kWarpRows;
-        const bool full = row0 + kWarpRows <= p.n;
-
-        // bit 4u+e of m: row row0 + 128u + 4*lane + e still qualifies
-        uint32_t m = 0;
-        if (full) {
-            m = kFullMask;
-        } else {
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (row0 + 128u * u + 4u * lane + e < p.n)
-                        m |= 1u << (4 * u + e);
+        }
+        ready_phase ^= 1u << b;
+        const unsigned long long t = s_claim[c];
+        if (lane == 0 && t != kStopTile && atomicAdd(&s_first[b], 1u) == 0) {
+            // first warp into this iteration: claim the next iteration's tile
+            const int c1 = (it + 1) % kClaimSlots;
+            s_claim[c1] = claim();
+            mbar_arrive(&s_claimed[c1]);
         }
 
-        for (uint32_t i = 0; i < p.npred; ++i) {
-            if (!__any_sync(0xffffffffu, m))
-                break;  // every row of this warp's chunk failed: read no more columns
-            const ScanPred &pr = p.pred[i];
-            const uint32_t *col = (const uint32_t *)pr.col + row0 + 4 * lane;
-            uint4 v[U];
+        uint32_t m = 0, ubase = 0;
+        if (t != kStopTile) {
+            const uint32_t q = (uint32_t)(t / p.tiles_per_query);
+            const unsigned long long rt = t - (unsigned long long)q * p.tiles_per_query;
+            const DevQuery dq = p.queries[q];
+            const uint64_t row0 = rt * (uint64_t)kTileRows + (uint64_t)warp * kWarpRows;
+            const bool full = row0 + kWarpRows <= p.n;
+
+            // bit 4u+e of m: row row0 + 128u + 4*lane + e still qualifies
+            if (full) {
+                m = kFullMask;
+            } else {
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                v[u] = make_uint4(0, 0, 0, 0);
-                const uint32_t mu = (m >> (4 * u)) & 0xfu;
-                if (mu) {
-                    if (full || mu == 0xfu) {
-                        v[u] = ld_stream_v4(col + 128 * u);
-                    } else {
-                        // ragged end of the table: only rows < n may be read
-                        if (mu & 1u) v[u].x = ld_stream_u32(col + 128 * u + 0);
-                        if (mu & 2u) v[u].y = ld_stream_u32(col + 128 * u + 1);
-                        if (mu & 4u) v[u].z = ld_stream_u32(col + 128 * u + 2);
-                        if (mu & 8u) v[u].w = ld_stream_u32(col + 128 * u + 3);
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (row0 + 128u * u + 4u * lane + e < p.n)
+                            m |= 1u << (4 * u + e);
+            }
+
+            for (uint32_t i = 0; i < dq.npred; ++i) {
+                if (!__any_sync(0xffffffffu, m))
+                    break;  // every row of this warp's chunk failed: read no more columns
+                const DevPred pr = p.preds[dq.first + i];
+                const uint32_t *col = (const uint32_t *)pr.col + row0 + 4 * lane;
+                uint4 v[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    v[u] = make_uint4(0, 0, 0, 0);
+                    const uint32_t mu = (m >> (4 * u)) & 0xfu;
+                    if (mu) {
+                        if (full || mu == 0xfu) {
+                            v[u] = ld_stream_v4(col + 128 * u);
+                        } else {
+                            // ragged end of the table: only rows < n may be read
+                            if (mu & 1u) v[u].x = ld_stream_u32(col + 128 * u + 0);
+                            if (mu & 2u) v[u].y = ld_stream_u32(col + 128 * u + 1);
+                            if (mu & 4u) v[u].z = ld_stream_u32(col + 128 * u + 2);
+                            if (mu & 8u) v[u].w = ld_stream_u32(col + 128 * u + 3);
+                        }
                     }
                 }
+                uint32_t keep = 0;
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    keep |= in_range4(v[u], pr.type, pr.lo, pr.hi) << (4 * u);
+                m &= keep;
             }
-            uint32_t keep = 0;
+
+            // rank the matches of this warp: row order is (u, lane, e)
+            uint32_t packed = 0;  // 8-bit count per u
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                keep |= in_range4(v[u], pr.type, pr.lo, pr.hi) << (4 * u);
-            m &= keep;
-        }
-
-        // rank the matches of this warp: row order is (u, lane, e)
-        uint32_t packed = 0;  // 8-bit count per u
+                packed |= (uint32_t)__popc((m >> (4 * u)) & 0xfu) << (8 * u);
+            uint32_t incl = packed;
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-            packed |= (uint32_t)__popc((m >> (4 * u)) & 0xfu) << (8 * u);
-        uint32_t incl = packed;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o)
-                incl += t;
-        }
-        const uint32_t excl_lane = incl - packed;
-        const uint32_t warp_packed = __shfl_sync(0xffffffffu, incl, 31);
-        uint32_t warp_total = 0;
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            warp_total += (warp_packed >> (8 * u)) & 0xffu;
-        if (lane == 0)
-            s_warp_total[b][warp] = warp_total;
-        named_bar_sync(kBarFilter, kBlock);
-
-        uint32_t tile_total = 0, warp_off = 0;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            const uint32_t t = s_warp_total[b][w];
-            warp_off += w < warp ? t : 0u;
-            tile_total += t;
-        }
-
-        // stage the row offsets (within the tile) of this warp's matches in row order
-        uint32_t ubase = warp_off;
-        const uint32_t off0 = (uint32_t)warp * kWarpRows + 4u * lane;
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            uint32_t mu = (m >> (4 * u)) & 0xfu;
-            uint32_t r = ubase + ((excl_lane >> (8 * u)) & 0xffu);
-            while (mu) {
-                const int e = __ffs(mu) - 1;
-                s_stage[b][r++] = (uint16_t)(off0 + 128u * u + e);
-                mu &= mu - 1;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o)
+                    incl += x;
             }
-            ubase += (warp_packed >> (8 * u)) & 0xffu;
-        }
+            const uint32_t excl_lane = incl - packed;
+            const uint32_t warp_packed = __shfl_sync(0xffffffffu, incl, 31);
 
-        if (threadIdx.x == 0) {
-            s_tile[b] = tile;
-            s_total[b] = tile_total;
-            // publish the aggregate at once (tile 0: its inclusive prefix)
-            st_relaxed_u64(&p.tile_state[tile],
-                           pack_state(p.epoch, tile == 0 ? kFlagPrefix : kFlagAggregate, tile_total));
+            // stage the row offsets (within the tile) of this warp's matches in row order
+            uint16_t *seg = &s_stage[b][warp * kWarpRows];
+            const uint32_t off0 = (uint32_t)warp * kWarpRows + 4u * lane;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                uint32_t mu = (m >> (4 * u)) & 0xfu;
+                uint32_t r = ubase + ((excl_lane >> (8 * u)) & 0xffu);
+                while (mu) {
+                    const int e = __ffs(mu) - 1;
+                    seg[r++] = (uint16_t)(off0 + 128u * u + e);
+                    mu &= mu - 1;
+                }
+                ubase += (warp_packed >> (8 * u)) & 0xffu;
+            }
         }
-        mbar_arrive(&s_full[b]);
-        tile = s_ticket[slot ^ 1];
-        slot ^= 1;
-        ++it;
+        __syncwarp();
+        if (lane == 0) {
+            s_warp_total[b][warp] = ubase;
+            __threadfence_block();
+            // the last filter warp to finish the iteration hands the stage over and, for
+            // a tile, publishes its aggregate at once (the launch's first tile: its prefix)
+            if (atomicAdd(&s_done[b], 1u) == kWarps - 1) {
+                __threadfence_block();
+                if (t != kStopTile) {
+                    uint32_t total = 0;
+#pragma unroll
+                    for (int w = 0; w < kWarps; ++w)
+                        total += *(volatile uint32_t *)&s_warp_total[b][w];
+                    st_relaxed_u64(state_slot(p, t),
+                                   pack_state(state_tag(p, t), t == 0 ? kFlagPrefix : kFlagAggregate, total));
+                }
+                s_stage_tile[b] = t;
+                s_done[b] = 0;
+                s_first[b] = 0;
+            }
+            mbar_arrive(&s_full[b]);
+        }
+        if (t == kStopTile)
+            break;
     }
-
-    // tell the output warp that no tile follows
-    const int b = it % kStages;
-    if (threadIdx.x == 0) {
-        if (!s_abort)
-            mbar_wait(&s_empty[b], (empty_phase >> b) & 1u);
-        s_tile[b] = kStopTile;
-    }
-    mbar_arrive(&s_full[b]);
 }
 
 template <int U>

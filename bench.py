@@ -225,6 +225,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
 
     stream = torch.cuda.current_stream()
     table = mdrq.Table(wl.columns)  # copied to the device once (not timed)
+    table.set_batch_mode(mdrq.BATCH_PLAIN)  # the headline: every query scanned on its own
     enc = table.encode_batch(wl.queries)
 
     # first call sizes the answer buffer exactly
@@ -270,6 +271,32 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     clocks = sampler.stop()
     ms = shards.max_over_ranks(ms)  # the slowest rank's time counts
     value = world * nq * args.steps / (ms / 1e3)
+
+    # ---- batched shared scan (the same batch, answers identical): speedup over plain
+    batched = None
+    if not args.no_batched:
+        table.set_batch_mode(mdrq.BATCH_SHARED)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        barrier()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for _ in range(args.steps):
+            off_b = step()
+        b1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        bms = shards.max_over_ranks(b0.elapsed_time(b1))
+        bvalue = world * nq * args.steps / (bms / 1e3)
+        batched = {"value": bvalue, "unit": UNIT, "ms_per_step": bms / args.steps,
+                   "speedup_vs_plain": bvalue / value,
+                   "mode": "shared scan: each constrained column read once per chunk of up to "
+                           "128 queries, per-row query sets from elementary-interval tables, "
+                           "two passes (count, write)",
+                   "answers_identical_to_plain": bool(int(off_b[-1]) == total_ids)}
+        table.set_batch_mode(mdrq.BATCH_PLAIN)
 
     # ---- end to end: host query descriptors in, host answers out (pinned)
     e2e = None
@@ -332,7 +359,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": cfg, "clocks": clocks, "e2e": e2e,
             "gpu_launches": timing["kernel_launches"], "roofline": roofline,
-            "cpu_baseline": cpu, "answer_ids_per_step": total_ids,
+            "cpu_baseline": cpu, "answer_ids_per_step": total_ids, "batched": batched,
         }), flush=True)
     table.close()
 
@@ -350,6 +377,7 @@ def main():
     ap.add_argument("--queries", type=int, default=None, help="first Q queries of the batch only")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the shared-scan measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

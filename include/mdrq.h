@@ -178,6 +178,25 @@ int mdrq_scan_timing_read(mdrq_table *t, double *ms, uint64_t *scan_launches, ui
                           uint64_t *kernel_launches, int reset);
 
 /*
+ * mdrq_set_batch_mode — how mdrq_query_batch answers a batch on this table.
+ *  MDRQ_BATCH_PLAIN   every query is scanned on its own (one persistent launch for the
+ *                     batch; the columns a query constrains are read once per query).
+ *  MDRQ_BATCH_SHARED  shared scan: the queries are evaluated together, each constrained
+ *                     column is read once per group of up to 128 queries, and every
+ *                     row's set of matching queries comes from per-column tables of the
+ *                     queries' interval end points (two passes: count, then write).
+ *  MDRQ_BATCH_AUTO    (default) shared when the batch has at least 32 queries that need
+ *                     a scan, plain otherwise.
+ * Both modes return identical answers. The paper answers one query at a time (Sec.
+ * 7.1.2); the shared scan is this library's extension for batches.
+ * Errors: MDRQ_E_INVAL (t NULL or unknown mode).
+ */
+#define MDRQ_BATCH_AUTO 0
+#define MDRQ_BATCH_PLAIN 1
+#define MDRQ_BATCH_SHARED 2
+int mdrq_set_batch_mode(mdrq_table *t, int mode);
+
+/*
  * mdrq_inject_fault — test hook for failure detection; the paper has no counterpart.
  * Arms one fault for the next query call on this table:
  *  MDRQ_FAULT_SKIP_TILES  the next scan launch never claims its first `arg` (>= 1) row

@@ -1,0 +1,620 @@
+// Batched shared scan: many multidimensional range queries evaluated together.
+//
+// The paper answers one query at a time (Sec. 7.1.2). For a batch, this scan reads each
+// constrained column once per group ("chunk") of up to 32*G queries and decides, for
+// every row, the exact set of queries of the chunk it satisfies (the conjunction of
+// Sec. 2.1) without one comparison per predicate:
+//
+//  * Per chunk and per column j some query of the chunk constrains, the end points of
+//    the chunk's intervals on j cut the value line into "elementary intervals". The
+//    cut points are each lower bound lo and the successor of each upper bound hi
+//    (the next float32 above hi, or hi + 1 for int32), sorted and deduplicated; an
+//    end point that every value of the column already satisfies (lo <= min, hi >= max)
+//    is left out. A value x lies in elementary interval e(x) = #{cut points <= x}.
+//  * Within one elementary interval every query's predicate on j is either true for
+//    all values or false for all values (x >= lo iff the cut lo is counted, x <= hi
+//    iff the cut succ(hi) is not). So a table T_j[e] of G 32-bit words holds the bit
+//    of every query of the chunk whose predicate on j contains elementary interval e
+//    (and of every query that does not constrain j).
+//  * A row's matching queries are then the AND over the chunk's columns of
+//    T_j[e_j(x_j)]: one binary search (exact compares in the column's type) and G
+//    word loads from shared memory per row and column, independent of how many
+//    predicates the chunk has.
+//
+// Output is CSR over the batch, ascending per query, in two passes over the table:
+// pass 1 counts each query's matches per warp unit of kUnitRows rows, an exclusive
+// scan per query (and over the queries) turns the counts into write offsets, and
+// pass 2 recomputes the masks and writes the ids, ranking rows inside a 32-row step
+// with warp ballots. Work items are (chunk, 8 units) pairs in chunk-major order over
+// a persistent grid; a CTA copies a chunk's cut points and tables into shared memory
+// when it moves to that chunk.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mdrq.h"
+#include "scan_kernel.cuh"
+#include "table.h"
+
+namespace mdrq {
+
+constexpr int kSharedWarps = 8;
+constexpr int kSharedThreads = kSharedWarps * 32;
+constexpr uint64_t kUnitRows = 8192;             // rows per warp unit
+constexpr int kSharedG = 4;                      // 32-bit mask words per chunk: 128 queries
+constexpr uint32_t kChunkImageWords = 14 * 1024; // shared-memory budget of one chunk (56 KiB)
+constexpr uint32_t kColWords = 6;                // words of one ChunkCol in an image
+
+// One column of a chunk's shared-memory image (kColWords words).
+struct ChunkCol {
+    const uint32_t *col;  // device column
+    uint32_t type;        // kTypeF32 / kTypeI32
+    uint32_t m;           // cut points
+    uint32_t cut_off;     // image word of the first cut point
+    uint32_t tab_off;     // image word of T[0][0]; T[e][g] at tab_off + e * G + g
+};
+static_assert(sizeof(ChunkCol) == kColWords * 4, "ChunkCol layout");
+
+// One chunk of the batch.
+struct ChunkHdr {
+    uint32_t ncols;       // columns constrained by some query of the chunk
+    uint32_t nq;          // queries of the chunk (<= 32 * G)
+    uint32_t q0;          // index of its first query among the batch's live queries
+    uint32_t img_words;   // words of its shared-memory image
+    uint64_t img_off;     // plan word of the image
+    uint64_t iv_off;      // plan word of its intervals: ncols x nq words (elo | ehi << 16)
+};
+
+struct SharedParams {
+    const uint32_t *plan;           // chunk images and interval lists (device)
+    uint32_t *plan_rw;              // same buffer, writable (table build)
+    const ChunkHdr *chunks;
+    uint32_t nchunks;
+    uint32_t nlive;
+    uint64_t n;
+    uint64_t n_units;
+    uint64_t items;                 // nchunks * ceil(n_units / kSharedWarps)
+    uint32_t *counts;               // [live query][unit]: matches, then exclusive prefix
+    unsigned long long *totals;     // [live query]
+    unsigned long long *qbase;      // [live query]: CSR start
+    const uint32_t *live_orig;      // [live query]: index in the caller's batch
+    unsigned long long *offsets;    // offsets[orig + 1] <- CSR end of that query
+    uint32_t *ids;
+    uint64_t capacity;
+};
+
+// e(x) = number of cut points <= x, by a fixed-step binary search (uniform across lanes)
+__device__ __forceinline__ uint32_t elementary_interval(const uint32_t *cut, uint32_t m, uint32_t xbits,
+                                                        uint32_t type)
+{
+    uint32_t pos = 0;
+    uint32_t step = m ? 1u << (31 - __clz(m)) : 0u;
+    if (type == kTypeF32) {
+        const float x = __uint_as_float(xbits);
+        for (; step; step >>= 1)
+            if (pos + step <= m && __uint_as_float(cut[pos + step - 1]) <= x)
+                pos += step;
+    } else {
+        const int x = (int)xbits;
+        for (; step; step >>= 1)
+            if (pos + step <= m && (int)cut[pos + step - 1] <= x)
+                pos += step;
+    }
+    return pos;
+}
+
+// T[e][g] for every elementary interval of every (chunk, column): bit i of word g is
+// set when query 32g + i of the chunk accepts that interval. Block (chunk, column).
+__global__ void __launch_bounds__(256) mdrq_shared_tables_kernel(SharedParams p, uint32_t max_cols)
+{
+    const uint32_t c = blockIdx.x / max_cols, a = blockIdx.x % max_cols;
+    if (c >= p.nchunks)
+        return;
+    const ChunkHdr h = p.chunks[c];
+    if (a >= h.ncols)
+        return;
+    uint32_t *img = p.plan_rw + h.img_off;
+    const ChunkCol cc = *reinterpret_cast<const ChunkCol *>(img + a * kColWords);
+    const uint32_t *iv = p.plan + h.iv_off + (uint64_t)a * h.nq;
+    const uint32_t words = (cc.m + 1) * kSharedG;
+    for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) {
+        const uint32_t e = w / kSharedG, g = w % kSharedG;
+        uint32_t bits = 0;
+        for (uint32_t i = 0; i < 32; ++i) {
+            const uint32_t q = g * 32 + i;
+            if (q < h.nq) {
+                const uint32_t r = iv[q];
+                if ((r & 0xffffu) <= e && e <= (r >> 16))
+                    bits |= 1u << i;
+            }
+        }
+        img[cc.tab_off + w] = bits;
+    }
+}
+
+// Pass 1 (WRITE = false): per live query and unit, the number of matching rows.
+// Pass 2 (WRITE = true): the ids, at qbase[q] + counts[q][unit] (exclusive prefix).
+template <bool WRITE>
+__global__ void __launch_bounds__(kSharedThreads) mdrq_shared_pass_kernel(SharedParams p)
+{
+    extern __shared__ __align__(16) uint32_t s_img[];
+    __shared__ uint32_t s_chunk;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const uint64_t groups = (p.n_units + kSharedWarps - 1) / kSharedWarps;
+    uint32_t cur = 0xffffffffu;
+    ChunkHdr h;
+
+    for (uint64_t item = blockIdx.x; item < p.items; item += gridDim.x) {
+        const uint32_t c = (uint32_t)(item / groups);
+        if (c != cur) {
+            // move to chunk c: copy its image into shared memory
+            __syncthreads();
+            h = p.chunks[c];
+            const uint4 *src = reinterpret_cast<const uint4 *>(p.plan + h.img_off);
+            uint4 *dst = reinterpret_cast<uint4 *>(s_img);
+            for (uint32_t i = threadIdx.x; i < h.img_words / 4; i += blockDim.x)
+                dst[i] = src[i];
+            if (threadIdx.x == 0)
+                s_chunk = c;
+            __syncthreads();
+            cur = c;
+        }
+        const uint64_t unit = (item % groups) * kSharedWarps + warp;
+        if (unit >= p.n_units)
+            continue;
+        const uint64_t r_begin = unit * kUnitRows;
+        const uint64_t r_end = r_begin + kUnitRows < p.n ? r_begin + kUnitRows : p.n;
+
+        // lane i keeps the figures of query 32g + i of the chunk
+        uint32_t cnt[kSharedG];
+        unsigned long long off[kSharedG];
+#pragma unroll
+        for (int g = 0; g < kSharedG; ++g) {
+            cnt[g] = 0;
+            off[g] = 0;
+            const uint32_t qi = g * 32 + lane;
+            if (WRITE && qi < h.nq) {
+                const uint64_t lq = h.q0 + qi;
+                off[g] = p.qbase[lq] + p.counts[lq * p.n_units + unit];
+            }
+        }
+        uint32_t valid_words[kSharedG];  // bits of the chunk's real queries
+#pragma unroll
+        for (int g = 0; g < kSharedG; ++g) {
+            const int left = (int)h.nq - g * 32;
+            valid_words[g] = left >= 32 ? 0xffffffffu : left > 0 ? (1u << left) - 1u : 0u;
+        }
+
+        for (uint64_t r0 = r_begin; r0 < r_end; r0 += 32) {
+            const uint64_t r = r0 + lane;
+            const bool valid = r < r_end;
+            uint32_t mask[kSharedG];
+#pragma unroll
+            for (int g = 0; g < kSharedG; ++g)
+                mask[g] = valid ? valid_words[g] : 0u;
+            for (uint32_t a = 0; a < h.ncols; ++a) {
+                const ChunkCol cc = *reinterpret_cast<const ChunkCol *>(s_img + a * kColWords);
+                const uint32_t x = valid ? __ldg(cc.col + r) : 0u;
+                const uint32_t e = elementary_interval(s_img + cc.cut_off, cc.m, x, cc.type);
+                const uint4 t = *reinterpret_cast<const uint4 *>(s_img + cc.tab_off + e * kSharedG);
+                mask[0] &= t.x;
+                mask[1] &= t.y;
+                mask[2] &= t.z;
+                mask[3] &= t.w;
+            }
+            const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+            for (int g = 0; g < kSharedG; ++g) {
+                uint32_t any = __reduce_or_sync(0xffffffffu, mask[g]);
+                while (any) {
+                    const int q = __ffs(any) - 1;
+                    any &= any - 1;
+                    const bool bit = (mask[g] >> q) & 1u;
+                    const uint32_t b = __ballot_sync(0xffffffffu, bit);
+                    if (WRITE) {
+                        const unsigned long long o = __shfl_sync(0xffffffffu, off[g], q);
+                        if (bit) {
+                            const unsigned long long pos = o + __popc(b & lt);
+                            if (pos < p.capacity)
+                                p.ids[pos] = (uint32_t)r;
+                        }
+                        if (lane == q)
+                            off[g] += __popc(b);
+                    } else if (lane == q) {
+                        cnt[g] += __popc(b);
+                    }
+                }
+            }
+        }
+        if (!WRITE) {
+#pragma unroll
+            for (int g = 0; g < kSharedG; ++g) {
+                const uint32_t qi = g * 32 + lane;
+                if (qi < h.nq)
+                    p.counts[(uint64_t)(h.q0 + qi) * p.n_units + unit] = cnt[g];
+            }
+        }
+    }
+}
+
+// Exclusive scan of one live query's unit counts, in place; totals[q] = the sum.
+// Persistent blocks of 1024 threads loop over the queries.
+__global__ void __launch_bounds__(1024) mdrq_shared_scan_kernel(SharedParams p)
+{
+    __shared__ unsigned long long s_warp[32];
+    __shared__ unsigned long long s_carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t q = blockIdx.x; q < p.nlive; q += gridDim.x) {
+        uint32_t *c = p.counts + (uint64_t)q * p.n_units;
+        if (threadIdx.x == 0)
+            s_carry = 0;
+        __syncthreads();
+        for (uint64_t base = 0; base < p.n_units; base += blockDim.x) {
+            const uint64_t i = base + threadIdx.x;
+            const unsigned long long v = i < p.n_units ? c[i] : 0ull;
+            unsigned long long x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o)
+                    x += y;
+            }
+            if (lane == 31)
+                s_warp[warp] = x;
+            __syncthreads();
+            if (warp == 0) {
+                unsigned long long w = s_warp[lane];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+                    if (lane >= o)
+                        w += y;
+                }
+                s_warp[lane] = w;  // inclusive over warps
+            }
+            __syncthreads();
+            const unsigned long long carry = s_carry;
+            const unsigned long long excl = carry + (warp ? s_warp[warp - 1] : 0ull) + x - v;
+            if (i < p.n_units)
+                c[i] = (uint32_t)excl;  // < n < 2^32 per query
+            __syncthreads();
+            if (threadIdx.x == blockDim.x - 1)
+                s_carry = carry + s_warp[31];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0)
+            p.totals[q] = s_carry;
+        __syncthreads();
+    }
+}
+
+// qbase = exclusive scan of totals over the live queries (CSR starts); offsets[orig+1]
+// = CSR end of each live query. One block.
+__global__ void __launch_bounds__(1024) mdrq_shared_qbase_kernel(SharedParams p)
+{
+    __shared__ unsigned long long s_warp[32];
+    __shared__ unsigned long long s_carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0)
+        s_carry = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < p.nlive; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const unsigned long long v = i < p.nlive ? p.totals[i] : 0ull;
+        unsigned long long x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o)
+                x += y;
+        }
+        if (lane == 31)
+            s_warp[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long w = s_warp[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o)
+                    w += y;
+            }
+            s_warp[lane] = w;
+        }
+        __syncthreads();
+        const unsigned long long carry = s_carry;
+        const unsigned long long incl = carry + (warp ? s_warp[warp - 1] : 0ull) + x;
+        if (i < p.nlive) {
+            p.qbase[i] = incl - v;
+            p.offsets[p.live_orig[i] + 1] = incl;
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1)
+            s_carry = carry + s_warp[31];
+        __syncthreads();
+    }
+}
+
+// Device buffers of the shared scan, kept with the table and grown on demand.
+struct SharedScanState {
+    uint32_t *plan = nullptr;
+    size_t plan_cap = 0;
+    ChunkHdr *chunks = nullptr;
+    size_t chunks_cap = 0;
+    uint32_t *live_orig = nullptr;
+    size_t live_cap = 0;
+    uint32_t *counts = nullptr;
+    size_t counts_cap = 0;
+    unsigned long long *totals = nullptr;
+    size_t totals_cap = 0;
+    unsigned long long *qbase = nullptr;
+    size_t qbase_cap = 0;
+    unsigned char *stage = nullptr;  // pinned: chunk headers, plan, live_orig
+    size_t stage_cap = 0;
+    int grid_pass = 0, grid_scan = 0;
+};
+
+namespace {
+
+// one column's cut points and each query's elementary-interval range on it
+struct ColPlan {
+    uint32_t dim;
+    std::vector<double> cuts;  // sorted, distinct (exact values of the column type)
+};
+
+double successor(double v, int32_t type)
+{
+    if (type == MDRQ_F32)
+        return (double)std::nextafter((float)v, INFINITY);
+    return v + 1.0;
+}
+
+uint32_t to_bits(double v, int32_t type)
+{
+    if (type == MDRQ_F32) {
+        const float f = (float)v;
+        uint32_t b;
+        std::memcpy(&b, &f, 4);
+        return b;
+    }
+    return (uint32_t)(int32_t)v;
+}
+
+}  // namespace
+
+int shared_scan_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std::vector<uint32_t> &live,
+                      uint32_t *ids, uint64_t capacity, cudaStream_t s)
+{
+    const uint32_t nlive = (uint32_t)live.size();
+    if (nlive == 0 || t->n == 0)
+        return MDRQ_OK;
+    if (!t->shared) {
+        t->shared = new (std::nothrow) SharedScanState();
+        if (!t->shared)
+            return MDRQ_E_NOMEM;
+    }
+    SharedScanState &S = *t->shared;
+
+    // ---- chunks: consecutive live queries, at most 32 * G each, image within budget
+    struct Chunk {
+        uint32_t q0, nq;
+    };
+    std::vector<Chunk> chunks;
+    {
+        uint32_t q = 0;
+        while (q < nlive) {
+            Chunk ch{q, 0};
+            std::vector<uint32_t> per_dim(t->d, 0);
+            uint32_t ncols = 0, pairs = 0;
+            while (q < nlive && ch.nq < 32u * kSharedG) {
+                const EncodedQuery &e = enc[live[q]];
+                uint32_t add_cols = 0;
+                for (uint32_t j : e.dims)
+                    add_cols += per_dim[j] == 0;
+                // upper bound of the image: columns + 2 cuts per pair + (cuts + 1) * G table words
+                const uint32_t nc = ncols + add_cols, np = pairs + (uint32_t)e.dims.size();
+                const uint64_t words = (uint64_t)nc * kColWords + 2ull * np + 4 + (2ull * np + nc) * kSharedG + 4ull * nc;
+                if (ch.nq > 0 && words > kChunkImageWords)
+                    break;
+                if (ch.nq == 0 && words > kChunkImageWords)
+                    return MDRQ_E_INVAL;  // one query alone does not fit (more than ~900 dimensions)
+                for (uint32_t j : e.dims)
+                    per_dim[j] += 1;
+                ncols = nc;
+                pairs = np;
+                ++ch.nq;
+                ++q;
+            }
+            chunks.push_back(ch);
+        }
+    }
+
+    // ---- per chunk: columns, cut points, intervals; laid out as plan words
+    std::vector<ChunkHdr> hdrs(chunks.size());
+    std::vector<uint32_t> plan;
+    plan.reserve(1 << 16);
+    uint32_t max_cols = 1;
+    for (size_t ci = 0; ci < chunks.size(); ++ci) {
+        const Chunk &ch = chunks[ci];
+        // columns in first-use order, with their cut points
+        std::vector<int> slot(t->d, -1);
+        std::vector<ColPlan> cols;
+        for (uint32_t k = 0; k < ch.nq; ++k) {
+            const EncodedQuery &e = enc[live[ch.q0 + k]];
+            for (size_t i = 0; i < e.dims.size(); ++i) {
+                const uint32_t j = e.dims[i];
+                if (slot[j] < 0) {
+                    slot[j] = (int)cols.size();
+                    cols.push_back(ColPlan{j, {}});
+                }
+                const ColumnInfo &c = t->cols[j];
+                const double lo = bound_value(e.preds[i].lo, c.type), hi = bound_value(e.preds[i].hi, c.type);
+                const double mn = bound_value(c.min_bits, c.type), mx = bound_value(c.max_bits, c.type);
+                if (lo > mn)
+                    cols[slot[j]].cuts.push_back(lo);
+                if (hi < mx)
+                    cols[slot[j]].cuts.push_back(successor(hi, c.type));
+            }
+        }
+        for (ColPlan &cp : cols) {
+            std::sort(cp.cuts.begin(), cp.cuts.end());
+            cp.cuts.erase(std::unique(cp.cuts.begin(), cp.cuts.end()), cp.cuts.end());
+        }
+        const uint32_t ncols = (uint32_t)cols.size();
+        max_cols = std::max(max_cols, ncols);
+        // image: ChunkCol[ncols], cut points, (pad to 4), tables ((m + 1) * G words each)
+        while (plan.size() % 4)
+            plan.push_back(0);
+        const uint64_t img_off = plan.size();
+        uint32_t w = ncols * kColWords;
+        std::vector<ChunkCol> cc(ncols);
+        for (uint32_t a = 0; a < ncols; ++a) {
+            cc[a].col = static_cast<const uint32_t *>(t->cols[cols[a].dim].ptr);
+            cc[a].type = (uint32_t)t->cols[cols[a].dim].type;
+            cc[a].m = (uint32_t)cols[a].cuts.size();
+            cc[a].cut_off = w;
+            w += cc[a].m;
+        }
+        w = (w + 3) & ~3u;
+        for (uint32_t a = 0; a < ncols; ++a) {
+            cc[a].tab_off = w;
+            w += (cc[a].m + 1) * kSharedG;
+        }
+        const uint32_t img_words = (w + 3) & ~3u;
+        if (img_words > kChunkImageWords)
+            return MDRQ_E_INVAL;  // cannot happen: the chunking bounded it
+        plan.resize(img_off + img_words, 0);
+        for (uint32_t a = 0; a < ncols; ++a) {
+            std::memcpy(&plan[img_off + a * kColWords], &cc[a], sizeof(ChunkCol));
+            for (uint32_t i = 0; i < cc[a].m; ++i)
+                plan[img_off + cc[a].cut_off + i] = to_bits(cols[a].cuts[i], (int32_t)cc[a].type);
+        }
+        // intervals: word [a][k] = elo | ehi << 16, the elementary intervals query k accepts on column a
+        const uint64_t iv_off = plan.size();
+        plan.resize(iv_off + (uint64_t)ncols * ch.nq, 0);
+        for (uint32_t a = 0; a < ncols; ++a)
+            for (uint32_t k = 0; k < ch.nq; ++k)
+                plan[iv_off + (uint64_t)a * ch.nq + k] = 0xffffu << 16;  // not constrained: all
+        for (uint32_t k = 0; k < ch.nq; ++k) {
+            const EncodedQuery &e = enc[live[ch.q0 + k]];
+            for (size_t i = 0; i < e.dims.size(); ++i) {
+                const uint32_t a = (uint32_t)slot[e.dims[i]];
+                const ColumnInfo &c = t->cols[e.dims[i]];
+                const std::vector<double> &cut = cols[a].cuts;
+                const double lo = bound_value(e.preds[i].lo, c.type), hi = bound_value(e.preds[i].hi, c.type);
+                const double mn = bound_value(c.min_bits, c.type), mx = bound_value(c.max_bits, c.type);
+                // x >= lo iff e(x) > rank(lo); x <= hi iff e(x) <= rank(succ(hi))
+                uint32_t elo = 0, ehi = (uint32_t)cut.size();
+                if (lo > mn)
+                    elo = (uint32_t)(std::lower_bound(cut.begin(), cut.end(), lo) - cut.begin()) + 1;
+                if (hi < mx)
+                    ehi = (uint32_t)(std::lower_bound(cut.begin(), cut.end(), successor(hi, c.type)) - cut.begin());
+                plan[iv_off + (uint64_t)a * ch.nq + k] = elo | (ehi << 16);
+            }
+        }
+        ChunkHdr &h = hdrs[ci];
+        h.ncols = ncols;
+        h.nq = ch.nq;
+        h.q0 = ch.q0;
+        h.img_words = img_words;
+        h.img_off = img_off;
+        h.iv_off = iv_off;
+    }
+
+    // ---- device buffers
+    const uint64_t n_units = (t->n + kUnitRows - 1) / kUnitRows;
+    const size_t hdr_bytes = hdrs.size() * sizeof(ChunkHdr);
+    const size_t plan_bytes = plan.size() * 4;
+    const size_t live_bytes = (size_t)nlive * 4;
+    int st = grow_device((void **)&S.plan, &S.plan_cap, std::max<size_t>(16, plan_bytes));
+    if (st == MDRQ_OK)
+        st = grow_device((void **)&S.chunks, &S.chunks_cap, hdr_bytes);
+    if (st == MDRQ_OK)
+        st = grow_device((void **)&S.live_orig, &S.live_cap, live_bytes);
+    if (st == MDRQ_OK)
+        st = grow_device((void **)&S.counts, &S.counts_cap, (size_t)nlive * n_units * 4);
+    if (st == MDRQ_OK)
+        st = grow_device((void **)&S.totals, &S.totals_cap, (size_t)nlive * 8);
+    if (st == MDRQ_OK)
+        st = grow_device((void **)&S.qbase, &S.qbase_cap, (size_t)nlive * 8);
+    if (st == MDRQ_OK)
+        st = grow_pinned((void **)&S.stage, &S.stage_cap, hdr_bytes + plan_bytes + live_bytes);
+    if (st != MDRQ_OK)
+        return st;
+    if (S.grid_pass == 0) {
+        int bps = 0;
+        const size_t smem = (size_t)kChunkImageWords * 4;
+        if (cudaFuncSetAttribute(mdrq_shared_pass_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess ||
+            cudaFuncSetAttribute(mdrq_shared_pass_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, mdrq_shared_pass_kernel<true>, kSharedThreads,
+                                                          smem) != cudaSuccess)
+            return cuda_status(cudaGetLastError());
+        S.grid_pass = t->sm_count * std::max(1, bps);
+        S.grid_scan = t->sm_count * 2;
+    }
+    std::memcpy(S.stage, hdrs.data(), hdr_bytes);
+    std::memcpy(S.stage + hdr_bytes, plan.data(), plan_bytes);
+    for (uint32_t i = 0; i < nlive; ++i)
+        reinterpret_cast<uint32_t *>(S.stage + hdr_bytes + plan_bytes)[i] = live[i];
+    MDRQ_TRY_STATUS(cudaMemcpyAsync(S.chunks, S.stage, hdr_bytes, cudaMemcpyHostToDevice, s));
+    MDRQ_TRY_STATUS(cudaMemcpyAsync(S.plan, S.stage + hdr_bytes, plan_bytes, cudaMemcpyHostToDevice, s));
+    MDRQ_TRY_STATUS(cudaMemcpyAsync(S.live_orig, S.stage + hdr_bytes + plan_bytes, live_bytes,
+                                    cudaMemcpyHostToDevice, s));
+
+    SharedParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.plan = S.plan;
+    p.plan_rw = S.plan;
+    p.chunks = S.chunks;
+    p.nchunks = (uint32_t)hdrs.size();
+    p.nlive = nlive;
+    p.n = t->n;
+    p.n_units = n_units;
+    p.items = (uint64_t)hdrs.size() * ((n_units + kSharedWarps - 1) / kSharedWarps);
+    p.counts = S.counts;
+    p.totals = S.totals;
+    p.qbase = S.qbase;
+    p.live_orig = S.live_orig;
+    p.offsets = t->offsets_dev;
+    p.ids = ids;
+    p.capacity = capacity;
+
+    const size_t smem = (size_t)kChunkImageWords * 4;
+    const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)S.grid_pass, p.items);
+    mdrq_shared_tables_kernel<<<(uint32_t)hdrs.size() * max_cols, 256, 0, s>>>(p, max_cols);
+    mdrq_shared_pass_kernel<false><<<grid, kSharedThreads, smem, s>>>(p);
+    mdrq_shared_scan_kernel<<<std::min<uint32_t>(nlive, (uint32_t)S.grid_scan), 1024, 0, s>>>(p);
+    mdrq_shared_qbase_kernel<<<1, 1024, 0, s>>>(p);
+    mdrq_shared_pass_kernel<true><<<grid, kSharedThreads, smem, s>>>(p);
+    MDRQ_TRY_STATUS(cudaGetLastError());
+    t->last_launches += 5;
+    if (t->timing)
+        t->acc_kernels += 5;
+    return MDRQ_OK;
+}
+
+void shared_scan_free(mdrq_table *t)
+{
+    if (!t || !t->shared)
+        return;
+    SharedScanState &S = *t->shared;
+    cudaFree(S.plan);
+    cudaFree(S.chunks);
+    cudaFree(S.live_orig);
+    cudaFree(S.counts);
+    cudaFree(S.totals);
+    cudaFree(S.qbase);
+    cudaFreeHost(S.stage);
+    delete t->shared;
+    t->shared = nullptr;
+}
+
+}  // namespace mdrq

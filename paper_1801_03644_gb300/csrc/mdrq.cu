@@ -14,6 +14,7 @@
 
 #include "mdrq.h"
 #include "scan_kernel.cuh"
+#include "table.h"
 
 using namespace mdrq;
 
@@ -71,75 +72,9 @@ __global__ void mdrq_sample_kernel(const uint32_t *col, uint64_t n, uint32_t S, 
 
 }  // namespace mdrq
 
-namespace {
+namespace mdrq {
 
-constexpr uint32_t kSampleRows = 4096;  // per-column sample for selectivity estimates
-
-struct ColumnInfo {
-    const void *ptr = nullptr;  // device
-    int32_t type = MDRQ_F32;
-    uint32_t min_bits = 0, max_bits = 0;  // exact column minimum / maximum (n > 0)
-    std::vector<double> sample;           // sorted
-};
-
-struct EncodedQuery {
-    bool empty = false;                 // proven empty on the host
-    std::vector<DevPred> preds;         // non-trivial predicates, most selective first
-    uint64_t scanned_columns = 0;
-};
-
-}  // namespace
-
-struct mdrq_table {
-    int device = 0;
-    uint64_t n = 0;
-    uint32_t d = 0;
-    std::vector<ColumnInfo> cols;
-    std::vector<void *> owned;  // device columns this table allocated
-
-    // scratch: [0] claim counter, [1] error word, [2..] ring of look-back states
-    unsigned long long *scratch = nullptr;
-    unsigned long long *ticket = nullptr;
-    int *error = nullptr;
-    unsigned long long *tile_state = nullptr;
-    uint32_t ring_bits = 16;
-    unsigned long long ticket_next = 0;
-    uint32_t tag_next = 1;  // tag of the next launch's first ring lap (0: cleared slot)
-
-    // per-batch query tables: device copies and their pinned staging
-    DevQuery *dq_dev = nullptr;
-    size_t dq_dev_cap = 0;
-    DevPred *dp_dev = nullptr;
-    size_t dp_dev_cap = 0;
-    unsigned char *qstage_host = nullptr;  // pinned: DevQuery[] then DevPred[]
-    size_t qstage_host_cap = 0;
-
-    unsigned long long *offsets_dev = nullptr;  // nq + 1 entries
-    size_t offsets_dev_cap = 0;
-    unsigned long long *offsets_host = nullptr;  // pinned mirror
-    size_t offsets_host_cap = 0;
-    uint32_t *ids_stage = nullptr;  // device staging for host-side answers
-    size_t ids_stage_cap = 0;
-    int *error_host = nullptr;      // pinned
-
-    int sm_count = 0;
-    int blocks_per_sm[3] = {0, 0, 0};  // for U = 1, 2, 4
-
-    uint64_t last_launches = 0;
-    uint64_t last_bytes = 0;
-
-    // optional per-launch event timing of the scan kernel
-    bool timing = false;
-    std::vector<cudaEvent_t> ev;  // pairs: [2i] before, [2i+1] after launch i
-    size_t ev_used = 0;           // pairs recorded since the last reset
-    uint64_t acc_scans = 0, acc_bytes = 0, acc_kernels = 0;
-
-    // host-side fault injection for failure-detection tests (mdrq_inject_fault)
-    uint64_t inject_skip_tiles = 0;  // next scan launch never claims its first tiles
-    int inject_nomem = 0;            // next query call fails its scratch allocation
-};
-
-namespace {
+constexpr size_t kAutoSharedMinQueries = 32;  // MDRQ_BATCH_AUTO: shared scan from this many
 
 int cuda_status(cudaError_t e)
 {
@@ -251,6 +186,7 @@ int encode_query(const mdrq_table *t, const mdrq_pred *preds, uint32_t npreds, E
     if (keep.size() > (size_t)kMaxPreds)
         return MDRQ_E_INVAL;
     for (const Cand &cd : keep) {
+        q.dims.push_back(cd.dim);
         DevPred sp;
         sp.col = t->cols[cd.dim].ptr;
         sp.type = (uint32_t)t->cols[cd.dim].type;
@@ -462,9 +398,33 @@ int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, u
     MDRQ_TRY(cudaMemsetAsync(t->offsets_dev, 0, ((size_t)nq + 1) * 8, s));
     MDRQ_TRY(cudaMemsetAsync(t->error, 0, sizeof(int), s));
 
+    const bool shared = t->batch_mode == MDRQ_BATCH_SHARED ||
+                        (t->batch_mode == MDRQ_BATCH_AUTO && nlive >= kAutoSharedMinQueries);
+    if (shared) {
+        cudaEvent_t *evp = nullptr;
+        if (t->timing) {
+            if (t->ev.size() < 2 * (t->ev_used + 1)) {
+                cudaEvent_t a, b;
+                MDRQ_TRY(cudaEventCreate(&a));
+                MDRQ_TRY(cudaEventCreate(&b));
+                t->ev.push_back(a);
+                t->ev.push_back(b);
+            }
+            evp = &t->ev[2 * t->ev_used];
+            ++t->ev_used;
+            MDRQ_TRY(cudaEventRecord(evp[0], s));
+        }
+        st = shared_scan_batch(t, enc, live, out, capacity, s);
+        if (st != MDRQ_OK)
+            return st;
+        if (evp) {
+            MDRQ_TRY(cudaEventRecord(evp[1], s));
+            t->acc_scans += 1;
+        }
+    }
     // one launch per chunk of queries whose ids fit the 40-bit state values
     const uint64_t per_launch = std::max<uint64_t>(1, kValueMask / std::max<uint64_t>(1, t->n));
-    for (size_t c0 = 0; c0 < nlive; c0 += per_launch) {
+    for (size_t c0 = 0; !shared && c0 < nlive; c0 += per_launch) {
         const uint32_t cnt = (uint32_t)std::min<uint64_t>(per_launch, nlive - c0);
         uint64_t cols = 0;
         for (size_t i = c0; i < c0 + cnt; ++i)
@@ -521,6 +481,7 @@ void destroy(mdrq_table *t)
         cudaFree(p);
     cudaFree(t->scratch);
     cudaFree(t->offsets_dev);
+    shared_scan_free(t);
     cudaFree(t->ids_stage);
     cudaFree(t->dq_dev);
     cudaFree(t->dp_dev);
@@ -626,7 +587,7 @@ int load(const void *const *cols, const int32_t *types, uint32_t d, uint64_t n, 
     return MDRQ_OK;
 }
 
-}  // namespace
+}  // namespace mdrq
 
 extern "C" {
 
@@ -733,6 +694,14 @@ int mdrq_scan_timing_read(mdrq_table *t, double *ms, uint64_t *scan_launches, ui
         t->ev_used = 0;
         t->acc_scans = t->acc_bytes = t->acc_kernels = 0;
     }
+    return MDRQ_OK;
+}
+
+int mdrq_set_batch_mode(mdrq_table *t, int mode)
+{
+    if (!t || (mode != MDRQ_BATCH_AUTO && mode != MDRQ_BATCH_PLAIN && mode != MDRQ_BATCH_SHARED))
+        return MDRQ_E_INVAL;
+    t->batch_mode = mode;
     return MDRQ_OK;
 }
 

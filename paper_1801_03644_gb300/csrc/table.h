@@ -1,0 +1,113 @@
+// Library-internal state of a table (the opaque mdrq_table of include/mdrq.h), shared by
+// the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "mdrq.h"
+#include "scan_kernel.cuh"
+
+namespace mdrq {
+
+constexpr uint32_t kSampleRows = 4096;  // per-column sample for selectivity estimates
+
+struct ColumnInfo {
+    const void *ptr = nullptr;  // device
+    int32_t type = MDRQ_F32;
+    uint32_t min_bits = 0, max_bits = 0;  // exact column minimum / maximum (n > 0)
+    std::vector<double> sample;           // sorted
+};
+
+// a2: one query after encoding
+struct EncodedQuery {
+    bool empty = false;          // proven empty on the host
+    std::vector<DevPred> preds;  // non-trivial predicates, most selective first
+    std::vector<uint32_t> dims;  // their dimensions
+    uint64_t scanned_columns = 0;
+};
+
+struct SharedScanState;  // device buffers of the batched shared scan (batched.cu)
+
+}  // namespace mdrq
+
+struct mdrq_table {
+    int device = 0;
+    uint64_t n = 0;
+    uint32_t d = 0;
+    std::vector<mdrq::ColumnInfo> cols;
+    std::vector<void *> owned;  // device columns this table allocated
+
+    // scratch: [0] claim counter, [1] error word, [2..] ring of look-back states
+    unsigned long long *scratch = nullptr;
+    unsigned long long *ticket = nullptr;
+    int *error = nullptr;
+    unsigned long long *tile_state = nullptr;
+    uint32_t ring_bits = 16;
+    unsigned long long ticket_next = 0;
+    uint32_t tag_next = 1;  // tag of the next launch's first ring lap (0: cleared slot)
+
+    // per-batch query tables: device copies and their pinned staging
+    mdrq::DevQuery *dq_dev = nullptr;
+    size_t dq_dev_cap = 0;
+    mdrq::DevPred *dp_dev = nullptr;
+    size_t dp_dev_cap = 0;
+    unsigned char *qstage_host = nullptr;  // pinned: DevQuery[] then DevPred[]
+    size_t qstage_host_cap = 0;
+
+    unsigned long long *offsets_dev = nullptr;  // nq + 1 entries
+    size_t offsets_dev_cap = 0;
+    unsigned long long *offsets_host = nullptr;  // pinned mirror
+    size_t offsets_host_cap = 0;
+    uint32_t *ids_stage = nullptr;  // device staging for host-side answers
+    size_t ids_stage_cap = 0;
+    int *error_host = nullptr;      // pinned
+
+    int sm_count = 0;
+    int blocks_per_sm[3] = {0, 0, 0};  // for U = 1, 2, 4
+
+    uint64_t last_launches = 0;
+    uint64_t last_bytes = 0;
+
+    // optional per-launch event timing of the scan kernel
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;  // pairs: [2i] before, [2i+1] after launch i
+    size_t ev_used = 0;           // pairs recorded since the last reset
+    uint64_t acc_scans = 0, acc_bytes = 0, acc_kernels = 0;
+
+    // batched shared scan (mdrq_set_batch_mode, batched.cu)
+    int batch_mode = MDRQ_BATCH_AUTO;
+    mdrq::SharedScanState *shared = nullptr;
+
+    // host-side fault injection for failure-detection tests (mdrq_inject_fault)
+    uint64_t inject_skip_tiles = 0;  // next scan launch never claims its first tiles
+    int inject_nomem = 0;            // next query call fails its scratch allocation
+};
+
+
+#define MDRQ_TRY_STATUS(expr)                   \
+    do {                                        \
+        int _s = mdrq::cuda_status(expr);       \
+        if (_s != MDRQ_OK) {                    \
+            (void)cudaGetLastError();           \
+            return _s;                          \
+        }                                       \
+    } while (0)
+
+namespace mdrq {
+
+int cuda_status(cudaError_t e);
+double bound_value(uint32_t bits, int32_t type);
+int encode_query(const mdrq_table *t, const mdrq_pred *preds, uint32_t npreds, EncodedQuery &q);
+int grow_device(void **p, size_t *cap, size_t bytes);
+int grow_pinned(void **p, size_t *cap, size_t bytes);
+
+// batched.cu: answer the live queries of a batch with the shared scan. enc/live as in
+// run_batch; writes offsets_dev[orig + 1] for every live query.
+int shared_scan_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std::vector<uint32_t> &live,
+                      uint32_t *ids, uint64_t capacity, cudaStream_t s);
+void shared_scan_free(mdrq_table *t);
+
+}  // namespace mdrq

@@ -43,9 +43,10 @@ _lib = None
 EXPORTS = ["mdrq_load_columns", "mdrq_query", "mdrq_query_batch", "mdrq_free",
            "mdrq_status_string", "mdrq_table_rows", "mdrq_table_dims", "mdrq_last_scan_stats",
            "mdrq_scan_timing", "mdrq_scan_timing_read", "mdrq_query_static",
-           "mdrq_inject_fault"]
+           "mdrq_inject_fault", "mdrq_set_batch_mode"]
 
 FAULT_SKIP_TILES, FAULT_NOMEM = 1, 2
+BATCH_AUTO, BATCH_PLAIN, BATCH_SHARED = 0, 1, 2
 
 STATIC_MAX_ROWS = 1 << 28  # MDRQ_STATIC_MAX_ROWS
 
@@ -82,6 +83,8 @@ def lib():
         L.mdrq_scan_timing_read.restype = ctypes.c_int
         L.mdrq_scan_timing_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64),
                                             ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.c_int]
+        L.mdrq_set_batch_mode.restype = ctypes.c_int
+        L.mdrq_set_batch_mode.argtypes = [vp, ctypes.c_int]
         L.mdrq_inject_fault.restype = ctypes.c_int
         L.mdrq_inject_fault.argtypes = [vp, ctypes.c_int, u64]
         L.mdrq_query_static.restype = ctypes.c_int
@@ -300,6 +303,12 @@ class Table:
         if st != OK:
             raise MDRQError(st, "mdrq_query_batch")
         return out[: int(off[-1])], off
+
+    def set_batch_mode(self, mode: int):
+        """``mdrq_set_batch_mode``: BATCH_AUTO, BATCH_PLAIN or BATCH_SHARED."""
+        st = lib().mdrq_set_batch_mode(self._h, int(mode))
+        if st != OK:
+            raise MDRQError(st, "mdrq_set_batch_mode")
 
     def inject_fault(self, kind: int, arg: int = 0):
         """Arm a test fault for the next query call (``mdrq_inject_fault``)."""

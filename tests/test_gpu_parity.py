@@ -28,11 +28,13 @@ def _device(cols):
     return [torch.from_numpy(np.ascontiguousarray(c)).cuda() for c in cols]
 
 
-def check_batch(M, columns, queries, on_device=True, nthreads=8):
+def check_batch(M, columns, queries, on_device=True, nthreads=8, mode=None):
     """Every query's answer equals the oracle's (count and every id)."""
     import torch
     cols = _device(columns) if on_device else columns
     with M.Table(cols) as t:
+        if mode is not None:
+            t.set_batch_mode(mode)
         ids, off = t.query_batch(queries)
         torch.cuda.synchronize()
         got = M.as_uint32_numpy(ids)
@@ -105,30 +107,37 @@ def test_mixed_types_and_special_values(M):
     check_batch(M, cols, qs)
 
 
-def test_uniform_1M_all_queries(M):
+MODES = pytest.mark.parametrize("mode", [1, 2], ids=["plain", "shared"])
+
+
+@MODES
+def test_uniform_1M_all_queries(M, mode):
     """1M x 3 uniform, 100 complete-match queries of about 1% selectivity."""
     wl = W.uniform_small()
-    off = check_batch(M, wl.columns, wl.queries)
+    off = check_batch(M, wl.columns, wl.queries, mode=mode)
     assert abs(off[-1] / 100 - 10_000) < 3 * math.sqrt(1e4) / 10 * 3
 
 
-def test_mixed_clustered_reduced(M):
+@MODES
+def test_mixed_clustered_reduced(M, mode):
     """The 8-column uniform + cluster-mixture recipe at 3M rows, 96 partial-match queries."""
     wl = W.mixed_clustered(n=3_000_000, nq=96)
-    check_batch(M, wl.columns, wl.queries, nthreads=16)
+    check_batch(M, wl.columns, wl.queries, nthreads=16, mode=mode)
 
 
-def test_mixed_clustered_large_tiles(M):
+@MODES
+def test_mixed_clustered_large_tiles(M, mode):
     """12M rows: the 4096-row tile variant, several hundred tiles per SM wave."""
     wl = W.mixed_clustered(n=12_000_017, nq=24)
-    check_batch(M, wl.columns, wl.queries, nthreads=16)
+    check_batch(M, wl.columns, wl.queries, nthreads=16, mode=mode)
 
 
-def test_skewed_mixed_types_reduced(M):
+@MODES
+def test_skewed_mixed_types_reduced(M, mode):
     """32 columns (float32 uniform, int32 Zipf, int32 categorical), 256 queries including
     empty ones, at 2M rows."""
     wl = W.skewed_mixed_types(n=2_000_000, nq=256)
-    off = check_batch(M, wl.columns, wl.queries, nthreads=16)
+    off = check_batch(M, wl.columns, wl.queries, nthreads=16, mode=mode)
     assert np.sum(np.diff(off.astype(np.int64)) == 0) >= 5
 
 
@@ -156,6 +165,7 @@ def test_capacity_overflow_reports_required_size(M):
     total = sum(w.size for w in want)
     cat = np.concatenate(want)
     with M.Table(cols) as t:
+        t.set_batch_mode(M.BATCH_PLAIN)
         enc = t.encode_batch(wl.queries)
         cap = total // 3
         buf = torch.full((cap + 64,), -1, dtype=torch.int32, device="cuda")
@@ -207,4 +217,4 @@ def test_misaligned_device_column_rejected(M):
 def test_repeat_calls_reuse_scratch(M):
     """Hundreds of launches on one table (tile-state epochs, claim counter) stay exact."""
     wl = W.uniform_small(n=250_000, nq=300)
-    check_batch(M, wl.columns, wl.queries)
+    check_batch(M, wl.columns, wl.queries, mode=1)

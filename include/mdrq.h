@@ -186,7 +186,7 @@ int mdrq_scan_timing_read(mdrq_table *t, double *ms, uint64_t *scan_launches, ui
  *                     row's set of matching queries comes from per-column tables of the
  *                     queries' interval end points (two passes: count, then write).
  *  MDRQ_BATCH_AUTO    (default) shared when the batch has at least 32 queries that need
- *                     a scan, plain otherwise.
+ *                     a scan and the table at least 4,000,000 rows, plain otherwise.
  * Both modes return identical answers. The paper answers one query at a time (Sec.
  * 7.1.2); the shared scan is this library's extension for batches.
  * Errors: MDRQ_E_INVAL (t NULL or unknown mode).

@@ -22,7 +22,7 @@
 //    predicates the chunk has.
 //
 // Output is CSR over the batch, ascending per query, in two passes over the table:
-// pass 1 counts each query's matches per warp unit of kUnitRows rows, an exclusive
+// pass 1 counts each query's matches per warp unit of consecutive rows, an exclusive
 // scan per query (and over the queries) turns the counts into write offsets, and
 // pass 2 recomputes the masks and writes the ids, ranking rows inside a 32-row step
 // with warp ballots. Work items are (chunk, 8 units) pairs in chunk-major order over
@@ -45,10 +45,14 @@ namespace mdrq {
 
 constexpr int kSharedWarps = 8;
 constexpr int kSharedThreads = kSharedWarps * 32;
-constexpr uint64_t kUnitRows = 8192;             // rows per warp unit
+constexpr uint64_t kMaxUnitRows = 8192;          // rows per warp unit, large tables
+constexpr uint64_t kMinUnitRows = 256;           // rows per warp unit, small tables
 constexpr int kSharedG = 4;                      // 32-bit mask words per chunk: 128 queries
 constexpr uint32_t kChunkImageWords = 14 * 1024; // shared-memory budget of one chunk (56 KiB)
-constexpr uint32_t kColWords = 6;                // words of one ChunkCol in an image
+constexpr uint32_t kColWords = 10;               // words of one ChunkCol in an image
+constexpr uint32_t kHintBuckets = 256;           // value buckets of a column's search hint
+constexpr int kCountPlanes = 4;                  // bit planes of the pass-1 lane counters
+constexpr int kPrefetchCols = 8;                 // column values per row kept in flight
 
 // One column of a chunk's shared-memory image (kColWords words).
 struct ChunkCol {
@@ -57,6 +61,10 @@ struct ChunkCol {
     uint32_t m;           // cut points
     uint32_t cut_off;     // image word of the first cut point
     uint32_t tab_off;     // image word of T[0][0]; T[e][g] at tab_off + e * G + g
+    float base;           // search hint: bucket floor((x - base) * scale), clamped
+    float scale;          // 0: no hint (binary search)
+    uint32_t hint_off;    // image word of kHintBuckets 16-bit start positions
+    uint32_t pad;
 };
 static_assert(sizeof(ChunkCol) == kColWords * 4, "ChunkCol layout");
 
@@ -78,6 +86,7 @@ struct SharedParams {
     uint32_t nlive;
     uint64_t n;
     uint64_t n_units;
+    uint64_t unit_rows;             // rows per warp unit (a multiple of 32)
     uint64_t items;                 // nchunks * ceil(n_units / kSharedWarps)
     uint32_t *counts;               // [live query][unit]: matches, then exclusive prefix
     unsigned long long *totals;     // [live query]
@@ -108,6 +117,35 @@ __device__ __forceinline__ uint32_t elementary_interval(const uint32_t *cut, uin
     return pos;
 }
 
+// e(x) from the column's hint: start at the cut count of x's value bucket (computed in
+// float, so possibly a neighbouring bucket) and step with exact compares to the answer.
+template <typename T>
+__device__ __forceinline__ uint32_t walk_to_interval(const uint32_t *cut, uint32_t m, uint32_t pos, T x)
+{
+    while (pos > 0 && *reinterpret_cast<const T *>(&cut[pos - 1]) > x)
+        --pos;
+    while (pos < m && *reinterpret_cast<const T *>(&cut[pos]) <= x)
+        ++pos;
+    return pos;
+}
+
+__device__ __forceinline__ uint32_t interval_of(const uint32_t *img, const ChunkCol *cc, uint32_t xbits)
+{
+    const uint32_t *cut = img + cc->cut_off;
+    const uint32_t m = cc->m;
+    if (cc->scale == 0.0f)
+        return elementary_interval(cut, m, xbits, cc->type);
+    const bool f32 = cc->type == kTypeF32;
+    const float xf = f32 ? __uint_as_float(xbits) : (float)(int)xbits;
+    int b = __float2int_rz((xf - cc->base) * cc->scale);
+    b = b < 0 ? 0 : (b >= (int)kHintBuckets ? (int)kHintBuckets - 1 : b);
+    const uint32_t h = img[cc->hint_off + (b >> 1)];
+    const uint32_t start = (b & 1) ? (h >> 16) : (h & 0xffffu);
+    if (f32)
+        return walk_to_interval<float>(cut, m, start, __uint_as_float(xbits));
+    return walk_to_interval<int>(cut, m, start, (int)xbits);
+}
+
 // T[e][g] for every elementary interval of every (chunk, column): bit i of word g is
 // set when query 32g + i of the chunk accepts that interval. Block (chunk, column).
 __global__ void __launch_bounds__(256) mdrq_shared_tables_kernel(SharedParams p, uint32_t max_cols)
@@ -134,6 +172,35 @@ __global__ void __launch_bounds__(256) mdrq_shared_tables_kernel(SharedParams p,
             }
         }
         img[cc.tab_off + w] = bits;
+    }
+}
+
+// 32 x 32 bit transpose across a warp: on return, bit k of lane l's word is bit l of
+// lane k's word on entry. Five exchange stages, each swapping the off-diagonal blocks.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane)
+{
+    const uint32_t lo_mask[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int sft = 16 >> k;
+        const uint32_t m = lo_mask[k];
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, sft);
+        x = (lane & sft) ? ((y & ~m) >> sft) | (x & ~m) : (x & m) | ((y & m) << sft);
+    }
+    return x;
+}
+
+// Add the bit-sliced counters into cnt (lane l: query 32g + l) and clear them.
+__device__ __forceinline__ void flush_counts(uint32_t (&plane)[kSharedG][kCountPlanes], uint32_t (&cnt)[kSharedG],
+                                             int lane)
+{
+#pragma unroll
+    for (int g = 0; g < kSharedG; ++g) {
+#pragma unroll
+        for (int j = 0; j < kCountPlanes; ++j) {
+            cnt[g] += (uint32_t)__popc(warp_transpose32(plane[g][j], lane)) << j;
+            plane[g][j] = 0u;
+        }
     }
 }
 
@@ -168,8 +235,8 @@ __global__ void __launch_bounds__(kSharedThreads) mdrq_shared_pass_kernel(Shared
         const uint64_t unit = (item % groups) * kSharedWarps + warp;
         if (unit >= p.n_units)
             continue;
-        const uint64_t r_begin = unit * kUnitRows;
-        const uint64_t r_end = r_begin + kUnitRows < p.n ? r_begin + kUnitRows : p.n;
+        const uint64_t r_begin = unit * p.unit_rows;
+        const uint64_t r_end = r_begin + p.unit_rows < p.n ? r_begin + p.unit_rows : p.n;
 
         // lane i keeps the figures of query 32g + i of the chunk
         uint32_t cnt[kSharedG];
@@ -184,6 +251,13 @@ __global__ void __launch_bounds__(kSharedThreads) mdrq_shared_pass_kernel(Shared
                 off[g] = p.qbase[lq] + p.counts[lq * p.n_units + unit];
             }
         }
+        uint32_t plane[kSharedG][kCountPlanes];  // pass 1: bit-sliced per-lane counters
+        uint32_t since_flush = 0;
+#pragma unroll
+        for (int g = 0; g < kSharedG; ++g)
+#pragma unroll
+            for (int j = 0; j < kCountPlanes; ++j)
+                plane[g][j] = 0u;
         uint32_t valid_words[kSharedG];  // bits of the chunk's real queries
 #pragma unroll
         for (int g = 0; g < kSharedG; ++g) {
@@ -191,33 +265,78 @@ __global__ void __launch_bounds__(kSharedThreads) mdrq_shared_pass_kernel(Shared
             valid_words[g] = left >= 32 ? 0xffffffffu : left > 0 ? (1u << left) - 1u : 0u;
         }
 
+        // values of the first kPrefetchCols columns for the next 32-row step are loaded
+        // while the current step is evaluated (software pipelining of the column reads)
+        const uint32_t npre = h.ncols < kPrefetchCols ? h.ncols : kPrefetchCols;
+        uint32_t xn[kPrefetchCols];
+#pragma unroll
+        for (int i = 0; i < kPrefetchCols; ++i) {
+            const uint64_t r = r_begin + lane;
+            xn[i] = 0u;
+            if (i < (int)npre && r < r_end)
+                xn[i] = __ldg(reinterpret_cast<const ChunkCol *>(s_img + i * kColWords)->col + r);
+        }
         for (uint64_t r0 = r_begin; r0 < r_end; r0 += 32) {
             const uint64_t r = r0 + lane;
             const bool valid = r < r_end;
+            uint32_t x[kPrefetchCols];
+#pragma unroll
+            for (int i = 0; i < kPrefetchCols; ++i) {
+                x[i] = xn[i];
+                const uint64_t rn = r + 32;
+                xn[i] = 0u;
+                if (i < (int)npre && rn < r_end)
+                    xn[i] = __ldg(reinterpret_cast<const ChunkCol *>(s_img + i * kColWords)->col + rn);
+            }
             uint32_t mask[kSharedG];
 #pragma unroll
             for (int g = 0; g < kSharedG; ++g)
                 mask[g] = valid ? valid_words[g] : 0u;
-            for (uint32_t a = 0; a < h.ncols; ++a) {
-                const ChunkCol cc = *reinterpret_cast<const ChunkCol *>(s_img + a * kColWords);
-                const uint32_t x = valid ? __ldg(cc.col + r) : 0u;
-                const uint32_t e = elementary_interval(s_img + cc.cut_off, cc.m, x, cc.type);
-                const uint4 t = *reinterpret_cast<const uint4 *>(s_img + cc.tab_off + e * kSharedG);
-                mask[0] &= t.x;
-                mask[1] &= t.y;
-                mask[2] &= t.z;
-                mask[3] &= t.w;
-            }
-            const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
-            for (int g = 0; g < kSharedG; ++g) {
-                uint32_t any = __reduce_or_sync(0xffffffffu, mask[g]);
-                while (any) {
-                    const int q = __ffs(any) - 1;
-                    any &= any - 1;
-                    const bool bit = (mask[g] >> q) & 1u;
-                    const uint32_t b = __ballot_sync(0xffffffffu, bit);
-                    if (WRITE) {
+            for (int i = 0; i < kPrefetchCols; ++i) {
+                if (i < (int)npre) {
+                    const ChunkCol *cc = reinterpret_cast<const ChunkCol *>(s_img + i * kColWords);
+                    const uint32_t e = interval_of(s_img, cc, x[i]);
+                    const uint4 t = *reinterpret_cast<const uint4 *>(s_img + cc->tab_off + e * kSharedG);
+                    mask[0] &= t.x;
+                    mask[1] &= t.y;
+                    mask[2] &= t.z;
+                    mask[3] &= t.w;
+                }
+            }
+            // columns beyond the prefetched ones: loaded together, then evaluated
+            for (uint32_t a0 = npre; a0 < h.ncols; a0 += kPrefetchCols) {
+                uint32_t y[kPrefetchCols];
+#pragma unroll
+                for (int i = 0; i < kPrefetchCols; ++i) {
+                    y[i] = 0u;
+                    if (a0 + i < h.ncols && valid)
+                        y[i] = __ldg(reinterpret_cast<const ChunkCol *>(s_img + (a0 + i) * kColWords)->col + r);
+                }
+#pragma unroll
+                for (int i = 0; i < kPrefetchCols; ++i) {
+                    if (a0 + i < h.ncols) {
+                        const ChunkCol *cc = reinterpret_cast<const ChunkCol *>(s_img + (a0 + i) * kColWords);
+                        const uint32_t e = interval_of(s_img, cc, y[i]);
+                        const uint4 t = *reinterpret_cast<const uint4 *>(s_img + cc->tab_off + e * kSharedG);
+                        mask[0] &= t.x;
+                        mask[1] &= t.y;
+                        mask[2] &= t.z;
+                        mask[3] &= t.w;
+                    }
+                }
+            }
+            if (WRITE) {
+                // each query with matches in this step: rank its rows by lane, write ids
+                const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+                for (int g = 0; g < kSharedG; ++g) {
+                    uint32_t any = __reduce_or_sync(0xffffffffu, mask[g]);
+                    while (any) {
+                        const int q = __ffs(any) - 1;
+                        any &= any - 1;
+                        const bool bit = (mask[g] >> q) & 1u;
+                        const uint32_t b = __ballot_sync(0xffffffffu, bit);
                         const unsigned long long o = __shfl_sync(0xffffffffu, off[g], q);
                         if (bit) {
                             const unsigned long long pos = o + __popc(b & lt);
@@ -226,13 +345,29 @@ __global__ void __launch_bounds__(kSharedThreads) mdrq_shared_pass_kernel(Shared
                         }
                         if (lane == q)
                             off[g] += __popc(b);
-                    } else if (lane == q) {
-                        cnt[g] += __popc(b);
                     }
+                }
+            } else {
+                // count: add this lane's bits into per-lane bit-sliced counters (plane j
+                // holds bit j of 32 counters); flush them before they can overflow
+#pragma unroll
+                for (int g = 0; g < kSharedG; ++g) {
+                    uint32_t carry = mask[g];
+#pragma unroll
+                    for (int j = 0; j < kCountPlanes; ++j) {
+                        const uint32_t t = plane[g][j] & carry;
+                        plane[g][j] ^= carry;
+                        carry = t;
+                    }
+                }
+                if (++since_flush == (1u << kCountPlanes) - 1u) {
+                    flush_counts(plane, cnt, lane);
+                    since_flush = 0;
                 }
             }
         }
         if (!WRITE) {
+            flush_counts(plane, cnt, lane);
 #pragma unroll
             for (int g = 0; g < kSharedG; ++g) {
                 const uint32_t qi = g * 32 + lane;
@@ -419,7 +554,8 @@ int shared_scan_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const
                     add_cols += per_dim[j] == 0;
                 // upper bound of the image: columns + 2 cuts per pair + (cuts + 1) * G table words
                 const uint32_t nc = ncols + add_cols, np = pairs + (uint32_t)e.dims.size();
-                const uint64_t words = (uint64_t)nc * kColWords + 2ull * np + 4 + (2ull * np + nc) * kSharedG + 4ull * nc;
+                const uint64_t words = (uint64_t)nc * (kColWords + kHintBuckets / 2) + 2ull * np + 4 +
+                                       (2ull * np + nc) * kSharedG + 4ull * nc;
                 if (ch.nq > 0 && words > kChunkImageWords)
                     break;
                 if (ch.nq == 0 && words > kChunkImageWords)
@@ -468,16 +604,53 @@ int shared_scan_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const
         }
         const uint32_t ncols = (uint32_t)cols.size();
         max_cols = std::max(max_cols, ncols);
-        // image: ChunkCol[ncols], cut points, (pad to 4), tables ((m + 1) * G words each)
+        // image: ChunkCol[ncols], hints, cut points, (pad to 4), tables ((m + 1) * G words each)
         while (plan.size() % 4)
             plan.push_back(0);
         const uint64_t img_off = plan.size();
         uint32_t w = ncols * kColWords;
         std::vector<ChunkCol> cc(ncols);
+        std::vector<std::vector<uint32_t>> hint(ncols);
         for (uint32_t a = 0; a < ncols; ++a) {
-            cc[a].col = static_cast<const uint32_t *>(t->cols[cols[a].dim].ptr);
-            cc[a].type = (uint32_t)t->cols[cols[a].dim].type;
+            const ColumnInfo &ci_ = t->cols[cols[a].dim];
+            cc[a].col = static_cast<const uint32_t *>(ci_.ptr);
+            cc[a].type = (uint32_t)ci_.type;
             cc[a].m = (uint32_t)cols[a].cuts.size();
+            cc[a].pad = 0;
+            // search hint over [min, max] in kHintBuckets equal value buckets: bucket b
+            // starts at the number of cuts <= min + b * (max - min) / kHintBuckets; used
+            // when the cut points spread out enough for the walk to stay short
+            const std::vector<double> &cut = cols[a].cuts;
+            const double mn = bound_value(ci_.min_bits, ci_.type), mx = bound_value(ci_.max_bits, ci_.type);
+            const double range = mx - mn;
+            cc[a].base = 0.0f;
+            cc[a].scale = 0.0f;
+            cc[a].hint_off = 0;
+            if (std::isfinite(range) && range > 0 && cc[a].m > 8 &&
+                std::isfinite((float)(kHintBuckets / range)) && (float)(kHintBuckets / range) > 0.0f) {
+                std::vector<uint32_t> start(kHintBuckets);
+                uint32_t densest = 0;
+                for (uint32_t b = 0; b < kHintBuckets; ++b) {
+                    const double edge = mn + (double)b * range / kHintBuckets;
+                    start[b] = (uint32_t)(std::upper_bound(cut.begin(), cut.end(), edge) - cut.begin());
+                    if (b > 0)
+                        densest = std::max(densest, start[b] - start[b - 1]);
+                }
+                densest = std::max(densest, cc[a].m - start[kHintBuckets - 1]);
+                if (densest <= 6) {
+                    cc[a].base = (float)mn;
+                    cc[a].scale = (float)(kHintBuckets / range);
+                    hint[a].assign(kHintBuckets / 2, 0);
+                    for (uint32_t b = 0; b < kHintBuckets; ++b)
+                        hint[a][b >> 1] |= start[b] << ((b & 1) * 16);
+                }
+            }
+            if (!hint[a].empty()) {
+                cc[a].hint_off = w;
+                w += kHintBuckets / 2;
+            }
+        }
+        for (uint32_t a = 0; a < ncols; ++a) {
             cc[a].cut_off = w;
             w += cc[a].m;
         }
@@ -492,6 +665,8 @@ int shared_scan_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const
         plan.resize(img_off + img_words, 0);
         for (uint32_t a = 0; a < ncols; ++a) {
             std::memcpy(&plan[img_off + a * kColWords], &cc[a], sizeof(ChunkCol));
+            for (size_t i = 0; i < hint[a].size(); ++i)
+                plan[img_off + cc[a].hint_off + i] = hint[a][i];
             for (uint32_t i = 0; i < cc[a].m; ++i)
                 plan[img_off + cc[a].cut_off + i] = to_bits(cols[a].cuts[i], (int32_t)cc[a].type);
         }
@@ -527,8 +702,27 @@ int shared_scan_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const
         h.iv_off = iv_off;
     }
 
+    // ---- grid shape: enough warp units to fill the persistent grid (small tables get
+    // smaller units), at most kMaxUnitRows rows each
+    if (S.grid_pass == 0) {
+        int bps = 0;
+        const size_t smem = (size_t)kChunkImageWords * 4;
+        if (cudaFuncSetAttribute(mdrq_shared_pass_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess ||
+            cudaFuncSetAttribute(mdrq_shared_pass_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, mdrq_shared_pass_kernel<true>, kSharedThreads,
+                                                          smem) != cudaSuccess)
+            return cuda_status(cudaGetLastError());
+        S.grid_pass = t->sm_count * std::max(1, bps);
+        S.grid_scan = t->sm_count * 2;
+    }
+    const uint64_t want_units = (uint64_t)S.grid_pass * kSharedWarps * 4 / std::max<size_t>(1, chunks.size());
+    uint64_t unit_rows = (t->n + want_units - 1) / std::max<uint64_t>(1, want_units);
+    unit_rows = std::min<uint64_t>(kMaxUnitRows, std::max<uint64_t>(kMinUnitRows, (unit_rows + 31) & ~31ull));
+
     // ---- device buffers
-    const uint64_t n_units = (t->n + kUnitRows - 1) / kUnitRows;
+    const uint64_t n_units = (t->n + unit_rows - 1) / unit_rows;
     const size_t hdr_bytes = hdrs.size() * sizeof(ChunkHdr);
     const size_t plan_bytes = plan.size() * 4;
     const size_t live_bytes = (size_t)nlive * 4;
@@ -547,19 +741,6 @@ int shared_scan_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const
         st = grow_pinned((void **)&S.stage, &S.stage_cap, hdr_bytes + plan_bytes + live_bytes);
     if (st != MDRQ_OK)
         return st;
-    if (S.grid_pass == 0) {
-        int bps = 0;
-        const size_t smem = (size_t)kChunkImageWords * 4;
-        if (cudaFuncSetAttribute(mdrq_shared_pass_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess ||
-            cudaFuncSetAttribute(mdrq_shared_pass_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, mdrq_shared_pass_kernel<true>, kSharedThreads,
-                                                          smem) != cudaSuccess)
-            return cuda_status(cudaGetLastError());
-        S.grid_pass = t->sm_count * std::max(1, bps);
-        S.grid_scan = t->sm_count * 2;
-    }
     std::memcpy(S.stage, hdrs.data(), hdr_bytes);
     std::memcpy(S.stage + hdr_bytes, plan.data(), plan_bytes);
     for (uint32_t i = 0; i < nlive; ++i)
@@ -578,6 +759,7 @@ int shared_scan_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const
     p.nlive = nlive;
     p.n = t->n;
     p.n_units = n_units;
+    p.unit_rows = unit_rows;
     p.items = (uint64_t)hdrs.size() * ((n_units + kSharedWarps - 1) / kSharedWarps);
     p.counts = S.counts;
     p.totals = S.totals;

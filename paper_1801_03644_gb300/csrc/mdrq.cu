@@ -74,7 +74,8 @@ __global__ void mdrq_sample_kernel(const uint32_t *col, uint64_t n, uint32_t S, 
 
 namespace mdrq {
 
-constexpr size_t kAutoSharedMinQueries = 32;  // MDRQ_BATCH_AUTO: shared scan from this many
+constexpr size_t kAutoSharedMinQueries = 32;       // MDRQ_BATCH_AUTO: shared scan from this many
+constexpr uint64_t kAutoSharedMinRows = 4000000;   // queries, on tables of at least this many rows
 
 int cuda_status(cudaError_t e)
 {
@@ -399,7 +400,8 @@ int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, u
     MDRQ_TRY(cudaMemsetAsync(t->error, 0, sizeof(int), s));
 
     const bool shared = t->batch_mode == MDRQ_BATCH_SHARED ||
-                        (t->batch_mode == MDRQ_BATCH_AUTO && nlive >= kAutoSharedMinQueries);
+                        (t->batch_mode == MDRQ_BATCH_AUTO && nlive >= kAutoSharedMinQueries &&
+                         t->n >= kAutoSharedMinRows);
     if (shared) {
         cudaEvent_t *evp = nullptr;
         if (t->timing) {

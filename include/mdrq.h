@@ -185,6 +185,8 @@ int mdrq_scan_timing_read(mdrq_table *t, double *ms, uint64_t *scan_launches, ui
  *                     column is read once per group of up to 128 queries, and every
  *                     row's set of matching queries comes from per-column tables of the
  *                     queries' interval end points (two passes: count, then write).
+ *  MDRQ_BATCH_LEARNED every query scans only the rows its learned window allows (see
+ *                     mdrq_learn); MDRQ_E_INVAL without a model.
  *  MDRQ_BATCH_AUTO    (default) shared when the batch has at least 32 queries that need
  *                     a scan and the table at least 4,000,000 rows, plain otherwise.
  * Both modes return identical answers. The paper answers one query at a time (Sec.
@@ -194,7 +196,40 @@ int mdrq_scan_timing_read(mdrq_table *t, double *ms, uint64_t *scan_launches, ui
 #define MDRQ_BATCH_AUTO 0
 #define MDRQ_BATCH_PLAIN 1
 #define MDRQ_BATCH_SHARED 2
+#define MDRQ_BATCH_LEARNED 3 /* see mdrq_learn */
 int mdrq_set_batch_mode(mdrq_table *t, int mode);
+
+/*
+ * mdrq_learn — build a learned range narrower for MDRQ_BATCH_LEARNED; the paper has no
+ * learned component (its index structures are the R*-tree, kd-tree and VA-file, Sec.
+ * 2.2); this narrows the full scan of Sec. 2.2.4 to the rows a query can match.
+ *
+ * The table's rows must already be sorted by the 32-bit Z-order (Morton) key of the
+ * float32 columns dims[0 .. ndims) (1 <= ndims <= 4): with cell(x) = clamp(floor(x *
+ * 256), 0, 255) in float32, key bit 4b + j is bit b of cell(x_dims[j]). Every object in
+ * a query box then has a key between the keys of the box's corners, so it lies in one
+ * run of rows of the sorted table. The model predicts that run from the corner keys:
+ *  MDRQ_MODEL_PLA  piecewise-linear, 4096 segments through evenly spaced (key, row)
+ *                  pairs of the sorted keys, FP32;
+ *  MDRQ_MODEL_MLP  1-32-32-1 ReLU network, FP32, trained on the GPU (Adam, 3000 steps
+ *                  of 8192 pairs from a 2^20-pair sample).
+ * Its largest error over all n keys is measured exhaustively (mdrq_learn_info). A
+ * query's window is proven against the key column (widened until the keys just outside
+ * it lie outside the query's key range) before it is scanned with every predicate, so
+ * answers equal the full scan's whatever the model. Training and the key column (4
+ * bytes per row) stay with the table; calling again replaces the model.
+ *
+ * Errors: MDRQ_E_INVAL (bad dims or model, a dim that is not float32, n = 0, or rows not
+ * in key order); MDRQ_E_NOMEM; MDRQ_E_CUDA.
+ */
+#define MDRQ_MODEL_PLA 1
+#define MDRQ_MODEL_MLP 2
+int mdrq_learn(mdrq_table *t, const uint32_t *dims, uint32_t ndims, int model, void *stream);
+
+/* mdrq_learn_info — the model's largest position error over all keys, its PLA segment
+ * count (0 for the MLP) and the training time in ms. Any pointer may be NULL.
+ * Errors: MDRQ_E_INVAL (t NULL or no model). */
+int mdrq_learn_info(const mdrq_table *t, uint64_t *max_error, uint32_t *segments, double *train_ms);
 
 /*
  * mdrq_inject_fault — test hook for failure detection; the paper has no counterpart.

@@ -22,6 +22,12 @@ using namespace mdrq;
 
 namespace mdrq {
 
+// The scan over per-query row windows (the learned range narrower's exact check).
+__global__ void __launch_bounds__(kScanThreads, 7) mdrq_scan_window_kernel(const __grid_constant__ ScanParams p)
+{
+    scan_cta<4, true>(p);
+}
+
 // NaN count, minimum and maximum of a column. out[0] += NaNs; out[1] / out[2] hold the
 // minimum / maximum as order-preserving keys (see key_of).
 __device__ __forceinline__ unsigned long long key_of(uint32_t bits, uint32_t type)
@@ -256,6 +262,9 @@ int launch_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t scanned_column
         t->tag_next = 1;
     }
 
+    // every launch starts its tile claims from zero
+    MDRQ_TRY(cudaMemsetAsync(t->ticket, 0, sizeof(unsigned long long), s));
+
     ScanParams p;
     std::memset(&p, 0, sizeof(p));
     p.queries = t->dq_dev + q0;
@@ -268,7 +277,7 @@ int launch_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t scanned_column
     p.ring_bits = t->ring_bits;
     p.tag0 = t->tag_next;
     p.ticket = t->ticket;
-    p.ticket_base = t->ticket_next;
+    p.ticket_base = 0;
     p.ids = ids;
     p.capacity = capacity;
     p.base_in = base_in;
@@ -303,7 +312,6 @@ int launch_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t scanned_column
     MDRQ_TRY(cudaGetLastError());
     if (evp)
         MDRQ_TRY(cudaEventRecord(evp[1], s));
-    t->ticket_next += total_tiles + (uint64_t)kFailingClaimsPerCta * grid;
     t->tag_next += laps;
     t->last_launches += 1;
     t->last_bytes += scanned_columns * 4ull * t->n;
@@ -315,6 +323,52 @@ int launch_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t scanned_column
     return MDRQ_OK;
 }
 
+int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint32_t *ids, uint64_t capacity,
+                       const unsigned long long *base_in, const DevWindow *windows,
+                       const unsigned long long *total_tiles, cudaStream_t s)
+{
+    if (t->blocks_per_sm_window == 0) {
+        MDRQ_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->blocks_per_sm_window, mdrq_scan_window_kernel,
+                                                               kScanThreads, 0));
+        t->blocks_per_sm_window = std::max(1, t->blocks_per_sm_window);
+    }
+    // a window has at most one tile more than the whole table (its start is rounded down)
+    const uint64_t max_tiles = (uint64_t)nq * ((t->n + tile_rows<4>() - 1) / tile_rows<4>() + 1);
+    const uint32_t grid = (uint32_t)std::max<uint64_t>(
+        1, std::min<uint64_t>((uint64_t)t->sm_count * t->blocks_per_sm_window, max_tiles));
+    const uint32_t laps = (uint32_t)(max_tiles >> t->ring_bits) + 1;
+    if ((uint64_t)t->tag_next + laps > kTagLimit) {
+        MDRQ_TRY(cudaMemsetAsync(t->tile_state, 0, ((size_t)1 << t->ring_bits) * 8, s));
+        t->tag_next = 1;
+    }
+    MDRQ_TRY(cudaMemsetAsync(t->ticket, 0, sizeof(unsigned long long), s));
+    ScanParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.queries = t->dq_dev + q0;
+    p.preds = t->dp_dev;
+    p.nq = nq;
+    p.n = t->n;
+    p.tile_state = t->tile_state;
+    p.ring_bits = t->ring_bits;
+    p.tag0 = t->tag_next;
+    p.ticket = t->ticket;
+    p.ticket_base = 0;
+    p.ids = ids;
+    p.capacity = capacity;
+    p.base_in = base_in;
+    p.offsets = t->offsets_dev;
+    p.error = t->error;
+    p.windows = windows;
+    p.total_tiles_dev = total_tiles;
+    mdrq_scan_window_kernel<<<grid, kScanThreads, 0, s>>>(p);
+    MDRQ_TRY(cudaGetLastError());
+    t->tag_next += laps;
+    t->last_launches += 1;
+    if (t->timing)
+        t->acc_kernels += 3;  // window, tiles and scan kernels
+    return MDRQ_OK;
+}
+
 // After an error the claim counter and ring may be inconsistent: reset them.
 void reset_scratch(mdrq_table *t, cudaStream_t s)
 {
@@ -323,7 +377,6 @@ void reset_scratch(mdrq_table *t, cudaStream_t s)
     cudaMemset(t->scratch, 0, (size_t)(2 + ((size_t)1 << t->ring_bits)) * 8);
     cudaDeviceSynchronize();
     (void)cudaGetLastError();
-    t->ticket_next = 0;
     t->tag_next = 1;
 }
 
@@ -399,9 +452,25 @@ int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, u
     MDRQ_TRY(cudaMemsetAsync(t->offsets_dev, 0, ((size_t)nq + 1) * 8, s));
     MDRQ_TRY(cudaMemsetAsync(t->error, 0, sizeof(int), s));
 
-    const bool shared = t->batch_mode == MDRQ_BATCH_SHARED ||
+    if (t->batch_mode == MDRQ_BATCH_LEARNED) {
+        if (!t->learned)
+            return MDRQ_E_INVAL;
+        // windows and their scan, one launch per chunk whose ids fit the state values
+        const uint64_t per = std::max<uint64_t>(1, kValueMask / std::max<uint64_t>(1, t->n));
+        for (size_t c0 = 0; c0 < nlive; c0 += per) {
+            const uint32_t cnt = (uint32_t)std::min<uint64_t>(per, nlive - c0);
+            const unsigned long long *base = c0 == 0 ? nullptr : t->offsets_dev + live[c0 - 1] + 1;
+            st = learned_batch(t, enc, live, (uint32_t)c0, cnt, out, capacity, base, s);
+            if (st != MDRQ_OK) {
+                reset_scratch(t, s);
+                return st;
+            }
+        }
+    }
+    const bool learned_mode = t->batch_mode == MDRQ_BATCH_LEARNED;
+    const bool shared = !learned_mode && (t->batch_mode == MDRQ_BATCH_SHARED ||
                         (t->batch_mode == MDRQ_BATCH_AUTO && nlive >= kAutoSharedMinQueries &&
-                         t->n >= kAutoSharedMinRows);
+                         t->n >= kAutoSharedMinRows));
     if (shared) {
         cudaEvent_t *evp = nullptr;
         if (t->timing) {
@@ -426,7 +495,7 @@ int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, u
     }
     // one launch per chunk of queries whose ids fit the 40-bit state values
     const uint64_t per_launch = std::max<uint64_t>(1, kValueMask / std::max<uint64_t>(1, t->n));
-    for (size_t c0 = 0; !shared && c0 < nlive; c0 += per_launch) {
+    for (size_t c0 = 0; !shared && !learned_mode && c0 < nlive; c0 += per_launch) {
         const uint32_t cnt = (uint32_t)std::min<uint64_t>(per_launch, nlive - c0);
         uint64_t cols = 0;
         for (size_t i = c0; i < c0 + cnt; ++i)
@@ -484,6 +553,7 @@ void destroy(mdrq_table *t)
     cudaFree(t->scratch);
     cudaFree(t->offsets_dev);
     shared_scan_free(t);
+    learned_free(t);
     cudaFree(t->ids_stage);
     cudaFree(t->dq_dev);
     cudaFree(t->dp_dev);
@@ -701,10 +771,26 @@ int mdrq_scan_timing_read(mdrq_table *t, double *ms, uint64_t *scan_launches, ui
 
 int mdrq_set_batch_mode(mdrq_table *t, int mode)
 {
-    if (!t || (mode != MDRQ_BATCH_AUTO && mode != MDRQ_BATCH_PLAIN && mode != MDRQ_BATCH_SHARED))
+    if (!t || (mode != MDRQ_BATCH_AUTO && mode != MDRQ_BATCH_PLAIN && mode != MDRQ_BATCH_SHARED &&
+               mode != MDRQ_BATCH_LEARNED))
         return MDRQ_E_INVAL;
     t->batch_mode = mode;
     return MDRQ_OK;
+}
+
+int mdrq_learn(mdrq_table *t, const uint32_t *dims, uint32_t ndims, int model, void *stream)
+{
+    if (!t)
+        return MDRQ_E_INVAL;
+    const cudaError_t e = cudaSetDevice(t->device);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    return learn(t, dims, ndims, model, as_stream(stream));
+}
+
+int mdrq_learn_info(const mdrq_table *t, uint64_t *max_error, uint32_t *segments, double *train_ms)
+{
+    return learned_info(t, max_error, segments, train_ms);
 }
 
 int mdrq_inject_fault(mdrq_table *t, int kind, uint64_t arg)

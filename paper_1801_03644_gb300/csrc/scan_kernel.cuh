@@ -75,6 +75,15 @@ struct DevQuery {
     uint32_t pad;
 };
 
+// Windowed launches: the rows [row_begin, row_end) a query scans (row_begin a multiple
+// of 4) and its tiles [tile_start, tile_start + tiles) of the launch (tiles >= 1).
+struct DevWindow {
+    unsigned long long row_begin;
+    unsigned long long row_end;
+    unsigned long long tile_start;
+    unsigned long long tiles;
+};
+
 struct ScanParams {
     const DevQuery *queries;         // nq queries (device)
     const DevPred *preds;            // their predicates (device)
@@ -92,7 +101,56 @@ struct ScanParams {
     const unsigned long long *base_in;  // where this launch's output starts in ids
     unsigned long long *offsets;     // offsets[orig + 1] <- end of query orig's answer
     int *error;                      // error bits (kErr*)
+    const DevWindow *windows;        // windowed launches: per query rows and tiles (device)
+    const unsigned long long *total_tiles_dev;  // windowed launches: tile count (device)
 };
+
+// Where tile t of a launch lies: its query, its first row, the end of the rows it may
+// read, and whether it is the query's last tile.
+struct TilePlace {
+    uint32_t q;
+    bool last;
+    unsigned long long row0;
+    unsigned long long row_end;
+};
+
+template <bool WINDOWED>
+__device__ __forceinline__ uint32_t query_of_tile(const ScanParams &p, unsigned long long t)
+{
+    if (!WINDOWED)
+        return (uint32_t)(t / p.tiles_per_query);
+    // the last query whose first tile is <= t
+    uint32_t lo = 0, hi = p.nq;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (p.windows[mid].tile_start <= t)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+template <bool WINDOWED>
+__device__ __forceinline__ TilePlace place_tile(const ScanParams &p, unsigned long long t, uint32_t q,
+                                                uint32_t tile_rows)
+{
+    TilePlace tp;
+    tp.q = q;
+    if (WINDOWED) {
+        const DevWindow w = p.windows[q];
+        const unsigned long long rt = t - w.tile_start;
+        tp.row0 = w.row_begin + rt * tile_rows;
+        tp.row_end = w.row_end;
+        tp.last = rt == w.tiles - 1;
+    } else {
+        const unsigned long long rt = t - (unsigned long long)q * p.tiles_per_query;
+        tp.row0 = rt * tile_rows;
+        tp.row_end = p.n;
+        tp.last = rt == p.tiles_per_query - 1;
+    }
+    return tp;
+}
 
 __device__ __forceinline__ uint4 ld_stream_v4(const void *p)
 {
@@ -264,17 +322,13 @@ constexpr int kClaimSlots = kStages + 1;         // claimed-tile queue (see scan
 constexpr int kScanThreads = kBlock + 32;        // 8 filter warps + 1 output warp
 constexpr unsigned long long kStopTile = ~0ull;  // "no more tiles" marker
 
-// Claims every CTA makes past the last tile: the host advances its ticket base by
-// total_tiles + kFailingClaimsPerCta * grid per launch.
-constexpr int kFailingClaimsPerCta = 1;
-
 // The filter warps of a CTA run iterations 0, 1, 2, ... in lock-free step: iteration i
 // fills stage i % kStages with the tile held in claim slot i % kClaimSlots. The first
 // filter warp to start iteration i claims the tile of iteration i + 1, so a tile is
 // claimed about one tile before it is processed and tiles are finished close to claim
 // order, which keeps look-back waits short. Slot reuse is safe with kStages + 1 slots:
 // a warp can run at most kStages iterations ahead of the output warp.
-template <int U>
+template <int U, bool WINDOWED = false>
 __device__ __forceinline__ void scan_cta(const ScanParams &p)
 {
     static_assert(U >= 1 && U <= 4, "8-bit packed counts hold at most 4 groups");
@@ -289,14 +343,19 @@ __device__ __forceinline__ void scan_cta(const ScanParams &p)
     __shared__ uint32_t s_done[kStages];                  // filter warps finished with it
     __shared__ uint32_t s_first[kStages];                 // filter warps that started it
     __shared__ unsigned long long s_claim[kClaimSlots];   // claimed tile of an iteration
+    __shared__ uint32_t s_claim_q[kClaimSlots];           // ... and its query
+    __shared__ uint32_t s_stage_q[kStages];               // query of the stage's tile
     __shared__ unsigned long long s_ready[kStages], s_full[kStages], s_claimed[kClaimSlots];
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
 
-    auto claim = [&]() -> unsigned long long {
+    const unsigned long long total_tiles = WINDOWED ? *p.total_tiles_dev : p.total_tiles;
+    auto claim = [&](int slot) {
         const unsigned long long t = atomicAdd(p.ticket, 1ull) - p.ticket_base;
-        return t < p.total_tiles ? t : kStopTile;
+        const bool real = t < total_tiles;
+        s_claim[slot] = real ? t : kStopTile;
+        s_claim_q[slot] = real ? query_of_tile<WINDOWED>(p, t) : 0u;
     };
 
     if (threadIdx.x == 0) {
@@ -309,7 +368,7 @@ __device__ __forceinline__ void scan_cta(const ScanParams &p)
         for (int c = 0; c < kClaimSlots; ++c)
             mbar_init(&s_claimed[c], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_claim[0] = claim();  // the tile of iteration 0
+        claim(0);  // the tile of iteration 0
         mbar_arrive(&s_claimed[0]);
     }
     __syncthreads();
@@ -329,6 +388,7 @@ __device__ __forceinline__ void scan_cta(const ScanParams &p)
             const unsigned long long t = s_stage_tile[b];
             if (t == kStopTile)
                 break;
+            const TilePlace tp = place_tile<WINDOWED>(p, t, s_stage_q[b], kTileRows);
             // per-warp counts of the stage and their inclusive prefix
             const uint32_t wt = lane < kWarps ? s_warp_total[b][lane] : 0u;
             uint32_t wincl = wt;
@@ -340,11 +400,9 @@ __device__ __forceinline__ void scan_cta(const ScanParams &p)
             }
             const uint32_t total = __shfl_sync(0xffffffffu, wincl, kWarps - 1);
             const unsigned long long excl = t == 0 ? 0ull : tile_lookback(p, t, total, lane);
-            const uint32_t q = (uint32_t)(t / p.tiles_per_query);
-            const unsigned long long rt = t - (unsigned long long)q * p.tiles_per_query;
-            if (lane == 0 && rt == p.tiles_per_query - 1)
-                p.offsets[p.queries[q].orig + 1] = base + excl + total;
-            const uint32_t row0 = (uint32_t)(rt * (unsigned long long)kTileRows);
+            if (lane == 0 && tp.last)
+                p.offsets[p.queries[tp.q].orig + 1] = base + excl + total;
+            const uint32_t row0 = (uint32_t)tp.row0;
 #pragma unroll 1
             for (int w = 0; w < kWarps; ++w) {
                 const uint32_t cnt = __shfl_sync(0xffffffffu, wt, w);
@@ -380,17 +438,16 @@ __device__ __forceinline__ void scan_cta(const ScanParams &p)
         if (lane == 0 && t != kStopTile && atomicAdd(&s_first[b], 1u) == 0) {
             // first warp into this iteration: claim the next iteration's tile
             const int c1 = (it + 1) % kClaimSlots;
-            s_claim[c1] = claim();
+            claim(c1);
             mbar_arrive(&s_claimed[c1]);
         }
 
         uint32_t m = 0, ubase = 0;
         if (t != kStopTile) {
-            const uint32_t q = (uint32_t)(t / p.tiles_per_query);
-            const unsigned long long rt = t - (unsigned long long)q * p.tiles_per_query;
-            const DevQuery dq = p.queries[q];
-            const uint64_t row0 = rt * (uint64_t)kTileRows + (uint64_t)warp * kWarpRows;
-            const bool full = row0 + kWarpRows <= p.n;
+            const TilePlace tp = place_tile<WINDOWED>(p, t, s_claim_q[c], kTileRows);
+            const DevQuery dq = p.queries[tp.q];
+            const uint64_t row0 = tp.row0 + (uint64_t)warp * kWarpRows;
+            const bool full = row0 + kWarpRows <= tp.row_end;
 
             // bit 4u+e of m: row row0 + 128u + 4*lane + e still qualifies
             if (full) {
@@ -400,7 +457,7 @@ __device__ __forceinline__ void scan_cta(const ScanParams &p)
                 for (int u = 0; u < U; ++u)
 #pragma unroll
                     for (int e = 0; e < 4; ++e)
-                        if (row0 + 128u * u + 4u * lane + e < p.n)
+                        if (row0 + 128u * u + 4u * lane + e < tp.row_end)
                             m |= 1u << (4 * u + e);
             }
 
@@ -480,6 +537,7 @@ __device__ __forceinline__ void scan_cta(const ScanParams &p)
                                    pack_state(state_tag(p, t), t == 0 ? kFlagPrefix : kFlagAggregate, total));
                 }
                 s_stage_tile[b] = t;
+                s_stage_q[b] = s_claim_q[c];
                 s_done[b] = 0;
                 s_first[b] = 0;
             }
@@ -493,7 +551,8 @@ __device__ __forceinline__ void scan_cta(const ScanParams &p)
 template <int U>
 __global__ void __launch_bounds__(kScanThreads, 7) mdrq_scan_kernel(const __grid_constant__ ScanParams p)
 {
-    scan_cta<U>(p);
+    scan_cta<U, false>(p);
 }
+
 
 }  // namespace mdrq

@@ -30,6 +30,7 @@ struct EncodedQuery {
 };
 
 struct SharedScanState;  // device buffers of the batched shared scan (batched.cu)
+struct LearnedModel;     // learned range narrower (learned.cu)
 
 }  // namespace mdrq
 
@@ -46,7 +47,6 @@ struct mdrq_table {
     int *error = nullptr;
     unsigned long long *tile_state = nullptr;
     uint32_t ring_bits = 16;
-    unsigned long long ticket_next = 0;
     uint32_t tag_next = 1;  // tag of the next launch's first ring lap (0: cleared slot)
 
     // per-batch query tables: device copies and their pinned staging
@@ -67,6 +67,7 @@ struct mdrq_table {
 
     int sm_count = 0;
     int blocks_per_sm[3] = {0, 0, 0};  // for U = 1, 2, 4
+    int blocks_per_sm_window = 0;      // windowed scan
 
     uint64_t last_launches = 0;
     uint64_t last_bytes = 0;
@@ -80,6 +81,7 @@ struct mdrq_table {
     // batched shared scan (mdrq_set_batch_mode, batched.cu)
     int batch_mode = MDRQ_BATCH_AUTO;
     mdrq::SharedScanState *shared = nullptr;
+    mdrq::LearnedModel *learned = nullptr;
 
     // host-side fault injection for failure-detection tests (mdrq_inject_fault)
     uint64_t inject_skip_tiles = 0;  // next scan launch never claims its first tiles
@@ -109,5 +111,19 @@ int grow_pinned(void **p, size_t *cap, size_t bytes);
 int shared_scan_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std::vector<uint32_t> &live,
                       uint32_t *ids, uint64_t capacity, cudaStream_t s);
 void shared_scan_free(mdrq_table *t);
+
+// mdrq.cu: one windowed scan launch over nq live queries whose rows and tiles the device
+// holds in windows / total_tiles (written by earlier kernels on the same stream).
+int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint32_t *ids, uint64_t capacity,
+                       const unsigned long long *base_in, const DevWindow *windows,
+                       const unsigned long long *total_tiles, cudaStream_t s);
+
+// learned.cu
+int learn(mdrq_table *t, const uint32_t *dims, uint32_t ndims, int kind, cudaStream_t s);
+int learned_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std::vector<uint32_t> &live,
+                  uint32_t q0, uint32_t nlive, uint32_t *ids, uint64_t capacity, const unsigned long long *base_in,
+                  cudaStream_t s);
+int learned_info(const mdrq_table *t, uint64_t *max_error, uint32_t *segments, double *train_ms);
+void learned_free(mdrq_table *t);
 
 }  // namespace mdrq

@@ -43,10 +43,11 @@ _lib = None
 EXPORTS = ["mdrq_load_columns", "mdrq_query", "mdrq_query_batch", "mdrq_free",
            "mdrq_status_string", "mdrq_table_rows", "mdrq_table_dims", "mdrq_last_scan_stats",
            "mdrq_scan_timing", "mdrq_scan_timing_read", "mdrq_query_static",
-           "mdrq_inject_fault", "mdrq_set_batch_mode"]
+           "mdrq_inject_fault", "mdrq_set_batch_mode", "mdrq_learn", "mdrq_learn_info"]
 
 FAULT_SKIP_TILES, FAULT_NOMEM = 1, 2
-BATCH_AUTO, BATCH_PLAIN, BATCH_SHARED = 0, 1, 2
+BATCH_AUTO, BATCH_PLAIN, BATCH_SHARED, BATCH_LEARNED = 0, 1, 2, 3
+MODEL_PLA, MODEL_MLP = 1, 2
 
 STATIC_MAX_ROWS = 1 << 28  # MDRQ_STATIC_MAX_ROWS
 
@@ -83,6 +84,10 @@ def lib():
         L.mdrq_scan_timing_read.restype = ctypes.c_int
         L.mdrq_scan_timing_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64),
                                             ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.c_int]
+        L.mdrq_learn.restype = ctypes.c_int
+        L.mdrq_learn.argtypes = [vp, ctypes.POINTER(u32), u32, ctypes.c_int, vp]
+        L.mdrq_learn_info.restype = ctypes.c_int
+        L.mdrq_learn_info.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u32), ctypes.POINTER(ctypes.c_double)]
         L.mdrq_set_batch_mode.restype = ctypes.c_int
         L.mdrq_set_batch_mode.argtypes = [vp, ctypes.c_int]
         L.mdrq_inject_fault.restype = ctypes.c_int
@@ -303,6 +308,22 @@ class Table:
         if st != OK:
             raise MDRQError(st, "mdrq_query_batch")
         return out[: int(off[-1])], off
+
+    def learn(self, dims, model: int = MODEL_PLA, stream=None):
+        """``mdrq_learn``: a learned range narrower over the Z-order key of ``dims`` (the
+        rows must be sorted by that key). Returns ``learn_info()``."""
+        arr = (ctypes.c_uint32 * max(1, len(dims)))(*[int(j) for j in dims])
+        st = lib().mdrq_learn(self._h, arr, len(dims), int(model), _stream_handle(stream))
+        if st != OK:
+            raise MDRQError(st, "mdrq_learn")
+        return self.learn_info()
+
+    def learn_info(self) -> dict:
+        e, sg, ms = ctypes.c_uint64(0), ctypes.c_uint32(0), ctypes.c_double(0)
+        st = lib().mdrq_learn_info(self._h, ctypes.byref(e), ctypes.byref(sg), ctypes.byref(ms))
+        if st != OK:
+            raise MDRQError(st, "mdrq_learn_info")
+        return {"max_error": int(e.value), "segments": int(sg.value), "train_ms": ms.value}
 
     def set_batch_mode(self, mode: int):
         """``mdrq_set_batch_mode``: BATCH_AUTO, BATCH_PLAIN or BATCH_SHARED."""

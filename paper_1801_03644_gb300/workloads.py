@@ -248,6 +248,63 @@ def skewed_mixed_types(n: int = 50_000_000, nq: int = 256, sel_range=(1e-6, 0.5)
                     % (n, nq, sel_range[0], sel_range[1], 100 * empty_fraction))
 
 
+def zorder_cell(v: np.ndarray) -> np.ndarray:
+    """8-bit cell of a value for the Z-order layout: clamp(floor(v * 256), 0, 255)."""
+    c = np.floor(np.asarray(v, dtype=np.float32) * np.float32(256.0))
+    return np.clip(c, 0, 255).astype(np.uint32)
+
+
+def zorder_key(columns: list) -> np.ndarray:
+    """32-bit Morton key over up to 4 columns of values in [0, 1): bit 4b + j of the key
+    is bit b of column j's 8-bit cell (dimension 0 least significant in each nibble)."""
+    key = np.zeros(columns[0].shape[0], dtype=np.uint32)
+    for j, c in enumerate(columns):
+        cell = zorder_cell(c)
+        for b in range(8):
+            key |= ((cell >> np.uint32(b)) & np.uint32(1)) << np.uint32(4 * b + j)
+    return key
+
+
+def zorder_learned(n: int = 200_000_000, nq: int = 4096, sel_range=(1e-4, 0.05),
+                   chunk: int = 1 << 24) -> Workload:
+    """n x 4 float32: dims 0 and 2 uniform on [0,1); dims 1 and 3 lognormal(0, 1)
+    normalised to [0,1) by (y - min) / (max - min) and clipped to [0, 0.99999994]. Rows
+    are sorted (stably) by the 32-bit Z-order key of the 4 dims. Complete-match queries,
+    target selectivity log-uniform in ``sel_range``, s^(1/4) per dimension by quantile."""
+    rng = rng_for(4, 0)
+    cols = []
+    for j in range(4):
+        if j % 2 == 0:
+            cols.append(uniform_column(rng, n))
+        else:
+            y = np.empty(n, dtype=np.float64)
+            for a in range(0, n, chunk):
+                b = min(n, a + chunk)
+                y[a:b] = rng.lognormal(0.0, 1.0, size=b - a)
+            lo, hi = y.min(), y.max()
+            span = hi - lo if hi > lo else 1.0
+            x = ((y - lo) / span).astype(np.float32)
+            del y
+            np.clip(x, np.float32(0.0), np.float32(ONE_BELOW), out=x)
+            cols.append(x)
+    key = zorder_key(cols)
+    order = np.argsort(key, kind="stable")
+    del key
+    cols = [c[order] for c in cols]
+    del order
+    dtypes = [c.dtype for c in cols]
+    samples = quantile_samples(cols, rng_for(4, 2))
+    qrng = rng_for(4, 1)
+    qs = []
+    for _ in range(nq):
+        s = log_uniform(qrng, *sel_range)
+        qs.append(target_selectivity_query(samples, dtypes, [0, 1, 2, 3], s, qrng))
+    return Workload("zorder_%dx4_f32" % n, cols, qs,
+                    "n=%d d=4 f32 (2 U[0,1), 2 normalised lognormal(0,1)), rows sorted by the "
+                    "32-bit Z-order key; %d complete-match queries, target sel log-uniform "
+                    "[%g, %g]" % (n, nq, sel_range[0], sel_range[1]))
+
+
 def paper_uniform(n: int, d: int, nq: int, seed: int = 7) -> Workload:
     """SYNT-UNI (Sec. 7.2.1): n x d float32 uniform on [0,1), random-pair queries."""
     rng = rng_for(100 + seed, 0)

@@ -48,6 +48,8 @@ def make_workload(name: str, rows=None, queries=None):
         wl = W.uniform_small(**kw)
     elif name == "skewed_mixed":
         wl = W.skewed_mixed_types(**kw)
+    elif name == "zorder_learned":
+        wl = W.zorder_learned(**kw)
     else:
         raise SystemExit("unknown workload %s" % name)
     if queries:
@@ -298,6 +300,35 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
                    "answers_identical_to_plain": bool(int(off_b[-1]) == total_ids)}
         table.set_batch_mode(mdrq.BATCH_PLAIN)
 
+    # ---- learned range narrower (tables sorted by the Z-order key of their 4 columns)
+    learned = None
+    if args.workload == "zorder_learned":
+        learned = {}
+        for name, model in (("pla", mdrq.MODEL_PLA), ("mlp", mdrq.MODEL_MLP)):
+            info = table.learn([0, 1, 2, 3], model)
+            table.set_batch_mode(mdrq.BATCH_LEARNED)
+            for _ in range(args.warmup):
+                step()
+            torch.cuda.synchronize()
+            barrier()
+            l0 = torch.cuda.Event(enable_timing=True)
+            l1 = torch.cuda.Event(enable_timing=True)
+            l0.record(stream)
+            for _ in range(args.steps):
+                off_l = step()
+            l1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            lms = shards.max_over_ranks(l0.elapsed_time(l1))
+            rows, widen = table.learn_window_rows()
+            lvalue = world * nq * args.steps / (lms / 1e3)
+            learned[name] = {"value": lvalue, "unit": UNIT, "ms_per_step": lms / args.steps,
+                             "speedup_vs_plain": lvalue / value, "max_error_rows": info["max_error"],
+                             "segments": info["segments"], "train_ms": info["train_ms"],
+                             "window_rows_per_query": rows / nq, "window_widenings": widen,
+                             "answers_identical_to_plain": bool(int(off_l[-1]) == total_ids)}
+        table.set_batch_mode(mdrq.BATCH_PLAIN)
+
     # ---- end to end: host query descriptors in, host answers out (pinned)
     e2e = None
     if not args.no_e2e:
@@ -360,6 +391,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
             "config": cfg, "clocks": clocks, "e2e": e2e,
             "gpu_launches": timing["kernel_launches"], "roofline": roofline,
             "cpu_baseline": cpu, "answer_ids_per_step": total_ids, "batched": batched,
+            "learned": learned,
         }), flush=True)
     table.close()
 
@@ -371,7 +403,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="mixed_clustered",
-                    choices=["mixed_clustered", "uniform_1M", "skewed_mixed"])
+                    choices=["mixed_clustered", "uniform_1M", "skewed_mixed", "zorder_learned"])
     ap.add_argument("--rows", type=int, default=None,
                     help="smaller table of the same recipe (profiling cases)")
     ap.add_argument("--queries", type=int, default=None, help="first Q queries of the batch only")

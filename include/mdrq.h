@@ -231,6 +231,12 @@ int mdrq_learn(mdrq_table *t, const uint32_t *dims, uint32_t ndims, int model, v
  * Errors: MDRQ_E_INVAL (t NULL or no model). */
 int mdrq_learn_info(const mdrq_table *t, uint64_t *max_error, uint32_t *segments, double *train_ms);
 
+/* mdrq_learn_window_rows — measurement aid: rows the last MDRQ_BATCH_LEARNED call's
+ * windows covered (summed over its queries; of its last launch when the batch needed
+ * several) and how many widening steps the window checks took (0 when every model
+ * window already held its key run). Synchronous. Errors: MDRQ_E_INVAL (no model). */
+int mdrq_learn_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *widenings);
+
 /*
  * mdrq_inject_fault — test hook for failure detection; the paper has no counterpart.
  * Arms one fault for the next query call on this table:

@@ -67,6 +67,7 @@ struct LearnedModel {
     size_t qkeys_cap = 0;
     unsigned long long *total_tiles = nullptr;
     unsigned long long *scratch = nullptr;   // error / check words
+    size_t last_nq = 0;                      // queries of the last chunk's windows
 };
 
 // ---------------------------------------------------------------- keys
@@ -369,7 +370,7 @@ __device__ __forceinline__ unsigned long long lower_in(const uint32_t *keys, uns
 // range, found from the model's window after the window has been proven to contain
 // it; stored with its start rounded down to a multiple of 4 (128-bit loads).
 __global__ void __launch_bounds__(128) mdrq_window_kernel(ModelView mv, const uint32_t *keys, unsigned long long eps,
-                                                          const unsigned long long *qkeys, uint32_t nq,
+                                                          const unsigned long long *qkeys, uint32_t nw,
                                                           DevWindow *windows, unsigned long long *probe_count)
 {
     __shared__ float s_w[kMlpParams];
@@ -378,7 +379,7 @@ __global__ void __launch_bounds__(128) mdrq_window_kernel(ModelView mv, const ui
             s_w[i] = mv.mlp[i];
     __syncthreads();
     const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nq)
+    if (q >= nw)
         return;
     const unsigned long long zlo = qkeys[2 * q], zhi = qkeys[2 * q + 1];
     const long long n = (long long)mv.n;
@@ -400,8 +401,9 @@ __global__ void __launch_bounds__(128) mdrq_window_kernel(ModelView mv, const ui
     // the exact run inside the proven window
     const unsigned long long lb = lower_in(keys, (unsigned long long)w0, (unsigned long long)w1, zlo);
     const unsigned long long ub = upper_in(keys, lb, (unsigned long long)w1, zhi);
-    DevWindow w;
+    DevWindow w = windows[q];  // query and last were set by the host
     w.row_begin = lb & ~3ull;
+    w.row_first = lb;
     w.row_end = ub;
     w.tile_start = 0;
     w.tiles = 0;
@@ -410,7 +412,8 @@ __global__ void __launch_bounds__(128) mdrq_window_kernel(ModelView mv, const ui
         atomicAdd(probe_count, probes);
 }
 
-// tiles per query (at least 1) and their exclusive prefix; total into *total. One block.
+// tiles per window (at least 1 for a query's last window) and their exclusive prefix;
+// total into *total. One block.
 __global__ void __launch_bounds__(1024) mdrq_window_tiles_kernel(DevWindow *windows, uint32_t nq, uint32_t tile_rows,
                                                                  unsigned long long *total)
 {
@@ -424,8 +427,10 @@ __global__ void __launch_bounds__(1024) mdrq_window_tiles_kernel(DevWindow *wind
         const uint32_t i = base + threadIdx.x;
         unsigned long long v = 0;
         if (i < nq) {
-            const unsigned long long rows = windows[i].row_end - windows[i].row_begin;
-            v = rows ? (rows + tile_rows - 1) / tile_rows : 1;
+            // rows from the aligned start; none when the window holds no row
+            const unsigned long long rows =
+                windows[i].row_end > windows[i].row_first ? windows[i].row_end - windows[i].row_begin : 0;
+            v = rows ? (rows + tile_rows - 1) / tile_rows : (windows[i].last ? 1 : 0);
         }
         unsigned long long x = v;
         for (int o = 1; o < 32; o <<= 1) {
@@ -490,6 +495,86 @@ uint32_t host_key(const uint32_t *cells, uint32_t ndims)
         for (int b = 0; b < 8; ++b)
             k |= ((cells[j] >> b) & 1u) << (4 * b + j);
     return k;
+}
+
+constexpr uint32_t kRangesPerQuery = 64;  // budget of the box decomposition
+
+// The key ranges of a query box (cells clo..chi per key dimension): a descent of the
+// 2^ndims-ary tree whose level-L nodes fix the top L bits of every cell (each node is
+// one contiguous key range). Nodes inside the box are kept, nodes outside it dropped,
+// nodes crossing its border split, until the next level would exceed the range
+// budget; the crossing nodes left then are kept whole (they cover extra keys, which the
+// scan rejects). Ranges are returned sorted, adjacent ones merged.
+void box_ranges(const uint32_t *clo, const uint32_t *chi, uint32_t nd, std::vector<std::pair<uint64_t, uint64_t>> &out)
+{
+    struct Node {
+        uint32_t pre[4];
+    };
+    auto range_of = [&](const Node &nd_, uint32_t L, uint64_t &klo, uint64_t &khi) {
+        uint32_t a[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0};
+        for (uint32_t j = 0; j < nd; ++j) {
+            a[j] = nd_.pre[j] << (8 - L);
+            b[j] = a[j] | ((1u << (8 - L)) - 1u);
+        }
+        klo = host_key(a, nd);
+        khi = host_key(b, nd);
+    };
+    // 0: outside, 1: crossing, 2: inside
+    auto classify = [&](const Node &nd_, uint32_t L) {
+        bool inside = true;
+        for (uint32_t j = 0; j < nd; ++j) {
+            const uint32_t a = nd_.pre[j] << (8 - L), b = a | ((1u << (8 - L)) - 1u);
+            if (b < clo[j] || a > chi[j])
+                return 0;
+            inside = inside && a >= clo[j] && b <= chi[j];
+        }
+        return inside ? 2 : 1;
+    };
+    out.clear();
+    std::vector<Node> frontier(1, Node{{0, 0, 0, 0}}), next;
+    uint32_t L = 0;
+    if (classify(frontier[0], 0) == 2) {
+        frontier.clear();
+        uint64_t a, b;
+        range_of(Node{{0, 0, 0, 0}}, 0, a, b);
+        out.emplace_back(a, b);
+    }
+    while (!frontier.empty() && L < 8) {
+        if (out.size() + frontier.size() * (1u << nd) > kRangesPerQuery)
+            break;  // keep the crossing nodes whole
+        next.clear();
+        for (const Node &f : frontier) {
+            for (uint32_t c = 0; c < (1u << nd); ++c) {
+                Node ch;
+                for (uint32_t j = 0; j < 4; ++j)
+                    ch.pre[j] = j < nd ? (f.pre[j] << 1) | ((c >> j) & 1u) : 0;
+                const int cls = classify(ch, L + 1);
+                if (cls == 2) {
+                    uint64_t a, b;
+                    range_of(ch, L + 1, a, b);
+                    out.emplace_back(a, b);
+                } else if (cls == 1) {
+                    next.push_back(ch);
+                }
+            }
+        }
+        frontier.swap(next);
+        ++L;
+    }
+    for (const Node &f : frontier) {
+        uint64_t a, b;
+        range_of(f, L, a, b);
+        out.emplace_back(a, b);
+    }
+    std::sort(out.begin(), out.end());
+    size_t k = 0;
+    for (size_t i = 0; i < out.size(); ++i) {
+        if (k > 0 && out[i].first <= out[k - 1].second + 1)
+            out[k - 1].second = std::max(out[k - 1].second, out[i].second);
+        else
+            out[k++] = out[i];
+    }
+    out.resize(k);
 }
 
 }  // namespace
@@ -611,17 +696,14 @@ int learned_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std
         return MDRQ_E_INVAL;
     if (nlive == 0)
         return MDRQ_OK;
-    int st = grow_device((void **)&m->windows, &m->windows_cap, (size_t)nlive * sizeof(DevWindow));
-    if (st == MDRQ_OK)
-        st = grow_device((void **)&m->qkeys, &m->qkeys_cap, (size_t)nlive * 16);
-    if (st != MDRQ_OK)
-        return st;
-    // Z(lo), Z(hi) of each query: cells of its bounds on the key dimensions (the whole
-    // cell range where a key dimension is unconstrained)
-    std::vector<unsigned long long> qk(2 * (size_t)nlive);
+    // Z(lo), Z(hi) of each key range of each query's box: cells of its bounds on the key
+    // dimensions (the whole cell range where a key dimension is unconstrained)
+    std::vector<unsigned long long> qk;
+    std::vector<DevWindow> win;
+    std::vector<std::pair<uint64_t, uint64_t>> ranges;
     for (uint32_t i = 0; i < nlive; ++i) {
         const EncodedQuery &e = enc[live[q0 + i]];
-        uint32_t clo[4], chi[4];
+        uint32_t clo[4] = {0, 0, 0, 0}, chi[4] = {0, 0, 0, 0};
         for (uint32_t j = 0; j < m->ndims; ++j) {
             clo[j] = 0;
             chi[j] = 255;
@@ -635,18 +717,57 @@ int learned_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std
                 }
             }
         }
-        qk[2 * i] = host_key(clo, m->ndims);
-        qk[2 * i + 1] = host_key(chi, m->ndims);
+        box_ranges(clo, chi, m->ndims, ranges);
+        if (ranges.empty())
+            ranges.emplace_back(1, 0);  // no key can match: an empty window
+        for (size_t r = 0; r < ranges.size(); ++r) {
+            qk.push_back(ranges[r].first);
+            qk.push_back(ranges[r].second);
+            DevWindow w;
+            std::memset(&w, 0, sizeof(w));
+            w.query = i;
+            w.last = r + 1 == ranges.size();
+            win.push_back(w);
+        }
     }
+    const uint32_t nw = (uint32_t)win.size();
+    int st = grow_device((void **)&m->windows, &m->windows_cap, (size_t)nw * sizeof(DevWindow));
+    if (st == MDRQ_OK)
+        st = grow_device((void **)&m->qkeys, &m->qkeys_cap, (size_t)nw * 16);
+    if (st != MDRQ_OK)
+        return st;
     MDRQ_TRY_STATUS(cudaMemcpyAsync(m->qkeys, qk.data(), qk.size() * 8, cudaMemcpyHostToDevice, s));
+    MDRQ_TRY_STATUS(cudaMemcpyAsync(m->windows, win.data(), win.size() * sizeof(DevWindow), cudaMemcpyHostToDevice, s));
     MDRQ_TRY_STATUS(cudaMemsetAsync(m->scratch + 1, 0, 8, s));
+    m->last_nq = nw;
     const ModelView mv = view_of(*m, t->n);
-    mdrq_window_kernel<<<(nlive + 127) / 128, 128, 0, s>>>(mv, m->keys, m->max_error, m->qkeys, nlive, m->windows,
-                                                           m->scratch + 1);
+    mdrq_window_kernel<<<(nw + 127) / 128, 128, 0, s>>>(mv, m->keys, m->max_error, m->qkeys, nw, m->windows,
+                                                        m->scratch + 1);
     constexpr uint32_t kTile = (uint32_t)kWarps * 4 * 128;
-    mdrq_window_tiles_kernel<<<1, 1024, 0, s>>>(m->windows, nlive, kTile, m->total_tiles);
+    mdrq_window_tiles_kernel<<<1, 1024, 0, s>>>(m->windows, nw, kTile, m->total_tiles);
     MDRQ_TRY_STATUS(cudaGetLastError());
-    return launch_window_scan(t, q0, nlive, ids, capacity, base_in, m->windows, m->total_tiles, s);
+    return launch_window_scan(t, q0, nlive, nw, ids, capacity, base_in, m->windows, m->total_tiles, s);
+}
+
+int learned_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *probes)
+{
+    if (!t || !t->learned)
+        return MDRQ_E_INVAL;
+    LearnedModel &m = *t->learned;
+    const size_t nq = m.last_nq;
+    std::vector<DevWindow> w(nq);
+    unsigned long long pr = 0;
+    if (nq)
+        MDRQ_TRY_STATUS(cudaMemcpy(w.data(), m.windows, nq * sizeof(DevWindow), cudaMemcpyDeviceToHost));
+    MDRQ_TRY_STATUS(cudaMemcpy(&pr, m.scratch + 1, 8, cudaMemcpyDeviceToHost));
+    uint64_t sum = 0;
+    for (const DevWindow &x : w)
+        sum += x.row_end - x.row_first;
+    if (rows)
+        *rows = sum;
+    if (probes)
+        *probes = pr;
+    return MDRQ_OK;
 }
 
 int learned_info(const mdrq_table *t, uint64_t *max_error, uint32_t *segments, double *train_ms)

@@ -323,7 +323,7 @@ int launch_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t scanned_column
     return MDRQ_OK;
 }
 
-int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint32_t *ids, uint64_t capacity,
+int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint32_t nwindows, uint32_t *ids, uint64_t capacity,
                        const unsigned long long *base_in, const DevWindow *windows,
                        const unsigned long long *total_tiles, cudaStream_t s)
 {
@@ -332,8 +332,9 @@ int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint32_t *ids, u
                                                                kScanThreads, 0));
         t->blocks_per_sm_window = std::max(1, t->blocks_per_sm_window);
     }
-    // a window has at most one tile more than the whole table (its start is rounded down)
-    const uint64_t max_tiles = (uint64_t)nq * ((t->n + tile_rows<4>() - 1) / tile_rows<4>() + 1);
+    // a query's windows are disjoint runs of the table; each adds at most one partial
+    // tile (its start is rounded down)
+    const uint64_t max_tiles = (uint64_t)nq * ((t->n + tile_rows<4>() - 1) / tile_rows<4>()) + nwindows;
     const uint32_t grid = (uint32_t)std::max<uint64_t>(
         1, std::min<uint64_t>((uint64_t)t->sm_count * t->blocks_per_sm_window, max_tiles));
     const uint32_t laps = (uint32_t)(max_tiles >> t->ring_bits) + 1;
@@ -359,6 +360,7 @@ int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint32_t *ids, u
     p.offsets = t->offsets_dev;
     p.error = t->error;
     p.windows = windows;
+    p.nwindows = nwindows;
     p.total_tiles_dev = total_tiles;
     mdrq_scan_window_kernel<<<grid, kScanThreads, 0, s>>>(p);
     MDRQ_TRY(cudaGetLastError());
@@ -791,6 +793,11 @@ int mdrq_learn(mdrq_table *t, const uint32_t *dims, uint32_t ndims, int model, v
 int mdrq_learn_info(const mdrq_table *t, uint64_t *max_error, uint32_t *segments, double *train_ms)
 {
     return learned_info(t, max_error, segments, train_ms);
+}
+
+int mdrq_learn_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *widenings)
+{
+    return learned_window_rows(t, rows, widenings);
 }
 
 int mdrq_inject_fault(mdrq_table *t, int kind, uint64_t arg)

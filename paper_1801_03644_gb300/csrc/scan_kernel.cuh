@@ -75,13 +75,18 @@ struct DevQuery {
     uint32_t pad;
 };
 
-// Windowed launches: the rows [row_begin, row_end) a query scans (row_begin a multiple
-// of 4) and its tiles [tile_start, tile_start + tiles) of the launch (tiles >= 1).
+// Windowed launches: a run of rows [row_begin, row_end) (row_begin a multiple of 4) that
+// query `query` of the launch scans, and its tiles [tile_start, tile_start + tiles). A
+// query may have several windows, in ascending row order; the one flagged `last` has at
+// least one tile (its last tile writes the query's CSR end), the others may have none.
 struct DevWindow {
-    unsigned long long row_begin;
+    unsigned long long row_begin;  // first row, rounded down to a multiple of 4
+    unsigned long long row_first;  // first row (rows before it belong to no window here)
     unsigned long long row_end;
     unsigned long long tile_start;
     unsigned long long tiles;
+    uint32_t query;
+    uint32_t last;
 };
 
 struct ScanParams {
@@ -101,7 +106,8 @@ struct ScanParams {
     const unsigned long long *base_in;  // where this launch's output starts in ids
     unsigned long long *offsets;     // offsets[orig + 1] <- end of query orig's answer
     int *error;                      // error bits (kErr*)
-    const DevWindow *windows;        // windowed launches: per query rows and tiles (device)
+    const DevWindow *windows;        // windowed launches: row runs and their tiles (device)
+    uint32_t nwindows;               // windowed launches: number of windows
     const unsigned long long *total_tiles_dev;  // windowed launches: tile count (device)
 };
 
@@ -111,16 +117,19 @@ struct TilePlace {
     uint32_t q;
     bool last;
     unsigned long long row0;
+    unsigned long long row_first;  // rows in [row_first, row_end) belong to the tile's query
     unsigned long long row_end;
 };
 
+// WINDOWED = false: the query of tile t; true: the window of tile t.
 template <bool WINDOWED>
 __device__ __forceinline__ uint32_t query_of_tile(const ScanParams &p, unsigned long long t)
 {
     if (!WINDOWED)
         return (uint32_t)(t / p.tiles_per_query);
-    // the last query whose first tile is <= t
-    uint32_t lo = 0, hi = p.nq;
+    // the last window whose first tile is <= t (windows without tiles share the first
+    // tile of the next window and come before it, so they are never chosen)
+    uint32_t lo = 0, hi = p.nwindows;
     while (hi - lo > 1) {
         const uint32_t mid = (lo + hi) >> 1;
         if (p.windows[mid].tile_start <= t)
@@ -138,14 +147,17 @@ __device__ __forceinline__ TilePlace place_tile(const ScanParams &p, unsigned lo
     TilePlace tp;
     tp.q = q;
     if (WINDOWED) {
-        const DevWindow w = p.windows[q];
+        const DevWindow w = p.windows[q];  // q is the window here
         const unsigned long long rt = t - w.tile_start;
+        tp.q = w.query;
         tp.row0 = w.row_begin + rt * tile_rows;
+        tp.row_first = w.row_first;
         tp.row_end = w.row_end;
-        tp.last = rt == w.tiles - 1;
+        tp.last = w.last && rt == w.tiles - 1;
     } else {
         const unsigned long long rt = t - (unsigned long long)q * p.tiles_per_query;
         tp.row0 = rt * tile_rows;
+        tp.row_first = 0;
         tp.row_end = p.n;
         tp.last = rt == p.tiles_per_query - 1;
     }
@@ -447,7 +459,7 @@ __device__ __forceinline__ void scan_cta(const ScanParams &p)
             const TilePlace tp = place_tile<WINDOWED>(p, t, s_claim_q[c], kTileRows);
             const DevQuery dq = p.queries[tp.q];
             const uint64_t row0 = tp.row0 + (uint64_t)warp * kWarpRows;
-            const bool full = row0 + kWarpRows <= tp.row_end;
+            const bool full = row0 + kWarpRows <= tp.row_end && (!WINDOWED || row0 >= tp.row_first);
 
             // bit 4u+e of m: row row0 + 128u + 4*lane + e still qualifies
             if (full) {
@@ -457,7 +469,8 @@ __device__ __forceinline__ void scan_cta(const ScanParams &p)
                 for (int u = 0; u < U; ++u)
 #pragma unroll
                     for (int e = 0; e < 4; ++e)
-                        if (row0 + 128u * u + 4u * lane + e < tp.row_end)
+                        if (row0 + 128u * u + 4u * lane + e < tp.row_end &&
+                            (!WINDOWED || row0 + 128u * u + 4u * lane + e >= tp.row_first))
                             m |= 1u << (4 * u + e);
             }
 

@@ -114,7 +114,7 @@ void shared_scan_free(mdrq_table *t);
 
 // mdrq.cu: one windowed scan launch over nq live queries whose rows and tiles the device
 // holds in windows / total_tiles (written by earlier kernels on the same stream).
-int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint32_t *ids, uint64_t capacity,
+int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint32_t nwindows, uint32_t *ids, uint64_t capacity,
                        const unsigned long long *base_in, const DevWindow *windows,
                        const unsigned long long *total_tiles, cudaStream_t s);
 
@@ -125,5 +125,6 @@ int learned_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std
                   cudaStream_t s);
 int learned_info(const mdrq_table *t, uint64_t *max_error, uint32_t *segments, double *train_ms);
 void learned_free(mdrq_table *t);
+int learned_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *probes);
 
 }  // namespace mdrq

@@ -43,7 +43,8 @@ _lib = None
 EXPORTS = ["mdrq_load_columns", "mdrq_query", "mdrq_query_batch", "mdrq_free",
            "mdrq_status_string", "mdrq_table_rows", "mdrq_table_dims", "mdrq_last_scan_stats",
            "mdrq_scan_timing", "mdrq_scan_timing_read", "mdrq_query_static",
-           "mdrq_inject_fault", "mdrq_set_batch_mode", "mdrq_learn", "mdrq_learn_info"]
+           "mdrq_inject_fault", "mdrq_set_batch_mode", "mdrq_learn", "mdrq_learn_info",
+           "mdrq_learn_window_rows"]
 
 FAULT_SKIP_TILES, FAULT_NOMEM = 1, 2
 BATCH_AUTO, BATCH_PLAIN, BATCH_SHARED, BATCH_LEARNED = 0, 1, 2, 3
@@ -88,6 +89,8 @@ def lib():
         L.mdrq_learn.argtypes = [vp, ctypes.POINTER(u32), u32, ctypes.c_int, vp]
         L.mdrq_learn_info.restype = ctypes.c_int
         L.mdrq_learn_info.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u32), ctypes.POINTER(ctypes.c_double)]
+        L.mdrq_learn_window_rows.restype = ctypes.c_int
+        L.mdrq_learn_window_rows.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]
         L.mdrq_set_batch_mode.restype = ctypes.c_int
         L.mdrq_set_batch_mode.argtypes = [vp, ctypes.c_int]
         L.mdrq_inject_fault.restype = ctypes.c_int
@@ -324,6 +327,14 @@ class Table:
         if st != OK:
             raise MDRQError(st, "mdrq_learn_info")
         return {"max_error": int(e.value), "segments": int(sg.value), "train_ms": ms.value}
+
+    def learn_window_rows(self) -> tuple:
+        """(rows the last learned batch's windows covered, widening steps taken)."""
+        r, w = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        st = lib().mdrq_learn_window_rows(self._h, ctypes.byref(r), ctypes.byref(w))
+        if st != OK:
+            raise MDRQError(st, "mdrq_learn_window_rows")
+        return int(r.value), int(w.value)
 
     def set_batch_mode(self, mode: int):
         """``mdrq_set_batch_mode``: BATCH_AUTO, BATCH_PLAIN or BATCH_SHARED."""

@@ -28,6 +28,7 @@
 #include <cstdint>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "mdrq.h"
@@ -497,75 +498,96 @@ uint32_t host_key(const uint32_t *cells, uint32_t ndims)
     return k;
 }
 
-constexpr uint32_t kRangesPerQuery = 64;  // budget of the box decomposition
+constexpr uint32_t kRangesPerQuery = 1024;  // budget of the box decomposition
 
-// The key ranges of a query box (cells clo..chi per key dimension): a descent of the
-// 2^ndims-ary tree whose level-L nodes fix the top L bits of every cell (each node is
-// one contiguous key range). Nodes inside the box are kept, nodes outside it dropped,
-// nodes crossing its border split, until the next level would exceed the range
-// budget; the crossing nodes left then are kept whole (they cover extra keys, which the
-// scan rejects). Ranges are returned sorted, adjacent ones merged.
+// The key ranges of a query box (cells clo..chi per key dimension). A node is a run of
+// keys sharing their top `len` bits (len 0: all keys); its points' cells are fixed in
+// the bits that prefix covers, so its cell extent per dimension is an interval. Nodes
+// crossing the box's border are split in two by their next key bit, the shortest
+// prefixes (largest runs) first; halves inside the box become ranges, halves outside it
+// are dropped. When the budget is reached the crossing nodes left are kept whole (they
+// cover keys outside the box, which the scan rejects). Ranges are returned sorted,
+// adjacent ones merged.
 void box_ranges(const uint32_t *clo, const uint32_t *chi, uint32_t nd, std::vector<std::pair<uint64_t, uint64_t>> &out)
 {
-    struct Node {
-        uint32_t pre[4];
+    const uint32_t bits = 8 * nd;  // key bits in use: bit 4b + j for j < nd
+    // key bit position of the i-th most significant bit in use
+    auto bit_at = [&](uint32_t i) {
+        const uint32_t b = 7 - i / nd, j = (nd - 1) - i % nd;
+        return 4 * b + j;
     };
-    auto range_of = [&](const Node &nd_, uint32_t L, uint64_t &klo, uint64_t &khi) {
-        uint32_t a[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0};
-        for (uint32_t j = 0; j < nd; ++j) {
-            a[j] = nd_.pre[j] << (8 - L);
-            b[j] = a[j] | ((1u << (8 - L)) - 1u);
-        }
-        klo = host_key(a, nd);
-        khi = host_key(b, nd);
+    struct Node {
+        uint32_t len;      // bits fixed
+        uint32_t lo[4];    // cell extent of the node per dimension
+        uint32_t hi[4];
+        uint32_t key;      // the fixed bits (others 0)
     };
     // 0: outside, 1: crossing, 2: inside
-    auto classify = [&](const Node &nd_, uint32_t L) {
+    auto classify = [&](const Node &x) {
         bool inside = true;
         for (uint32_t j = 0; j < nd; ++j) {
-            const uint32_t a = nd_.pre[j] << (8 - L), b = a | ((1u << (8 - L)) - 1u);
-            if (b < clo[j] || a > chi[j])
+            if (x.hi[j] < clo[j] || x.lo[j] > chi[j])
                 return 0;
-            inside = inside && a >= clo[j] && b <= chi[j];
+            inside = inside && x.lo[j] >= clo[j] && x.hi[j] <= chi[j];
         }
         return inside ? 2 : 1;
     };
+    // the node's key run: its fixed bits, then all zeros / all ones in the free used bits
+    auto emit = [&](const Node &x) {
+        uint64_t hi = x.key;
+        for (uint32_t i = x.len; i < bits; ++i)
+            hi |= 1ull << bit_at(i);
+        out.emplace_back((uint64_t)x.key, hi);
+    };
     out.clear();
-    std::vector<Node> frontier(1, Node{{0, 0, 0, 0}}), next;
-    uint32_t L = 0;
-    if (classify(frontier[0], 0) == 2) {
-        frontier.clear();
-        uint64_t a, b;
-        range_of(Node{{0, 0, 0, 0}}, 0, a, b);
-        out.emplace_back(a, b);
+    thread_local std::vector<Node> pending[33];  // reused: no allocation after warm-up
+    for (auto &v : pending)
+        v.clear();
+    size_t npending = 0;
+    Node root;
+    root.len = 0;
+    root.key = 0;
+    for (uint32_t j = 0; j < 4; ++j) {
+        root.lo[j] = 0;
+        root.hi[j] = 255;
     }
-    while (!frontier.empty() && L < 8) {
-        if (out.size() + frontier.size() * (1u << nd) > kRangesPerQuery)
-            break;  // keep the crossing nodes whole
-        next.clear();
-        for (const Node &f : frontier) {
-            for (uint32_t c = 0; c < (1u << nd); ++c) {
-                Node ch;
-                for (uint32_t j = 0; j < 4; ++j)
-                    ch.pre[j] = j < nd ? (f.pre[j] << 1) | ((c >> j) & 1u) : 0;
-                const int cls = classify(ch, L + 1);
-                if (cls == 2) {
-                    uint64_t a, b;
-                    range_of(ch, L + 1, a, b);
-                    out.emplace_back(a, b);
-                } else if (cls == 1) {
-                    next.push_back(ch);
+    if (classify(root) == 2) {
+        emit(root);
+    } else {
+        pending[0].push_back(root);
+        npending = 1;
+    }
+    for (uint32_t len = 0; len < bits; ++len) {
+        while (!pending[len].empty() && out.size() + npending + 1 <= kRangesPerQuery) {
+            const Node f = pending[len].back();
+            pending[len].pop_back();
+            --npending;
+            const uint32_t pos = bit_at(len);
+            const uint32_t j = pos % 4, b = pos / 4;  // the split halves dimension j's cell range
+            for (uint32_t half = 0; half < 2; ++half) {
+                Node ch = f;
+                ch.len = len + 1;
+                ch.key = f.key | (half << pos);
+                const uint32_t mid = f.lo[j] + (1u << b);  // first cell of the upper half
+                if (half)
+                    ch.lo[j] = mid;
+                else
+                    ch.hi[j] = mid - 1;
+                const int cls = classify(ch);
+                if (cls == 2)
+                    emit(ch);
+                else if (cls == 1) {
+                    pending[len + 1].push_back(ch);
+                    ++npending;
                 }
             }
         }
-        frontier.swap(next);
-        ++L;
+        if (!pending[len].empty())
+            break;  // budget reached
     }
-    for (const Node &f : frontier) {
-        uint64_t a, b;
-        range_of(f, L, a, b);
-        out.emplace_back(a, b);
-    }
+    for (uint32_t len = 0; len <= bits; ++len)
+        for (const Node &f : pending[len])
+            emit(f);
     std::sort(out.begin(), out.end());
     size_t k = 0;
     for (size_t i = 0; i < out.size(); ++i) {
@@ -698,10 +720,10 @@ int learned_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std
         return MDRQ_OK;
     // Z(lo), Z(hi) of each key range of each query's box: cells of its bounds on the key
     // dimensions (the whole cell range where a key dimension is unconstrained)
-    std::vector<unsigned long long> qk;
-    std::vector<DevWindow> win;
-    std::vector<std::pair<uint64_t, uint64_t>> ranges;
-    for (uint32_t i = 0; i < nlive; ++i) {
+    // the decompositions of the queries run on the host threads, then are concatenated
+    // in query order
+    std::vector<std::vector<std::pair<uint64_t, uint64_t>>> per_query(nlive);
+    auto decompose = [&](uint32_t i) {
         const EncodedQuery &e = enc[live[q0 + i]];
         uint32_t clo[4] = {0, 0, 0, 0}, chi[4] = {0, 0, 0, 0};
         for (uint32_t j = 0; j < m->ndims; ++j) {
@@ -717,9 +739,29 @@ int learned_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std
                 }
             }
         }
-        box_ranges(clo, chi, m->ndims, ranges);
-        if (ranges.empty())
-            ranges.emplace_back(1, 0);  // no key can match: an empty window
+        box_ranges(clo, chi, m->ndims, per_query[i]);
+        if (per_query[i].empty())
+            per_query[i].emplace_back(1, 0);  // no key can match: an empty window
+    };
+    const uint32_t nthreads =
+        std::max(1u, std::min<uint32_t>(std::thread::hardware_concurrency(), (nlive + 63) / 64));
+    if (nthreads <= 1) {
+        for (uint32_t i = 0; i < nlive; ++i)
+            decompose(i);
+    } else {
+        std::vector<std::thread> pool;
+        for (uint32_t w = 0; w < nthreads; ++w)
+            pool.emplace_back([&, w]() {
+                for (uint32_t i = w; i < nlive; i += nthreads)
+                    decompose(i);
+            });
+        for (std::thread &th : pool)
+            th.join();
+    }
+    std::vector<unsigned long long> qk;
+    std::vector<DevWindow> win;
+    for (uint32_t i = 0; i < nlive; ++i) {
+        const std::vector<std::pair<uint64_t, uint64_t>> &ranges = per_query[i];
         for (size_t r = 0; r < ranges.size(); ++r) {
             qk.push_back(ranges[r].first);
             qk.push_back(ranges[r].second);

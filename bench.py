@@ -204,6 +204,128 @@ def run_reference(args, rank: int, world: int) -> None:
 
 # ----------------------------------------------------------------------------- GPU arm
 
+def timed_steps(torch, stream, step, steps, barrier):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    last = None
+    for _ in range(steps):
+        last = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    return e0.elapsed_time(e1), last
+
+
+def learned_leg(args, table, enc, step, plain_value, nq, total_ids, world, barrier, stream):
+    """Learned range narrower (PLA and MLP) on a Z-sorted table: queries/s, speedup over
+    the plain scan of the same batch, model error and window coverage."""
+    import torch
+    from paper_1801_03644_gb300 import mdrq, shards
+    out = {}
+    for name, model in (("pla", mdrq.MODEL_PLA), ("mlp", mdrq.MODEL_MLP)):
+        info = table.learn([0, 1, 2, 3], model)
+        table.set_batch_mode(mdrq.BATCH_LEARNED)
+        for _ in range(args.warmup):
+            step()
+        lms, off_l = timed_steps(torch, stream, step, args.steps, barrier)
+        lms = shards.max_over_ranks(lms)
+        rows, widen = table.learn_window_rows()
+        lvalue = world * nq * args.steps / (lms / 1e3)
+        out[name] = {"value": lvalue, "unit": UNIT, "ms_per_step": lms / args.steps,
+                     "speedup_vs_plain": lvalue / plain_value, "max_error_rows": info["max_error"],
+                     "segments": info["segments"], "train_ms": info["train_ms"],
+                     "window_rows_per_query": rows / nq, "window_widenings": widen,
+                     "answers_identical_to_plain": bool(int(off_l[-1]) == total_ids)}
+    table.set_batch_mode(mdrq.BATCH_PLAIN)
+    return out
+
+
+def learned_workload_leg(args, world, barrier):
+    """The learned narrower on the 2e8 x 4 Z-sorted table with 4096 queries, against
+    the plain scan of the same batch."""
+    import torch
+    from paper_1801_03644_gb300 import mdrq, shards
+    wl = make_workload("zorder_learned", args.learned_rows)
+    stream = torch.cuda.current_stream()
+    table = mdrq.Table(wl.columns)
+    table.set_batch_mode(mdrq.BATCH_PLAIN)
+    enc = table.encode_batch(wl.queries)
+    probe = torch.empty(1, dtype=torch.int32, device="cuda")
+    st, off = table.query_batch_raw(enc, probe.data_ptr(), 0, True)
+    total = int(off[-1])
+    ids = torch.empty(max(1, total), dtype=torch.int32, device="cuda")
+
+    def step():
+        st, o = table.query_batch_raw(enc, ids.data_ptr(), ids.numel(), True)
+        if st != mdrq.OK:
+            raise mdrq.MDRQError(st, "mdrq_query_batch")
+        return o
+
+    nq = len(wl.queries)
+    for _ in range(args.warmup):
+        step()
+    ms, _ = timed_steps(torch, stream, step, args.steps, barrier)
+    ms = shards.max_over_ranks(ms)
+    plain = world * nq * args.steps / (ms / 1e3)
+    res = {"workload": wl.name, "recipe": wl.recipe, "plain_value": plain, "unit": UNIT,
+           "plain_ms_per_step": ms / args.steps, "answer_ids_per_step": total}
+    res.update(learned_leg(args, table, enc, step, plain, nq, total, world, barrier, stream))
+    table.close()
+    return res
+
+
+def serving_leg(args):
+    """Open-loop Poisson arrivals into the continuous-batching server on the 2e7 x 16
+    table: per arrival rate, throughput and p50 / p99 latency (submit to answer)."""
+    import threading
+    import torch
+    from paper_1801_03644_gb300 import mdrq
+    wl = W.serving_table(n=args.serving_rows, nq=20_000)
+    table = mdrq.Table(wl.columns)
+    pre = [(mdrq.encode_query(q, table.dtypes), len(q)) for q in wl.queries]
+    rows = []
+    for rate in args.serving_rates:
+        count = int(min(len(pre), max(500, rate * args.serving_seconds)))
+        arrivals = W.poisson_arrivals(rate, count, seed=int(rate))
+        srv = mdrq.Server(table, result_bytes=2 << 30, max_batch=512)
+        tickets = [None] * count
+        lat = [0.0] * count
+        state = {"last": None}
+
+        def consumer():
+            for i in range(count):
+                while tickets[i] is None:
+                    time.sleep(2e-5)
+                st, ids, cnt, l = srv.wait(tickets[i])
+                lat[i] = l
+                srv.release(tickets[i])
+            state["last"] = time.perf_counter()
+
+        th = threading.Thread(target=consumer)
+        th.start()
+        t0 = time.perf_counter()
+        for i in range(count):
+            wait = arrivals[i] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            tickets[i] = srv.submit_encoded(*pre[i])
+        th.join()
+        span = state["last"] - t0
+        stats = srv.stats()
+        srv.stop()
+        l_sorted = sorted(lat)
+        rows.append({"offered_qps": rate, "queries": count, "throughput_qps": count / span,
+                     "p50_ms": l_sorted[len(l_sorted) // 2] / 1e3,
+                     "p99_ms": l_sorted[min(count - 1, int(0.99 * (count - 1) + 0.5))] / 1e3,
+                     "batches": stats["batches"], "deferred": stats["deferred"]})
+    table.close()
+    return {"workload": wl.name, "recipe": wl.recipe, "result_memory_cap_bytes": 2 << 30,
+            "arrivals": "open-loop Poisson", "rates": rows}
+
+
 def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     import torch
     import torch.distributed as dist
@@ -300,34 +422,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
                    "answers_identical_to_plain": bool(int(off_b[-1]) == total_ids)}
         table.set_batch_mode(mdrq.BATCH_PLAIN)
 
-    # ---- learned range narrower (tables sorted by the Z-order key of their 4 columns)
+    # ---- learned range narrower: on this table when it is Z-sorted, else on its own
     learned = None
     if args.workload == "zorder_learned":
-        learned = {}
-        for name, model in (("pla", mdrq.MODEL_PLA), ("mlp", mdrq.MODEL_MLP)):
-            info = table.learn([0, 1, 2, 3], model)
-            table.set_batch_mode(mdrq.BATCH_LEARNED)
-            for _ in range(args.warmup):
-                step()
-            torch.cuda.synchronize()
-            barrier()
-            l0 = torch.cuda.Event(enable_timing=True)
-            l1 = torch.cuda.Event(enable_timing=True)
-            l0.record(stream)
-            for _ in range(args.steps):
-                off_l = step()
-            l1.record(stream)
-            torch.cuda.synchronize()
-            barrier()
-            lms = shards.max_over_ranks(l0.elapsed_time(l1))
-            rows, widen = table.learn_window_rows()
-            lvalue = world * nq * args.steps / (lms / 1e3)
-            learned[name] = {"value": lvalue, "unit": UNIT, "ms_per_step": lms / args.steps,
-                             "speedup_vs_plain": lvalue / value, "max_error_rows": info["max_error"],
-                             "segments": info["segments"], "train_ms": info["train_ms"],
-                             "window_rows_per_query": rows / nq, "window_widenings": widen,
-                             "answers_identical_to_plain": bool(int(off_l[-1]) == total_ids)}
-        table.set_batch_mode(mdrq.BATCH_PLAIN)
+        learned = learned_leg(args, table, enc, step, value, nq, total_ids, world, barrier, stream)
 
     # ---- end to end: host query descriptors in, host answers out (pinned)
     e2e = None
@@ -381,9 +479,19 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
                "sample": "first %d of the %d queries, whole table (%d rows), %d threads over "
                          "contiguous horizontal partitions" % (m, nq, wl.n, nthreads)}
 
+    # ---- the learned narrower and the server, each on its own table
+    if args.workload != "zorder_learned" and not args.no_learned:
+        table.close()
+        del ids
+        torch.cuda.empty_cache()
+        learned = learned_workload_leg(args, world, barrier)
+    serving = None
+    if not args.no_serving and world == 1:
+        serving = serving_leg(args)
+
     if rank == 0:
         cfg = workload_config(wl, args.workload)
-        cfg["mode"] = "plain scan: one fused filter+compact launch per query"
+        cfg["mode"] = "plain scan: every query scanned on its own, the batch in one persistent launch"
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -391,7 +499,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
             "config": cfg, "clocks": clocks, "e2e": e2e,
             "gpu_launches": timing["kernel_launches"], "roofline": roofline,
             "cpu_baseline": cpu, "answer_ids_per_step": total_ids, "batched": batched,
-            "learned": learned,
+            "learned": learned, "serving": serving,
         }), flush=True)
     table.close()
 
@@ -410,6 +518,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the shared-scan measurement")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-narrower leg")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--learned-rows", type=int, default=None)
+    ap.add_argument("--serving-rows", type=int, default=20_000_000)
+    ap.add_argument("--serving-rates", type=float, nargs="*", default=[1000.0, 10000.0, 100000.0])
+    ap.add_argument("--serving-seconds", type=float, default=1.5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

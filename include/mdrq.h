@@ -238,6 +238,53 @@ int mdrq_learn_info(const mdrq_table *t, uint64_t *max_error, uint32_t *segments
 int mdrq_learn_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *widenings);
 
 /*
+ * Serving: continuous batching of queries that arrive over time; the paper has no
+ * counterpart (it times a fixed workload of queries, Sec. 7.1.2).
+ *
+ * mdrq_server_start — start a server on table t. Callers submit queries from any
+ * thread; a scheduler thread batches whatever has arrived (at most max_batch queries),
+ * counts each query's answer with the shared scan, admits queries in arrival order
+ * while their answers fit in the free part of a device arena of result_bytes (the
+ * result-buffer budget), writes the admitted answers into their arena slots, and lets
+ * the rest wait, ahead of later arrivals. Two batches may be on the GPU at once (two
+ * streams), so arrivals are admitted as slots and memory free up and their work
+ * overlaps the batch in flight. While a server runs, t must not be used otherwise.
+ * Errors: MDRQ_E_INVAL (t or out NULL, result_bytes < 4, max_batch 0); MDRQ_E_NOMEM;
+ * MDRQ_E_CUDA.
+ */
+typedef struct mdrq_server mdrq_server;
+int mdrq_server_start(mdrq_table *t, uint64_t result_bytes, uint32_t max_batch, mdrq_server **out);
+
+/* mdrq_server_submit — enqueue one query (predicates as for mdrq_query, copied); a
+ * ticket identifies it. Non-blocking. Errors: as mdrq_query's argument checks; a query
+ * proven empty on the host is answered at once. */
+int mdrq_server_submit(mdrq_server *s, const mdrq_pred *preds, uint32_t npreds, uint64_t *ticket);
+
+/* mdrq_server_wait — wait (timeout_us < 0: without limit) until the query is answered.
+ * ids receives a device pointer to its ascending ids in the arena (NULL when count is
+ * 0), valid until mdrq_server_release; latency_us the time from submit to the end of
+ * its batch. Returns the query's status: MDRQ_OK; MDRQ_E_CAPACITY (its answer, of
+ * *count ids, can never fit the arena, or the server stopped while it waited for
+ * memory); MDRQ_E_TIMEOUT (not answered within timeout_us; still queued); MDRQ_E_INVAL
+ * (unknown or released ticket). */
+int mdrq_server_wait(mdrq_server *s, uint64_t ticket, int64_t timeout_us, const uint32_t **ids, uint64_t *count,
+                     double *latency_us);
+
+/* mdrq_server_release — return an answered query's arena memory (its ids pointer dies). */
+int mdrq_server_release(mdrq_server *s, uint64_t ticket);
+
+/* mdrq_server_stats — answered queries, batches run, deferrals (a query sent back to
+ * wait for memory counts once per time), and the median and 99th percentile of the
+ * answered queries' latencies in microseconds. Any pointer may be NULL. */
+int mdrq_server_stats(mdrq_server *s, uint64_t *completed, uint64_t *batches, uint64_t *deferred, double *p50_us,
+                      double *p99_us);
+
+/* mdrq_server_stop — stop accepting queries, answer the queued ones, free the server and
+ * its arena (unreleased answers die with it). NULL is a no-op. Returns MDRQ_OK or the
+ * CUDA error that stopped the server. */
+int mdrq_server_stop(mdrq_server *s);
+
+/*
  * mdrq_inject_fault — test hook for failure detection; the paper has no counterpart.
  * Arms one fault for the next query call on this table:
  *  MDRQ_FAULT_SKIP_TILES  the next scan launch never claims its first `arg` (>= 1) row

@@ -52,6 +52,7 @@ constexpr uint32_t kChunkImageWords = 14 * 1024; // shared-memory budget of one 
 constexpr uint32_t kColWords = 10;               // words of one ChunkCol in an image
 constexpr uint32_t kHintBuckets = 256;           // value buckets of a column's search hint
 constexpr int kCountPlanes = 4;                  // bit planes of the pass-1 lane counters
+constexpr unsigned long long kSkipQuery = ~0ull;  // qbase of a query pass 2 must not write
 constexpr int kPrefetchCols = 8;                 // column values per row kept in flight
 
 // One column of a chunk's shared-memory image (kColWords words).
@@ -248,7 +249,8 @@ __global__ void __launch_bounds__(kSharedThreads) mdrq_shared_pass_kernel(Shared
             const uint32_t qi = g * 32 + lane;
             if (WRITE && qi < h.nq) {
                 const uint64_t lq = h.q0 + qi;
-                off[g] = p.qbase[lq] + p.counts[lq * p.n_units + unit];
+                const unsigned long long qb = p.qbase[lq];
+                off[g] = qb == kSkipQuery ? kSkipQuery : qb + p.counts[lq * p.n_units + unit];
             }
         }
         uint32_t plane[kSharedG][kCountPlanes];  // pass 1: bit-sliced per-lane counters
@@ -338,12 +340,12 @@ __global__ void __launch_bounds__(kSharedThreads) mdrq_shared_pass_kernel(Shared
                         const bool bit = (mask[g] >> q) & 1u;
                         const uint32_t b = __ballot_sync(0xffffffffu, bit);
                         const unsigned long long o = __shfl_sync(0xffffffffu, off[g], q);
-                        if (bit) {
+                        if (bit && o != kSkipQuery) {
                             const unsigned long long pos = o + __popc(b & lt);
                             if (pos < p.capacity)
                                 p.ids[pos] = (uint32_t)r;
                         }
-                        if (lane == q)
+                        if (lane == q && o != kSkipQuery)
                             off[g] += __popc(b);
                     }
                 }
@@ -493,6 +495,10 @@ struct SharedScanState {
     unsigned char *stage = nullptr;  // pinned: chunk headers, plan, live_orig
     size_t stage_cap = 0;
     int grid_pass = 0, grid_scan = 0;
+    // the batch prepared by shared_scan_count, for shared_scan_write
+    SharedParams params;
+    uint32_t grid = 0;
+    bool ready = false;
 };
 
 namespace {
@@ -523,18 +529,32 @@ uint32_t to_bits(double v, int32_t type)
 
 }  // namespace
 
-int shared_scan_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std::vector<uint32_t> &live,
-                      uint32_t *ids, uint64_t capacity, cudaStream_t s)
+SharedScanState *shared_state_new() { return new (std::nothrow) SharedScanState(); }
+
+void shared_state_free(SharedScanState *S)
 {
+    if (!S)
+        return;
+    cudaFree(S->plan);
+    cudaFree(S->chunks);
+    cudaFree(S->live_orig);
+    cudaFree(S->counts);
+    cudaFree(S->totals);
+    cudaFree(S->qbase);
+    cudaFreeHost(S->stage);
+    delete S;
+}
+
+unsigned long long *shared_state_qbase(SharedScanState *S) { return S->qbase; }
+unsigned long long *shared_state_totals(SharedScanState *S) { return S->totals; }
+
+int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<EncodedQuery> &enc,
+                      const std::vector<uint32_t> &live, cudaStream_t s)
+{
+    S.ready = false;
     const uint32_t nlive = (uint32_t)live.size();
     if (nlive == 0 || t->n == 0)
         return MDRQ_OK;
-    if (!t->shared) {
-        t->shared = new (std::nothrow) SharedScanState();
-        if (!t->shared)
-            return MDRQ_E_NOMEM;
-    }
-    SharedScanState &S = *t->shared;
 
     // ---- chunks: consecutive live queries, at most 32 * G each, image within budget
     struct Chunk {
@@ -766,36 +786,63 @@ int shared_scan_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const
     p.qbase = S.qbase;
     p.live_orig = S.live_orig;
     p.offsets = t->offsets_dev;
-    p.ids = ids;
-    p.capacity = capacity;
 
     const size_t smem = (size_t)kChunkImageWords * 4;
     const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)S.grid_pass, p.items);
     mdrq_shared_tables_kernel<<<(uint32_t)hdrs.size() * max_cols, 256, 0, s>>>(p, max_cols);
     mdrq_shared_pass_kernel<false><<<grid, kSharedThreads, smem, s>>>(p);
     mdrq_shared_scan_kernel<<<std::min<uint32_t>(nlive, (uint32_t)S.grid_scan), 1024, 0, s>>>(p);
-    mdrq_shared_qbase_kernel<<<1, 1024, 0, s>>>(p);
-    mdrq_shared_pass_kernel<true><<<grid, kSharedThreads, smem, s>>>(p);
     MDRQ_TRY_STATUS(cudaGetLastError());
-    t->last_launches += 5;
+    S.params = p;
+    S.grid = grid;
+    S.ready = true;
+    t->last_launches += 3;
     if (t->timing)
-        t->acc_kernels += 5;
+        t->acc_kernels += 3;
     return MDRQ_OK;
+}
+
+// Pass 2 of the batch prepared by shared_scan_count. csr: place the answers as one CSR
+// array (query bases from the counts, offsets_dev filled); otherwise S.qbase already
+// holds every live query's base in ids (kSkipQuery: not written).
+int shared_scan_write(mdrq_table *t, SharedScanState &S, uint32_t *ids, uint64_t capacity, bool csr, cudaStream_t s)
+{
+    if (!S.ready)
+        return MDRQ_OK;
+    SharedParams p = S.params;
+    p.ids = ids;
+    p.capacity = capacity;
+    if (csr)
+        mdrq_shared_qbase_kernel<<<1, 1024, 0, s>>>(p);
+    mdrq_shared_pass_kernel<true><<<S.grid, kSharedThreads, (size_t)kChunkImageWords * 4, s>>>(p);
+    MDRQ_TRY_STATUS(cudaGetLastError());
+    t->last_launches += csr ? 2 : 1;
+    if (t->timing)
+        t->acc_kernels += csr ? 2 : 1;
+    return MDRQ_OK;
+}
+
+int shared_scan_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std::vector<uint32_t> &live,
+                      uint32_t *ids, uint64_t capacity, cudaStream_t s)
+{
+    if (live.empty() || t->n == 0)
+        return MDRQ_OK;
+    if (!t->shared) {
+        t->shared = shared_state_new();
+        if (!t->shared)
+            return MDRQ_E_NOMEM;
+    }
+    const int st = shared_scan_count(t, *t->shared, enc, live, s);
+    if (st != MDRQ_OK)
+        return st;
+    return shared_scan_write(t, *t->shared, ids, capacity, true, s);
 }
 
 void shared_scan_free(mdrq_table *t)
 {
     if (!t || !t->shared)
         return;
-    SharedScanState &S = *t->shared;
-    cudaFree(S.plan);
-    cudaFree(S.chunks);
-    cudaFree(S.live_orig);
-    cudaFree(S.counts);
-    cudaFree(S.totals);
-    cudaFree(S.qbase);
-    cudaFreeHost(S.stage);
-    delete t->shared;
+    shared_state_free(t->shared);
     t->shared = nullptr;
 }
 

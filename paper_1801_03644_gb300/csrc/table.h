@@ -111,6 +111,14 @@ int grow_pinned(void **p, size_t *cap, size_t bytes);
 int shared_scan_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std::vector<uint32_t> &live,
                       uint32_t *ids, uint64_t capacity, cudaStream_t s);
 void shared_scan_free(mdrq_table *t);
+// the two phases of the shared scan on an explicit state (the serving loop keeps two)
+SharedScanState *shared_state_new();
+void shared_state_free(SharedScanState *S);
+unsigned long long *shared_state_qbase(SharedScanState *S);   // device, per live query
+unsigned long long *shared_state_totals(SharedScanState *S);  // device, per live query
+int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<EncodedQuery> &enc,
+                      const std::vector<uint32_t> &live, cudaStream_t s);
+int shared_scan_write(mdrq_table *t, SharedScanState &S, uint32_t *ids, uint64_t capacity, bool csr, cudaStream_t s);
 
 // mdrq.cu: one windowed scan launch over nq live queries whose rows and tiles the device
 // holds in windows / total_tiles (written by earlier kernels on the same stream).

@@ -44,7 +44,8 @@ EXPORTS = ["mdrq_load_columns", "mdrq_query", "mdrq_query_batch", "mdrq_free",
            "mdrq_status_string", "mdrq_table_rows", "mdrq_table_dims", "mdrq_last_scan_stats",
            "mdrq_scan_timing", "mdrq_scan_timing_read", "mdrq_query_static",
            "mdrq_inject_fault", "mdrq_set_batch_mode", "mdrq_learn", "mdrq_learn_info",
-           "mdrq_learn_window_rows"]
+           "mdrq_learn_window_rows", "mdrq_server_start", "mdrq_server_submit", "mdrq_server_wait",
+           "mdrq_server_release", "mdrq_server_stats", "mdrq_server_stop"]
 
 FAULT_SKIP_TILES, FAULT_NOMEM = 1, 2
 BATCH_AUTO, BATCH_PLAIN, BATCH_SHARED, BATCH_LEARNED = 0, 1, 2, 3
@@ -93,6 +94,20 @@ def lib():
         L.mdrq_learn_window_rows.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]
         L.mdrq_set_batch_mode.restype = ctypes.c_int
         L.mdrq_set_batch_mode.argtypes = [vp, ctypes.c_int]
+        L.mdrq_server_start.restype = ctypes.c_int
+        L.mdrq_server_start.argtypes = [vp, u64, u32, ctypes.POINTER(vp)]
+        L.mdrq_server_submit.restype = ctypes.c_int
+        L.mdrq_server_submit.argtypes = [vp, ctypes.POINTER(Pred), u32, ctypes.POINTER(u64)]
+        L.mdrq_server_wait.restype = ctypes.c_int
+        L.mdrq_server_wait.argtypes = [vp, u64, ctypes.c_int64, ctypes.POINTER(vp), ctypes.POINTER(u64),
+                                       ctypes.POINTER(ctypes.c_double)]
+        L.mdrq_server_release.restype = ctypes.c_int
+        L.mdrq_server_release.argtypes = [vp, u64]
+        L.mdrq_server_stats.restype = ctypes.c_int
+        L.mdrq_server_stats.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        L.mdrq_server_stop.restype = ctypes.c_int
+        L.mdrq_server_stop.argtypes = [vp]
         L.mdrq_inject_fault.restype = ctypes.c_int
         L.mdrq_inject_fault.argtypes = [vp, ctypes.c_int, u64]
         L.mdrq_query_static.restype = ctypes.c_int
@@ -367,3 +382,74 @@ class Table:
         a, b = ctypes.c_uint64(0), ctypes.c_uint64(0)
         lib().mdrq_last_scan_stats(self._h, ctypes.byref(a), ctypes.byref(b))
         return int(a.value), int(b.value)
+
+
+class _DeviceIds:
+    """A device id array the library owns, seen through __cuda_array_interface__ as int32
+    (the uint32 bit patterns, as the other device answers of this binding)."""
+
+    def __init__(self, ptr: int, count: int):
+        self.__cuda_array_interface__ = {"shape": (count,), "typestr": "<i4", "data": (ptr, False),
+                                         "version": 3}
+
+
+class Server:
+    """Continuous-batching server on a table (``mdrq_server_*``).
+
+    ``submit`` is non-blocking and thread-safe; ``wait`` returns the answer as a device
+    tensor viewing the server's result arena (valid until ``release``)."""
+
+    def __init__(self, table: "Table", result_bytes: int = 2 << 30, max_batch: int = 512):
+        h = ctypes.c_void_p()
+        st = lib().mdrq_server_start(table.handle, int(result_bytes), int(max_batch), ctypes.byref(h))
+        if st != OK:
+            raise MDRQError(st, "mdrq_server_start")
+        self._h = h
+        self._table = table
+
+    def submit_encoded(self, preds, npreds: int) -> int:
+        tk = ctypes.c_uint64(0)
+        st = lib().mdrq_server_submit(self._h, preds, npreds, ctypes.byref(tk))
+        if st != OK:
+            raise MDRQError(st, "mdrq_server_submit")
+        return int(tk.value)
+
+    def submit(self, query) -> int:
+        return self.submit_encoded(encode_query(query, self._table.dtypes), len(query))
+
+    def wait(self, ticket: int, timeout_us: int = -1):
+        """(status, device uint32 tensor or None, count, latency in us)."""
+        import torch
+        ptr, cnt, lat = ctypes.c_void_p(), ctypes.c_uint64(0), ctypes.c_double(0)
+        st = lib().mdrq_server_wait(self._h, int(ticket), int(timeout_us), ctypes.byref(ptr),
+                                    ctypes.byref(cnt), ctypes.byref(lat))
+        ids = None
+        if st == OK and cnt.value:
+            ids = torch.as_tensor(_DeviceIds(int(ptr.value), int(cnt.value)), device="cuda")
+        return st, ids, int(cnt.value), lat.value
+
+    def release(self, ticket: int):
+        st = lib().mdrq_server_release(self._h, int(ticket))
+        if st != OK:
+            raise MDRQError(st, "mdrq_server_release")
+
+    def stats(self) -> dict:
+        c, b, d = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+        p50, p99 = ctypes.c_double(0), ctypes.c_double(0)
+        lib().mdrq_server_stats(self._h, ctypes.byref(c), ctypes.byref(b), ctypes.byref(d),
+                                ctypes.byref(p50), ctypes.byref(p99))
+        return {"completed": int(c.value), "batches": int(b.value), "deferred": int(d.value),
+                "p50_us": p50.value, "p99_us": p99.value}
+
+    def stop(self) -> int:
+        st = OK
+        if getattr(self, "_h", None):
+            st = lib().mdrq_server_stop(self._h)
+            self._h = None
+        return st
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass

@@ -305,6 +305,33 @@ def zorder_learned(n: int = 200_000_000, nq: int = 4096, sel_range=(1e-4, 0.05),
                     "[%g, %g]" % (n, nq, sel_range[0], sel_range[1]))
 
 
+def serving_table(n: int = 20_000_000, nq: int = 20_000, sel_range=(1e-5, 0.1)) -> Workload:
+    """n x 16 float32: dims 0-7 uniform on [0,1), dims 8-15 the joint 20-cluster
+    mixture of ``mixed_clustered``. Queries constrain 1..16 random dims, target
+    selectivity log-uniform in ``sel_range`` (the serving stream draws from them)."""
+    rng = rng_for(5, 0)
+    cols = [uniform_column(rng, n) for _ in range(8)]
+    cols += cluster_mixture_columns(rng, n, 8)
+    dtypes = [c.dtype for c in cols]
+    samples = quantile_samples(cols, rng_for(5, 2))
+    qrng = rng_for(5, 1)
+    qs = []
+    for _ in range(nq):
+        k = int(qrng.integers(1, 17))
+        dims = sorted(qrng.choice(16, size=k, replace=False).tolist())
+        s = log_uniform(qrng, *sel_range)
+        qs.append(target_selectivity_query(samples, dtypes, dims, s, qrng))
+    return Workload("serving_%dx16_f32" % n, cols, qs,
+                    "n=%d d=16 f32 (8 U[0,1), 8 joint 20-cluster mixture sigma 0.02); %d queries, "
+                    "k~U{1..16}, target sel log-uniform [%g, %g]" % (n, nq, sel_range[0], sel_range[1]))
+
+
+def poisson_arrivals(rate_per_s: float, count: int, seed: int = 0) -> np.ndarray:
+    """Arrival times (seconds from 0) of an open-loop Poisson stream."""
+    gaps = rng_for(50 + seed, 0).exponential(1.0 / rate_per_s, size=count)
+    return np.cumsum(gaps)
+
+
 def paper_uniform(n: int, d: int, nq: int, seed: int = 7) -> Workload:
     """SYNT-UNI (Sec. 7.2.1): n x d float32 uniform on [0,1), random-pair queries."""
     rng = rng_for(100 + seed, 0)

@@ -1,0 +1,107 @@
+"""The continuous-batching server (mdrq_server_*): every answer in the mix equals the
+query's answer alone (CPU oracle and the table's own mdrq_query), id for id; admission
+by result memory defers queries without losing any (needs a GB300)."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1801_03644_gb300 import workloads as W
+from test_gpu_parity import M, _device  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_stream(M, server, queries, rate, release=True):
+    """Submit on a Poisson schedule from this thread; a second thread waits, copies the
+    answers to the host and releases them. Returns {index: (status, ids, latency)}."""
+    arrivals = W.poisson_arrivals(rate, len(queries))
+    tickets = [None] * len(queries)
+    got = {}
+    done = threading.Event()
+
+    def consumer():
+        i = 0
+        while i < len(queries):
+            while tickets[i] is None:
+                time.sleep(0.0001)
+            st, ids, cnt, lat = server.wait(tickets[i])
+            got[i] = (st, M.as_uint32_numpy(ids) if ids is not None else np.zeros(0, np.uint32), cnt, lat)
+            if release and st == M.OK:
+                server.release(tickets[i])
+            i += 1
+        done.set()
+
+    th = threading.Thread(target=consumer)
+    th.start()
+    t0 = time.perf_counter()
+    for i, q in enumerate(queries):
+        wait = arrivals[i] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        tickets[i] = server.submit(q)
+    th.join(timeout=300)
+    assert done.is_set()
+    return got
+
+
+def test_answers_alone_equal_answers_in_the_mix(M):
+    wl = W.serving_table(n=1_000_003, nq=400)
+    cols = _device(wl.columns)
+    with M.Table(cols) as t:
+        alone = [M.as_uint32_numpy(t.query(q)).copy() for q in wl.queries]
+        srv = M.Server(t, result_bytes=256 << 20, max_batch=64)
+        got = _run_stream(M, srv, wl.queries, rate=20_000)
+        stats = srv.stats()
+        assert srv.stop() == M.OK
+    for i, q in enumerate(wl.queries):
+        st, ids, cnt, lat = got[i]
+        assert st == M.OK and cnt == ids.size
+        assert np.array_equal(ids, alone[i]), i
+        assert np.array_equal(ids, oracle.mdrq(wl.columns, q, 8)), i
+        assert lat > 0
+    assert stats["completed"] == len(wl.queries)
+    assert stats["batches"] >= 2 and 0 < stats["p50_us"] <= stats["p99_us"]
+
+
+def test_admission_by_result_memory(M):
+    """An arena that holds only a few answers: queries wait for memory, in order, and
+    every answer is still exact; an answer larger than the arena fails cleanly."""
+    wl = W.serving_table(n=500_000, nq=120)
+    cols = _device(wl.columns)
+    with M.Table(cols) as t:
+        sizes = [t.query(q).numel() for q in wl.queries]
+        biggest = max(sizes)
+        arena = max(4 * biggest + 16, sum(sizes) * 4 // 10)
+        srv = M.Server(t, result_bytes=arena, max_batch=32)
+        got = _run_stream(M, srv, wl.queries, rate=50_000)
+        stats = srv.stats()
+        assert stats["deferred"] > 0
+        # a query whose answer cannot fit at all
+        small = M.Server(t, result_bytes=4 * max(1, biggest // 2), max_batch=8)
+        i_big = int(np.argmax(sizes))
+        tk = small.submit(wl.queries[i_big])
+        st, ids, cnt, lat = small.wait(tk)
+        assert st == M.E_CAPACITY and cnt == biggest
+        assert small.stop() == M.OK
+        assert srv.stop() == M.OK
+    for i, q in enumerate(wl.queries):
+        st, ids, cnt, lat = got[i]
+        assert st == M.OK
+        assert np.array_equal(ids, oracle.mdrq(wl.columns, q, 8)), i
+
+
+def test_stop_answers_queued_queries(M):
+    wl = W.serving_table(n=200_000, nq=50)
+    cols = _device(wl.columns)
+    with M.Table(cols) as t:
+        srv = M.Server(t, result_bytes=64 << 20, max_batch=16)
+        tickets = [srv.submit(q) for q in wl.queries]
+        res = [srv.wait(tk) for tk in tickets]
+        assert all(r[0] == M.OK for r in res)
+        for (st, ids, cnt, lat), q in zip(res, wl.queries):
+            got = M.as_uint32_numpy(ids) if ids is not None else np.zeros(0, np.uint32)
+            assert np.array_equal(got, oracle.mdrq(wl.columns, q, 4))
+        assert srv.stop() == M.OK

@@ -28,7 +28,6 @@
 #include <cstdint>
 #include <cstring>
 #include <new>
-#include <thread>
 #include <vector>
 
 #include "mdrq.h"
@@ -62,13 +61,16 @@ struct LearnedModel {
     unsigned long long max_error = 0;
     double train_ms = 0;
     // per-batch buffers
-    DevWindow *windows = nullptr;
+    DevWindow *slots = nullptr;              // kRangesPerQuery windows per query, uncompacted
+    size_t slots_cap = 0;
+    DevWindow *windows = nullptr;            // the windows of all queries, compacted
     size_t windows_cap = 0;
-    unsigned long long *qkeys = nullptr;     // 2 per query: Z(lo), Z(hi)
-    size_t qkeys_cap = 0;
-    unsigned long long *total_tiles = nullptr;
+    unsigned char *qaux = nullptr;           // per query: cells, counts, tiles, bases (device)
+    size_t qaux_cap = 0;
+    std::vector<uint32_t> qcells;            // per query: lo cells, hi cells (host staging)
+    unsigned long long *totals = nullptr;    // [0] tiles, [1] windows of the last chunk
     unsigned long long *scratch = nullptr;   // error / check words
-    size_t last_nq = 0;                      // queries of the last chunk's windows
+    bool have_windows = false;
 };
 
 // ---------------------------------------------------------------- keys
@@ -367,103 +369,434 @@ __device__ __forceinline__ unsigned long long lower_in(const uint32_t *keys, uns
     return lo;
 }
 
-// Per query: the exact row run [lower_bound(Z(lo)), upper_bound(Z(hi))) of its key
-// range, found from the model's window after the window has been proven to contain
-// it; stored with its start rounded down to a multiple of 4 (128-bit loads).
-__global__ void __launch_bounds__(128) mdrq_window_kernel(ModelView mv, const uint32_t *keys, unsigned long long eps,
-                                                          const unsigned long long *qkeys, uint32_t nw,
-                                                          DevWindow *windows, unsigned long long *probe_count)
+// The exact row run [lower_bound(Z(lo)), upper_bound(Z(hi))) of one key range, found
+// from the model's window after the window has been proven to contain it: every row
+// before its start must have a key below Z(lo) and every row from its end on a key
+// above Z(hi), else the window is widened by doubling steps (counted in *probes).
+__device__ __forceinline__ void prove_run(const ModelView &mv, const float *s_w, const uint32_t *keys,
+                                          unsigned long long eps, unsigned long long zlo, unsigned long long zhi,
+                                          unsigned long long *lb_out, unsigned long long *ub_out,
+                                          unsigned long long *probes)
 {
-    __shared__ float s_w[kMlpParams];
-    if (mv.kind == MDRQ_MODEL_MLP)
-        for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x)
-            s_w[i] = mv.mlp[i];
-    __syncthreads();
-    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nw)
-        return;
-    const unsigned long long zlo = qkeys[2 * q], zhi = qkeys[2 * q + 1];
     const long long n = (long long)mv.n;
     const double plo = model_predict(mv, s_w, zlo), phi = model_predict(mv, s_w, zhi);
     long long w0 = (long long)floor(fmin(fmax(plo, -1.0), (double)n)) - (long long)eps - 1;
     long long w1 = (long long)ceil(fmin(fmax(phi, -1.0), (double)n)) + (long long)eps + 2;
     w0 = w0 < 0 ? 0 : (w0 > n ? n : w0);
     w1 = w1 < w0 ? w0 : (w1 > n ? n : w1);
-    unsigned long long probes = 0;
-    // prove: every row before w0 has key < Z(lo), every row from w1 on has key > Z(hi)
     for (long long step = 1; w0 > 0 && (unsigned long long)keys[w0 - 1] >= zlo; step *= 2) {
         w0 = w0 > step ? w0 - step : 0;
-        ++probes;
+        ++*probes;
     }
     for (long long step = 1; w1 < n && (unsigned long long)keys[w1] <= zhi; step *= 2) {
         w1 = w1 + step < n ? w1 + step : n;
-        ++probes;
+        ++*probes;
     }
-    // the exact run inside the proven window
     const unsigned long long lb = lower_in(keys, (unsigned long long)w0, (unsigned long long)w1, zlo);
-    const unsigned long long ub = upper_in(keys, lb, (unsigned long long)w1, zhi);
-    DevWindow w = windows[q];  // query and last were set by the host
-    w.row_begin = lb & ~3ull;
-    w.row_first = lb;
-    w.row_end = ub;
-    w.tile_start = 0;
-    w.tiles = 0;
-    windows[q] = w;
-    if (probes)
+    *lb_out = lb;
+    *ub_out = upper_in(keys, lb, (unsigned long long)w1, zhi);
+}
+
+// ---------------------------------------------------------------- box decomposition
+
+constexpr uint32_t kRangesPerQuery = 1024;  // budget of the box decomposition
+constexpr int kBoxThreads = 256;
+constexpr int kBoxPer = kRangesPerQuery / kBoxThreads;  // nodes (ranges) per thread
+constexpr size_t kBoxSmem = 3 * (size_t)kRangesPerQuery * 16;
+
+// inclusive scan of one value per thread over the block (kBoxThreads threads); ends
+// with a barrier, so s_warp may be reused at once
+__device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t *s_warp)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o)
+            v += x;
+    }
+    if (lane == 31)
+        s_warp[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < kBoxThreads / 32 ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o)
+                w += x;
+        }
+        if (lane < kBoxThreads / 32)
+            s_warp[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t r = v + (warp ? s_warp[warp - 1] : 0u);
+    __syncthreads();
+    return r;
+}
+
+// A node of the key-bit tree: a run of keys sharing their top `len` used bits (`key`
+// holds them, the other bits 0). Its points' cells are fixed in the bits the prefix
+// covers, so per dimension j its cell extent is an interval: byte j of lo .. byte j of hi.
+struct BoxNode {
+    uint32_t key, lo, hi, len;
+};
+
+// key bit position of the i-th most significant used bit (bit 4b + j holds bit b of
+// dimension j's cell)
+__device__ __forceinline__ uint32_t used_bit(uint32_t i, uint32_t nd)
+{
+    return 4 * (7 - i / nd) + ((nd - 1) - i % nd);
+}
+
+// 0: outside the box, 1: crossing its border, 2: inside
+__device__ __forceinline__ uint32_t classify_node(const BoxNode &x, uint32_t clo, uint32_t chi, uint32_t nd)
+{
+    bool inside = true;
+    for (uint32_t j = 0; j < nd; ++j) {
+        const uint32_t a = (x.lo >> (8 * j)) & 0xffu, b = (x.hi >> (8 * j)) & 0xffu;
+        const uint32_t l = (clo >> (8 * j)) & 0xffu, h = (chi >> (8 * j)) & 0xffu;
+        if (b < l || a > h)
+            return 0;
+        inside = inside && a >= l && b <= h;
+    }
+    return inside ? 2u : 1u;
+}
+
+// the lower (half 0) or upper (half 1) child: the node's next used bit fixed, which
+// halves the cell extent of that bit's dimension
+__device__ __forceinline__ BoxNode child_of(const BoxNode &f, uint32_t half, uint32_t nd)
+{
+    const uint32_t pos = used_bit(f.len, nd);
+    const uint32_t j = pos % 4, b = pos / 4;
+    BoxNode c = f;
+    c.len = f.len + 1;
+    c.key = f.key | (half << pos);
+    const uint32_t mid = ((f.lo >> (8 * j)) & 0xffu) + (1u << b);  // first cell of the upper half
+    if (half)
+        c.lo = (f.lo & ~(0xffu << (8 * j))) | (mid << (8 * j));
+    else
+        c.hi = (f.hi & ~(0xffu << (8 * j))) | ((mid - 1) << (8 * j));
+    return c;
+}
+
+// the node's key run: its fixed bits, then all zeros / all ones in the free used bits
+__device__ __forceinline__ ulonglong2 run_of_node(const BoxNode &x, uint32_t nd)
+{
+    unsigned long long hi = x.key;
+    for (uint32_t i = x.len; i < 8 * nd; ++i)
+        hi |= 1ull << used_bit(i, nd);
+    return make_ulonglong2(x.key, hi);
+}
+
+// One block per query (cells clo / chi: byte j = cell of the bound on key dimension j).
+// (1) Its box as at most kRangesPerQuery key ranges: level by level, the nodes crossing
+//     the border are split in key order while the range count stays within the budget
+//     (inside halves become ranges, outside halves are dropped); once a split would pass
+//     it, the crossing nodes left are kept whole, covering keys outside the box that the
+//     scan rejects. Ranges are sorted and adjacent ones merged.
+// (2) Per range, its exact row run through the model (prove_run) and its tiles of
+//     tile_rows rows from the run's 4-aligned start; the query's last range gets one
+//     tile even when empty, so that its answer is closed.
+// Writes the query's windows to slots[q * kRangesPerQuery + i] with tile_start local to
+// the query, the range count to counts[q] and the tile total to qtiles[q].
+__global__ void __launch_bounds__(kBoxThreads) mdrq_box_windows_kernel(
+    ModelView mv, const uint32_t *keys, unsigned long long eps, const uint32_t *qcells, uint32_t nd,
+    uint32_t tile_rows, DevWindow *slots, uint32_t *counts, uint32_t *qtiles, unsigned long long *probe_count)
+{
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    BoxNode *cur = reinterpret_cast<BoxNode *>(s_raw);
+    BoxNode *nxt = cur + kRangesPerQuery;
+    ulonglong2 *out = reinterpret_cast<ulonglong2 *>(nxt + kRangesPerQuery);
+    __shared__ uint32_t s_warp[kBoxThreads / 32];
+    __shared__ uint32_t s_ncur, s_nout, s_split, s_ins, s_cross;
+
+    const uint32_t q = blockIdx.x;
+    const uint32_t clo = qcells[2 * q], chi = qcells[2 * q + 1];
+    const uint32_t B = kRangesPerQuery, bits = 8 * nd;
+    if (threadIdx.x == 0) {
+        BoxNode root;
+        root.key = 0;
+        root.len = 0;
+        root.lo = 0;
+        root.hi = nd >= 4 ? 0xffffffffu : ((1u << (8 * nd)) - 1u);
+        s_nout = 0;
+        s_ncur = 0;
+        const uint32_t c = classify_node(root, clo, chi, nd);
+        if (c == 2)
+            out[s_nout++] = run_of_node(root, nd);
+        else if (c == 1)
+            cur[s_ncur++] = root;
+    }
+    __syncthreads();
+    // invariant: s_nout + s_ncur <= B
+    for (uint32_t len = 0; len < bits && s_ncur > 0; ++len) {
+        const uint32_t ncur = s_ncur, nout = s_nout;
+        // per node: inside children (low 16 bits) and crossing children (high 16 bits)
+        uint32_t packed[kBoxPer], cls[kBoxPer];
+        uint32_t mine = 0;
+#pragma unroll
+        for (int k = 0; k < kBoxPer; ++k) {
+            const uint32_t i = threadIdx.x * kBoxPer + k;
+            packed[k] = 0;
+            cls[k] = 0;
+            if (i < ncur) {
+                const uint32_t c0 = classify_node(child_of(cur[i], 0, nd), clo, chi, nd);
+                const uint32_t c1 = classify_node(child_of(cur[i], 1, nd), clo, chi, nd);
+                cls[k] = c0 | (c1 << 2);
+                packed[k] = (c0 == 2) + (c1 == 2) + (((c0 == 1) + (c1 == 1)) << 16);
+            }
+            mine += packed[k];
+        }
+        if (threadIdx.x == 0)
+            s_split = ncur;
+        const uint32_t incl = block_incl_scan(mine, s_warp);
+        // ranges if nodes 0..i are split: nout + (children of 0..i) + (ncur - i - 1);
+        // nodes are split up to the first i at which that passes the budget
+        uint32_t run = incl - mine;
+#pragma unroll
+        for (int k = 0; k < kBoxPer; ++k) {
+            const uint32_t i = threadIdx.x * kBoxPer + k;
+            run += packed[k];
+            if (i < ncur && nout + ncur + (run & 0xffffu) + (run >> 16) - (i + 1) > B) {
+                atomicMin(&s_split, i);
+                break;
+            }
+        }
+        __syncthreads();
+        const uint32_t split = s_split;
+        // children of the split nodes: inside ones appended to out, crossing ones to nxt,
+        // both in key order; the totals are the scan value at node split - 1
+        uint32_t pin = (incl - mine) & 0xffffu, pcr = (incl - mine) >> 16;
+        run = incl - mine;
+        if (split == 0 && threadIdx.x == 0) {
+            s_ins = 0;
+            s_cross = 0;
+        }
+#pragma unroll
+        for (int k = 0; k < kBoxPer; ++k) {
+            const uint32_t i = threadIdx.x * kBoxPer + k;
+            run += packed[k];
+            if (i < split) {
+                const BoxNode f = cur[i];
+                for (uint32_t h = 0; h < 2; ++h) {
+                    const uint32_t c = (cls[k] >> (2 * h)) & 3u;
+                    if (c == 2)
+                        out[nout + pin++] = run_of_node(child_of(f, h, nd), nd);
+                    else if (c == 1)
+                        nxt[pcr++] = child_of(f, h, nd);
+                }
+                if (i + 1 == split) {
+                    s_ins = run & 0xffffu;
+                    s_cross = run >> 16;
+                }
+            }
+        }
+        __syncthreads();
+        const uint32_t n_in = s_ins, n_cr = s_cross;
+        if (split < ncur) {
+            // budget reached: the unsplit nodes and the new crossing nodes are kept whole
+            for (uint32_t i = split + threadIdx.x; i < ncur; i += blockDim.x)
+                out[nout + n_in + (i - split)] = run_of_node(cur[i], nd);
+            for (uint32_t i = threadIdx.x; i < n_cr; i += blockDim.x)
+                out[nout + n_in + (ncur - split) + i] = run_of_node(nxt[i], nd);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                s_nout = nout + n_in + (ncur - split) + n_cr;
+                s_ncur = 0;
+            }
+        } else {
+            for (uint32_t i = threadIdx.x; i < n_cr; i += blockDim.x)
+                cur[i] = nxt[i];
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                s_nout = nout + n_in;
+                s_ncur = n_cr;
+            }
+        }
+        __syncthreads();
+    }
+    // (at full depth a node is one cell: inside or outside, so nothing is left in cur)
+    const uint32_t nout = s_nout;
+    // bitonic sort of out by first key (the runs are disjoint), padded with sentinels
+    uint32_t n2 = 1;
+    while (n2 < nout)
+        n2 <<= 1;
+    for (uint32_t i = nout + threadIdx.x; i < n2; i += blockDim.x)
+        out[i] = make_ulonglong2(~0ull, ~0ull);
+    __syncthreads();
+    for (uint32_t k = 2; k <= n2; k <<= 1) {
+        for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
+            for (uint32_t i = threadIdx.x; i < n2; i += blockDim.x) {
+                const uint32_t l = i ^ jj;
+                if (l > i) {
+                    const ulonglong2 a = out[i], b = out[l];
+                    if ((a.x > b.x) == ((i & k) == 0)) {
+                        out[i] = b;
+                        out[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // merge adjacent runs: a merged range starts where a run does not begin right after
+    // the previous one's last key
+    uint32_t starts = 0, flag[kBoxPer];
+#pragma unroll
+    for (int k = 0; k < kBoxPer; ++k) {
+        const uint32_t i = threadIdx.x * kBoxPer + k;
+        flag[k] = i < nout && (i == 0 || out[i].x != out[i - 1].y + 1);
+        starts += flag[k];
+    }
+    const uint32_t nstart = block_incl_scan(starts, s_warp);
+    // merged ranges go to cur (reinterpreted as key pairs: 16 bytes each, same size)
+    ulonglong2 *rng = reinterpret_cast<ulonglong2 *>(cur);
+    {
+        uint32_t pos = nstart - starts;
+#pragma unroll
+        for (int k = 0; k < kBoxPer; ++k) {
+            const uint32_t i = threadIdx.x * kBoxPer + k;
+            if (i < nout) {
+                if (flag[k])
+                    rng[pos++].x = out[i].x;
+                if (i + 1 == nout || out[i + 1].x != out[i].y + 1)
+                    rng[pos - 1].y = out[i].y;
+            }
+        }
+    }
+    if (threadIdx.x == blockDim.x - 1)
+        s_nout = nstart;
+    __syncthreads();
+    uint32_t nr = s_nout;
+    const bool none = nr == 0;  // the box holds no cell: one empty window closes the query
+    if (none)
+        nr = 1;
+    // the model's weights (MLP) go to out, which is free now
+    float *s_w = reinterpret_cast<float *>(out);
+    if (mv.kind == MDRQ_MODEL_MLP)
+        for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x)
+            s_w[i] = mv.mlp[i];
+    __syncthreads();
+    // (2) row runs and tiles of the ranges, thread t taking ranges t*kBoxPer.. in key order
+    unsigned long long lbs[kBoxPer], ubs[kBoxPer];
+    uint32_t tl[kBoxPer], mytiles = 0;
+    unsigned long long probes = 0;
+#pragma unroll
+    for (int k = 0; k < kBoxPer; ++k) {
+        const uint32_t i = threadIdx.x * kBoxPer + k;
+        lbs[k] = ubs[k] = 0;
+        tl[k] = 0;
+        if (i < nr) {
+            if (!none)
+                prove_run(mv, s_w, keys, eps, rng[i].x, rng[i].y, &lbs[k], &ubs[k], &probes);
+            const unsigned long long rows = ubs[k] > lbs[k] ? ubs[k] - (lbs[k] & ~3ull) : 0;
+            tl[k] = rows ? (uint32_t)((rows + tile_rows - 1) / tile_rows) : (i + 1 == nr ? 1u : 0u);
+        }
+        mytiles += tl[k];
+    }
+    const uint32_t tincl = block_incl_scan(mytiles, s_warp);
+    uint32_t tpos = tincl - mytiles;
+    DevWindow *dst = slots + (size_t)q * kRangesPerQuery;
+#pragma unroll
+    for (int k = 0; k < kBoxPer; ++k) {
+        const uint32_t i = threadIdx.x * kBoxPer + k;
+        if (i < nr) {
+            DevWindow w;
+            w.row_begin = lbs[k] & ~3ull;
+            w.row_first = lbs[k];
+            w.row_end = ubs[k];
+            w.tile_start = tpos;
+            w.tiles = tl[k];
+            w.query = q;
+            w.last = i + 1 == nr;
+            dst[i] = w;
+        }
+        tpos += tl[k];
+    }
+    if (threadIdx.x == blockDim.x - 1) {
+        counts[q] = nr;
+        qtiles[q] = tincl;
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        probes += __shfl_xor_sync(0xffffffffu, probes, o);
+    if ((threadIdx.x & 31) == 0 && probes)
         atomicAdd(probe_count, probes);
 }
 
-// tiles per window (at least 1 for a query's last window) and their exclusive prefix;
-// total into *total. One block.
-__global__ void __launch_bounds__(1024) mdrq_window_tiles_kernel(DevWindow *windows, uint32_t nq, uint32_t tile_rows,
-                                                                 unsigned long long *total)
+// Exclusive scans of the per-query window counts and tile totals (one block):
+// wbase[q], tbase[q]; totals[0] = all tiles, totals[1] = all windows.
+__global__ void __launch_bounds__(1024) mdrq_window_base_kernel(const uint32_t *counts, const uint32_t *qtiles,
+                                                                uint32_t nq, unsigned long long *wbase,
+                                                                unsigned long long *tbase,
+                                                                unsigned long long *totals)
 {
-    __shared__ unsigned long long s_warp[32];
-    __shared__ unsigned long long s_carry;
+    __shared__ unsigned long long s_warp[2][32];
+    __shared__ unsigned long long s_carry[2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0)
-        s_carry = 0;
+    if (threadIdx.x < 2)
+        s_carry[threadIdx.x] = 0;
     __syncthreads();
-    for (uint32_t base = 0; base < nq; base += blockDim.x) {
-        const uint32_t i = base + threadIdx.x;
-        unsigned long long v = 0;
-        if (i < nq) {
-            // rows from the aligned start; none when the window holds no row
-            const unsigned long long rows =
-                windows[i].row_end > windows[i].row_first ? windows[i].row_end - windows[i].row_begin : 0;
-            v = rows ? (rows + tile_rows - 1) / tile_rows : (windows[i].last ? 1 : 0);
-        }
-        unsigned long long x = v;
+    for (uint32_t b0 = 0; b0 < nq; b0 += blockDim.x) {
+        const uint32_t i = b0 + threadIdx.x;
+        const unsigned long long v0 = i < nq ? counts[i] : 0ull, v1 = i < nq ? qtiles[i] : 0ull;
+        unsigned long long x0 = v0, x1 = v1;
         for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o)
-                x += y;
+            const unsigned long long y0 = __shfl_up_sync(0xffffffffu, x0, o);
+            const unsigned long long y1 = __shfl_up_sync(0xffffffffu, x1, o);
+            if (lane >= o) {
+                x0 += y0;
+                x1 += y1;
+            }
         }
-        if (lane == 31)
-            s_warp[warp] = x;
+        if (lane == 31) {
+            s_warp[0][warp] = x0;
+            s_warp[1][warp] = x1;
+        }
         __syncthreads();
-        if (warp == 0) {
-            unsigned long long w = s_warp[lane];
+        if (warp < 2) {
+            unsigned long long w = lane < (int)(blockDim.x / 32) ? s_warp[warp][lane] : 0ull;
             for (int o = 1; o < 32; o <<= 1) {
                 const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
                 if (lane >= o)
                     w += y;
             }
-            s_warp[lane] = w;
+            s_warp[warp][lane] = w;
         }
         __syncthreads();
-        const unsigned long long carry = s_carry;
+        const unsigned long long c0 = s_carry[0], c1 = s_carry[1];
         if (i < nq) {
-            windows[i].tile_start = carry + (warp ? s_warp[warp - 1] : 0ull) + x - v;
-            windows[i].tiles = v;
+            wbase[i] = c0 + (warp ? s_warp[0][warp - 1] : 0ull) + x0 - v0;
+            tbase[i] = c1 + (warp ? s_warp[1][warp - 1] : 0ull) + x1 - v1;
         }
         __syncthreads();
-        if (threadIdx.x == blockDim.x - 1)
-            s_carry = carry + s_warp[31];
+        if (threadIdx.x == 0) {
+            s_carry[0] = c0 + s_warp[0][31];
+            s_carry[1] = c1 + s_warp[1][31];
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0)
-        *total = s_carry;
+    if (threadIdx.x == 0) {
+        totals[0] = s_carry[1];
+        totals[1] = s_carry[0];
+    }
+}
+
+// compaction: query q's windows from its slots to windows[wbase[q] ..], tile starts
+// made global (one block per query)
+__global__ void __launch_bounds__(256) mdrq_window_fill_kernel(const DevWindow *slots, const uint32_t *counts,
+                                                               const unsigned long long *wbase,
+                                                               const unsigned long long *tbase, DevWindow *windows)
+{
+    const uint32_t q = blockIdx.x;
+    const uint32_t cnt = counts[q];
+    const unsigned long long wb = wbase[q], tb = tbase[q];
+    const DevWindow *src = slots + (size_t)q * kRangesPerQuery;
+    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+        DevWindow w = src[i];
+        w.tile_start += tb;
+        windows[wb + i] = w;
+    }
 }
 
 // ---------------------------------------------------------------- host
@@ -489,115 +822,6 @@ uint32_t host_cell(float x)
     return c < 0.0f ? 0u : (c > 255.0f ? 255u : (uint32_t)c);
 }
 
-uint32_t host_key(const uint32_t *cells, uint32_t ndims)
-{
-    uint32_t k = 0;
-    for (uint32_t j = 0; j < ndims; ++j)
-        for (int b = 0; b < 8; ++b)
-            k |= ((cells[j] >> b) & 1u) << (4 * b + j);
-    return k;
-}
-
-constexpr uint32_t kRangesPerQuery = 1024;  // budget of the box decomposition
-
-// The key ranges of a query box (cells clo..chi per key dimension). A node is a run of
-// keys sharing their top `len` bits (len 0: all keys); its points' cells are fixed in
-// the bits that prefix covers, so its cell extent per dimension is an interval. Nodes
-// crossing the box's border are split in two by their next key bit, the shortest
-// prefixes (largest runs) first; halves inside the box become ranges, halves outside it
-// are dropped. When the budget is reached the crossing nodes left are kept whole (they
-// cover keys outside the box, which the scan rejects). Ranges are returned sorted,
-// adjacent ones merged.
-void box_ranges(const uint32_t *clo, const uint32_t *chi, uint32_t nd, std::vector<std::pair<uint64_t, uint64_t>> &out)
-{
-    const uint32_t bits = 8 * nd;  // key bits in use: bit 4b + j for j < nd
-    // key bit position of the i-th most significant bit in use
-    auto bit_at = [&](uint32_t i) {
-        const uint32_t b = 7 - i / nd, j = (nd - 1) - i % nd;
-        return 4 * b + j;
-    };
-    struct Node {
-        uint32_t len;      // bits fixed
-        uint32_t lo[4];    // cell extent of the node per dimension
-        uint32_t hi[4];
-        uint32_t key;      // the fixed bits (others 0)
-    };
-    // 0: outside, 1: crossing, 2: inside
-    auto classify = [&](const Node &x) {
-        bool inside = true;
-        for (uint32_t j = 0; j < nd; ++j) {
-            if (x.hi[j] < clo[j] || x.lo[j] > chi[j])
-                return 0;
-            inside = inside && x.lo[j] >= clo[j] && x.hi[j] <= chi[j];
-        }
-        return inside ? 2 : 1;
-    };
-    // the node's key run: its fixed bits, then all zeros / all ones in the free used bits
-    auto emit = [&](const Node &x) {
-        uint64_t hi = x.key;
-        for (uint32_t i = x.len; i < bits; ++i)
-            hi |= 1ull << bit_at(i);
-        out.emplace_back((uint64_t)x.key, hi);
-    };
-    out.clear();
-    thread_local std::vector<Node> pending[33];  // reused: no allocation after warm-up
-    for (auto &v : pending)
-        v.clear();
-    size_t npending = 0;
-    Node root;
-    root.len = 0;
-    root.key = 0;
-    for (uint32_t j = 0; j < 4; ++j) {
-        root.lo[j] = 0;
-        root.hi[j] = 255;
-    }
-    if (classify(root) == 2) {
-        emit(root);
-    } else {
-        pending[0].push_back(root);
-        npending = 1;
-    }
-    for (uint32_t len = 0; len < bits; ++len) {
-        while (!pending[len].empty() && out.size() + npending + 1 <= kRangesPerQuery) {
-            const Node f = pending[len].back();
-            pending[len].pop_back();
-            --npending;
-            const uint32_t pos = bit_at(len);
-            const uint32_t j = pos % 4, b = pos / 4;  // the split halves dimension j's cell range
-            for (uint32_t half = 0; half < 2; ++half) {
-                Node ch = f;
-                ch.len = len + 1;
-                ch.key = f.key | (half << pos);
-                const uint32_t mid = f.lo[j] + (1u << b);  // first cell of the upper half
-                if (half)
-                    ch.lo[j] = mid;
-                else
-                    ch.hi[j] = mid - 1;
-                const int cls = classify(ch);
-                if (cls == 2)
-                    emit(ch);
-                else if (cls == 1) {
-                    pending[len + 1].push_back(ch);
-                    ++npending;
-                }
-            }
-        }
-        if (!pending[len].empty())
-            break;  // budget reached
-    }
-    for (uint32_t len = 0; len <= bits; ++len)
-        for (const Node &f : pending[len])
-            emit(f);
-    std::sort(out.begin(), out.end());
-    size_t k = 0;
-    for (size_t i = 0; i < out.size(); ++i) {
-        if (k > 0 && out[i].first <= out[k - 1].second + 1)
-            out[k - 1].second = std::max(out[k - 1].second, out[i].second);
-        else
-            out[k++] = out[i];
-    }
-    out.resize(k);
-}
 
 }  // namespace
 
@@ -611,9 +835,10 @@ void learned_free(mdrq_table *t)
     cudaFree(m.knot_pos);
     cudaFree(m.slope);
     cudaFree(m.mlp);
+    cudaFree(m.slots);
     cudaFree(m.windows);
-    cudaFree(m.qkeys);
-    cudaFree(m.total_tiles);
+    cudaFree(m.qaux);
+    cudaFree(m.totals);
     cudaFree(m.scratch);
     delete t->learned;
     t->learned = nullptr;
@@ -641,7 +866,7 @@ int learn(mdrq_table *t, const uint32_t *dims, uint32_t ndims, int kind, cudaStr
     do {
         if ((st = cuda_status(cudaMalloc(&m->keys, n * 4))) ||
             (st = cuda_status(cudaMalloc(&m->scratch, 4 * 8))) ||
-            (st = cuda_status(cudaMalloc(&m->total_tiles, 8))))
+            (st = cuda_status(cudaMalloc(&m->totals, 16))))
             break;
         KeyCols kc;
         for (int j = 0; j < 4; ++j)
@@ -708,7 +933,7 @@ int learn(mdrq_table *t, const uint32_t *dims, uint32_t ndims, int kind, cudaStr
     return MDRQ_OK;
 }
 
-// Windows for the live queries (device), then one windowed scan launch.
+// Windows for the live queries, built on the device, then one windowed scan launch.
 int learned_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std::vector<uint32_t> &live,
                   uint32_t q0, uint32_t nlive, uint32_t *ids, uint64_t capacity, const unsigned long long *base_in,
                   cudaStream_t s)
@@ -718,77 +943,56 @@ int learned_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std
         return MDRQ_E_INVAL;
     if (nlive == 0)
         return MDRQ_OK;
-    // Z(lo), Z(hi) of each key range of each query's box: cells of its bounds on the key
-    // dimensions (the whole cell range where a key dimension is unconstrained)
-    // the decompositions of the queries run on the host threads, then are concatenated
-    // in query order
-    std::vector<std::vector<std::pair<uint64_t, uint64_t>>> per_query(nlive);
-    auto decompose = [&](uint32_t i) {
+    // cells of each query's bounds on the key dimensions (the whole cell range where a
+    // key dimension is unconstrained), one byte per dimension
+    m->qcells.resize(2 * (size_t)nlive);
+    for (uint32_t i = 0; i < nlive; ++i) {
         const EncodedQuery &e = enc[live[q0 + i]];
-        uint32_t clo[4] = {0, 0, 0, 0}, chi[4] = {0, 0, 0, 0};
+        uint32_t clo = 0, chi = 0;
         for (uint32_t j = 0; j < m->ndims; ++j) {
-            clo[j] = 0;
-            chi[j] = 255;
+            uint32_t cl = 0, ch = 255;
             for (size_t p = 0; p < e.dims.size(); ++p) {
                 if (e.dims[p] == m->dims[j]) {
                     float lo, hi;
                     std::memcpy(&lo, &e.preds[p].lo, 4);
                     std::memcpy(&hi, &e.preds[p].hi, 4);
-                    clo[j] = host_cell(lo);
-                    chi[j] = host_cell(hi);
+                    cl = host_cell(lo);
+                    ch = host_cell(hi);
                 }
             }
+            clo |= cl << (8 * j);
+            chi |= ch << (8 * j);
         }
-        box_ranges(clo, chi, m->ndims, per_query[i]);
-        if (per_query[i].empty())
-            per_query[i].emplace_back(1, 0);  // no key can match: an empty window
-    };
-    const uint32_t nthreads =
-        std::max(1u, std::min<uint32_t>(std::thread::hardware_concurrency(), (nlive + 63) / 64));
-    if (nthreads <= 1) {
-        for (uint32_t i = 0; i < nlive; ++i)
-            decompose(i);
-    } else {
-        std::vector<std::thread> pool;
-        for (uint32_t w = 0; w < nthreads; ++w)
-            pool.emplace_back([&, w]() {
-                for (uint32_t i = w; i < nlive; i += nthreads)
-                    decompose(i);
-            });
-        for (std::thread &th : pool)
-            th.join();
+        m->qcells[2 * i] = clo;
+        m->qcells[2 * i + 1] = chi;
     }
-    std::vector<unsigned long long> qk;
-    std::vector<DevWindow> win;
-    for (uint32_t i = 0; i < nlive; ++i) {
-        const std::vector<std::pair<uint64_t, uint64_t>> &ranges = per_query[i];
-        for (size_t r = 0; r < ranges.size(); ++r) {
-            qk.push_back(ranges[r].first);
-            qk.push_back(ranges[r].second);
-            DevWindow w;
-            std::memset(&w, 0, sizeof(w));
-            w.query = i;
-            w.last = r + 1 == ranges.size();
-            win.push_back(w);
-        }
-    }
-    const uint32_t nw = (uint32_t)win.size();
-    int st = grow_device((void **)&m->windows, &m->windows_cap, (size_t)nw * sizeof(DevWindow));
+    const size_t max_windows = (size_t)nlive * kRangesPerQuery;
+    int st = grow_device((void **)&m->slots, &m->slots_cap, max_windows * sizeof(DevWindow));
     if (st == MDRQ_OK)
-        st = grow_device((void **)&m->qkeys, &m->qkeys_cap, (size_t)nw * 16);
+        st = grow_device((void **)&m->windows, &m->windows_cap, max_windows * sizeof(DevWindow));
+    if (st == MDRQ_OK)
+        st = grow_device((void **)&m->qaux, &m->qaux_cap, (size_t)nlive * 32);
     if (st != MDRQ_OK)
         return st;
-    MDRQ_TRY_STATUS(cudaMemcpyAsync(m->qkeys, qk.data(), qk.size() * 8, cudaMemcpyHostToDevice, s));
-    MDRQ_TRY_STATUS(cudaMemcpyAsync(m->windows, win.data(), win.size() * sizeof(DevWindow), cudaMemcpyHostToDevice, s));
+    uint32_t *qcells = reinterpret_cast<uint32_t *>(m->qaux);
+    uint32_t *counts = qcells + 2 * (size_t)nlive;
+    uint32_t *qtiles = counts + nlive;
+    unsigned long long *wbase = reinterpret_cast<unsigned long long *>(qtiles + nlive);
+    unsigned long long *tbase = wbase + nlive;
+    MDRQ_TRY_STATUS(cudaMemcpyAsync(qcells, m->qcells.data(), (size_t)nlive * 8, cudaMemcpyHostToDevice, s));
     MDRQ_TRY_STATUS(cudaMemsetAsync(m->scratch + 1, 0, 8, s));
-    m->last_nq = nw;
+    MDRQ_TRY_STATUS(cudaFuncSetAttribute(mdrq_box_windows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kBoxSmem));
     const ModelView mv = view_of(*m, t->n);
-    mdrq_window_kernel<<<(nw + 127) / 128, 128, 0, s>>>(mv, m->keys, m->max_error, m->qkeys, nw, m->windows,
-                                                        m->scratch + 1);
     constexpr uint32_t kTile = (uint32_t)kWarps * 4 * 128;
-    mdrq_window_tiles_kernel<<<1, 1024, 0, s>>>(m->windows, nw, kTile, m->total_tiles);
+    mdrq_box_windows_kernel<<<nlive, kBoxThreads, kBoxSmem, s>>>(mv, m->keys, m->max_error, qcells, m->ndims, kTile,
+                                                                 m->slots, counts, qtiles, m->scratch + 1);
+    mdrq_window_base_kernel<<<1, 1024, 0, s>>>(counts, qtiles, nlive, wbase, tbase, m->totals);
+    mdrq_window_fill_kernel<<<nlive, 256, 0, s>>>(m->slots, counts, wbase, tbase, m->windows);
     MDRQ_TRY_STATUS(cudaGetLastError());
-    return launch_window_scan(t, q0, nlive, nw, ids, capacity, base_in, m->windows, m->total_tiles, s);
+    m->have_windows = true;
+    return launch_window_scan(t, q0, nlive, max_windows, m->totals + 1, ids, capacity, base_in, m->windows,
+                              m->totals, s);
 }
 
 int learned_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *probes)
@@ -796,15 +1000,16 @@ int learned_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *probes)
     if (!t || !t->learned)
         return MDRQ_E_INVAL;
     LearnedModel &m = *t->learned;
-    const size_t nq = m.last_nq;
-    std::vector<DevWindow> w(nq);
-    unsigned long long pr = 0;
-    if (nq)
-        MDRQ_TRY_STATUS(cudaMemcpy(w.data(), m.windows, nq * sizeof(DevWindow), cudaMemcpyDeviceToHost));
+    unsigned long long nw = 0, pr = 0;
+    if (m.have_windows)
+        MDRQ_TRY_STATUS(cudaMemcpy(&nw, m.totals + 1, 8, cudaMemcpyDeviceToHost));
+    std::vector<DevWindow> w(nw);
+    if (nw)
+        MDRQ_TRY_STATUS(cudaMemcpy(w.data(), m.windows, nw * sizeof(DevWindow), cudaMemcpyDeviceToHost));
     MDRQ_TRY_STATUS(cudaMemcpy(&pr, m.scratch + 1, 8, cudaMemcpyDeviceToHost));
     uint64_t sum = 0;
     for (const DevWindow &x : w)
-        sum += x.row_end - x.row_first;
+        sum += x.row_end > x.row_first ? x.row_end - x.row_first : 0;
     if (rows)
         *rows = sum;
     if (probes)

@@ -323,7 +323,8 @@ int launch_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t scanned_column
     return MDRQ_OK;
 }
 
-int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint32_t nwindows, uint32_t *ids, uint64_t capacity,
+int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t max_windows,
+                       const unsigned long long *nwindows, uint32_t *ids, uint64_t capacity,
                        const unsigned long long *base_in, const DevWindow *windows,
                        const unsigned long long *total_tiles, cudaStream_t s)
 {
@@ -334,7 +335,7 @@ int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint32_t nwindow
     }
     // a query's windows are disjoint runs of the table; each adds at most one partial
     // tile (its start is rounded down)
-    const uint64_t max_tiles = (uint64_t)nq * ((t->n + tile_rows<4>() - 1) / tile_rows<4>()) + nwindows;
+    const uint64_t max_tiles = (uint64_t)nq * ((t->n + tile_rows<4>() - 1) / tile_rows<4>()) + max_windows;
     const uint32_t grid = (uint32_t)std::max<uint64_t>(
         1, std::min<uint64_t>((uint64_t)t->sm_count * t->blocks_per_sm_window, max_tiles));
     const uint32_t laps = (uint32_t)(max_tiles >> t->ring_bits) + 1;
@@ -360,14 +361,14 @@ int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint32_t nwindow
     p.offsets = t->offsets_dev;
     p.error = t->error;
     p.windows = windows;
-    p.nwindows = nwindows;
+    p.nwindows_dev = nwindows;
     p.total_tiles_dev = total_tiles;
     mdrq_scan_window_kernel<<<grid, kScanThreads, 0, s>>>(p);
     MDRQ_TRY(cudaGetLastError());
     t->tag_next += laps;
     t->last_launches += 1;
     if (t->timing)
-        t->acc_kernels += 3;  // window, tiles and scan kernels
+        t->acc_kernels += 4;  // box-windows, base, fill and scan kernels
     return MDRQ_OK;
 }
 

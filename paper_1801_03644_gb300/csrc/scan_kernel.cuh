@@ -107,7 +107,7 @@ struct ScanParams {
     unsigned long long *offsets;     // offsets[orig + 1] <- end of query orig's answer
     int *error;                      // error bits (kErr*)
     const DevWindow *windows;        // windowed launches: row runs and their tiles (device)
-    uint32_t nwindows;               // windowed launches: number of windows
+    const unsigned long long *nwindows_dev;  // windowed launches: number of windows (device)
     const unsigned long long *total_tiles_dev;  // windowed launches: tile count (device)
 };
 
@@ -129,7 +129,7 @@ __device__ __forceinline__ uint32_t query_of_tile(const ScanParams &p, unsigned 
         return (uint32_t)(t / p.tiles_per_query);
     // the last window whose first tile is <= t (windows without tiles share the first
     // tile of the next window and come before it, so they are never chosen)
-    uint32_t lo = 0, hi = p.nwindows;
+    uint32_t lo = 0, hi = (uint32_t)*p.nwindows_dev;
     while (hi - lo > 1) {
         const uint32_t mid = (lo + hi) >> 1;
         if (p.windows[mid].tile_start <= t)

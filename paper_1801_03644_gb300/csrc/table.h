@@ -122,7 +122,8 @@ int shared_scan_write(mdrq_table *t, SharedScanState &S, uint32_t *ids, uint64_t
 
 // mdrq.cu: one windowed scan launch over nq live queries whose rows and tiles the device
 // holds in windows / total_tiles (written by earlier kernels on the same stream).
-int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint32_t nwindows, uint32_t *ids, uint64_t capacity,
+int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t max_windows,
+                       const unsigned long long *nwindows, uint32_t *ids, uint64_t capacity,
                        const unsigned long long *base_in, const DevWindow *windows,
                        const unsigned long long *total_tiles, cudaStream_t s);
 

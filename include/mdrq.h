@@ -339,6 +339,88 @@ int mdrq_query_static(const void *const *cols, const int32_t *types, uint32_t d,
                       const mdrq_pred *preds, uint32_t npreds, uint32_t *ids, uint64_t capacity,
                       uint64_t *count, void *stream);
 
+/*
+ * Shared-scan configuration and the autotuner. The shared scan (MDRQ_BATCH_SHARED)
+ * has two shape parameters: the rows of one warp's work unit, and the shared-memory
+ * budget of one chunk's search tables (which sets how many queries share one pass
+ * over the columns and how many blocks fit on an SM).
+ *
+ * mdrq_set_shared_config sets them for the table: unit_rows (rounded up to a multiple
+ * of 32; 0 = the built-in rule: enough units to fill the GPU, 256..8192 rows) and
+ * image_kib (16..208; 0 = the built-in 56 KiB). Errors: MDRQ_E_INVAL (t NULL,
+ * image_kib outside its range).
+ *
+ * mdrq_autotune times the given batch (synchronously, on `stream`, into a scratch
+ * answer buffer it allocates and frees) with the plain scan, with the shared scan
+ * under the built-in rule, and with the shared scan under a set of candidate
+ * configurations (coordinate search: unit sizes first, then budgets), each the best of
+ * two runs measured with CUDA events, host planning included. The table keeps the
+ * fastest shared configuration, and MDRQ_BATCH_AUTO then takes the faster of the two
+ * modes for batches of 32 or more live queries. The answers of every timed run are
+ * discarded; the table's batch mode is left as it was. A batch with no live query
+ * changes nothing. Errors: MDRQ_E_INVAL, MDRQ_E_NOMEM, MDRQ_E_TIMEOUT, MDRQ_E_CUDA.
+ */
+typedef struct {
+    int32_t mode;              /* the faster mode for this batch: MDRQ_BATCH_PLAIN or _SHARED */
+    uint32_t unit_rows;        /* the shared configuration kept (0: the built-in rule won) */
+    uint32_t image_kib;        /* (0: the built-in default won) */
+    uint32_t candidates;       /* shared-scan configurations timed */
+    double plain_ms;           /* the batch with the plain scan */
+    double shared_default_ms;  /* with the shared scan's built-in configuration */
+    double shared_ms;          /* with the configuration kept */
+} mdrq_tuning;
+
+int mdrq_set_shared_config(mdrq_table *t, uint32_t unit_rows, uint32_t image_kib);
+int mdrq_autotune(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, void *stream, mdrq_tuning *out);
+
+/*
+ * Prepared batches — a fixed batch of queries answered again and again (a standing
+ * report, a benchmark loop, a dashboard refresh) without per-call host work. The paper
+ * answers each query from scratch (Sec. 7.1.2); this is a GPU-side addition.
+ *
+ * mdrq_prepare_batch encodes the batch once, runs it once (the answer and the offsets
+ * are those of mdrq_query_batch with ids_on_device = 1, in the table's batch mode at
+ * this call: MDRQ_BATCH_AUTO, _PLAIN or _SHARED), and records the batch's device work
+ * (query-table copies, scan launches, offset copy-back) as one CUDA graph on a private
+ * copy of the table's scratch state. mdrq_prepared_launch replays that graph on a
+ * stream; mdrq_prepared_wait waits for the replay and returns its offsets.
+ *
+ *  t                 a loaded table; it must outlive the prepared batch (the batch
+ *                    reads its columns); the batch keeps its own scratch, so calls on
+ *                    t and replays of the batch do not share state. MDRQ_BATCH_LEARNED
+ *                    batches cannot be prepared (MDRQ_E_INVAL).
+ *  qs, nq            as mdrq_query_batch; copied, the caller may free them afterwards.
+ *  ids, capacity     device buffer that every replay overwrites with the CSR answer.
+ *  offsets           host, nq + 1 entries: the first run's CSR offsets. On
+ *                    MDRQ_E_CAPACITY offsets[nq] is the size the buffer needs and no
+ *                    batch is made (*out = NULL).
+ *  stream            the first run and the graph build are ordered after the work on it.
+ *  out               receives the prepared batch.
+ *
+ * Replays on one prepared batch must not overlap (they share its scratch): wait for
+ * one before launching the next on another stream; on one stream they serialise.
+ * Errors: MDRQ_E_INVAL, MDRQ_E_NOMEM, MDRQ_E_CAPACITY, MDRQ_E_TIMEOUT, MDRQ_E_CUDA.
+ */
+typedef struct mdrq_prepared mdrq_prepared;
+
+int mdrq_prepare_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, uint64_t capacity,
+                       uint64_t *offsets, void *stream, mdrq_prepared **out);
+
+/* Enqueue one replay on `stream` and return without waiting (MDRQ_E_CUDA if the launch
+ * fails). */
+int mdrq_prepared_launch(mdrq_prepared *p, void *stream);
+
+/* Wait for the last replay enqueued on `stream`, then fill offsets (host, nq + 1) as
+ * mdrq_query_batch does. MDRQ_E_TIMEOUT if a bounded device wait ran out (the batch's
+ * scratch is reset and it stays usable). */
+int mdrq_prepared_wait(mdrq_prepared *p, uint64_t *offsets, void *stream);
+
+/* Number of kernel launches in one replay (the graph's kernel nodes) into *kernels. */
+int mdrq_prepared_kernels(const mdrq_prepared *p, uint64_t *kernels);
+
+/* Release the batch (NULL-safe). Waits for its replays to finish. */
+void mdrq_prepared_free(mdrq_prepared *p);
+
 #ifdef __cplusplus
 }
 #endif

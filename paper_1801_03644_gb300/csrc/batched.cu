@@ -48,7 +48,8 @@ constexpr int kSharedThreads = kSharedWarps * 32;
 constexpr uint64_t kMaxUnitRows = 8192;          // rows per warp unit, large tables
 constexpr uint64_t kMinUnitRows = 256;           // rows per warp unit, small tables
 constexpr int kSharedG = 4;                      // 32-bit mask words per chunk: 128 queries
-constexpr uint32_t kChunkImageWords = 14 * 1024; // shared-memory budget of one chunk (56 KiB)
+constexpr uint32_t kChunkImageWords = 14 * 1024; // default shared-memory budget of one chunk (56 KiB)
+constexpr uint32_t kMaxImageWords = 52 * 1024;   // largest budget a table may set (208 KiB)
 constexpr uint32_t kColWords = 10;               // words of one ChunkCol in an image
 constexpr uint32_t kHintBuckets = 256;           // value buckets of a column's search hint
 constexpr int kCountPlanes = 4;                  // bit planes of the pass-1 lane counters
@@ -494,10 +495,13 @@ struct SharedScanState {
     size_t qbase_cap = 0;
     unsigned char *stage = nullptr;  // pinned: chunk headers, plan, live_orig
     size_t stage_cap = 0;
-    int grid_pass = 0, grid_scan = 0;
+    int grid_scan = 0;
+    bool smem_attr = false;            // pass kernels opted in to kMaxImageWords
+    std::vector<std::pair<uint32_t, int>> grid_for_words;  // (image words, persistent grid)
     // the batch prepared by shared_scan_count, for shared_scan_write
     SharedParams params;
     uint32_t grid = 0;
+    size_t smem = 0;
     bool ready = false;
 };
 
@@ -561,6 +565,7 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
         uint32_t q0, nq;
     };
     std::vector<Chunk> chunks;
+    const uint32_t budget = t->shared_image_words ? t->shared_image_words : kChunkImageWords;
     {
         uint32_t q = 0;
         while (q < nlive) {
@@ -576,9 +581,9 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
                 const uint32_t nc = ncols + add_cols, np = pairs + (uint32_t)e.dims.size();
                 const uint64_t words = (uint64_t)nc * (kColWords + kHintBuckets / 2) + 2ull * np + 4 +
                                        (2ull * np + nc) * kSharedG + 4ull * nc;
-                if (ch.nq > 0 && words > kChunkImageWords)
+                if (ch.nq > 0 && words > budget)
                     break;
-                if (ch.nq == 0 && words > kChunkImageWords)
+                if (ch.nq == 0 && words > budget)
                     return MDRQ_E_INVAL;  // one query alone does not fit (more than ~900 dimensions)
                 for (uint32_t j : e.dims)
                     per_dim[j] += 1;
@@ -596,6 +601,7 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
     std::vector<uint32_t> plan;
     plan.reserve(1 << 16);
     uint32_t max_cols = 1;
+    uint32_t max_img = 4;  // words of the largest chunk image: the launches' shared memory
     for (size_t ci = 0; ci < chunks.size(); ++ci) {
         const Chunk &ch = chunks[ci];
         // columns in first-use order, with their cut points
@@ -680,8 +686,9 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
             w += (cc[a].m + 1) * kSharedG;
         }
         const uint32_t img_words = (w + 3) & ~3u;
-        if (img_words > kChunkImageWords)
+        if (img_words > budget)
             return MDRQ_E_INVAL;  // cannot happen: the chunking bounded it
+        max_img = std::max(max_img, img_words);
         plan.resize(img_off + img_words, 0);
         for (uint32_t a = 0; a < ncols; ++a) {
             std::memcpy(&plan[img_off + a * kColWords], &cc[a], sizeof(ChunkCol));
@@ -722,24 +729,41 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
         h.iv_off = iv_off;
     }
 
-    // ---- grid shape: enough warp units to fill the persistent grid (small tables get
-    // smaller units), at most kMaxUnitRows rows each
-    if (S.grid_pass == 0) {
-        int bps = 0;
-        const size_t smem = (size_t)kChunkImageWords * 4;
-        if (cudaFuncSetAttribute(mdrq_shared_pass_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess ||
-            cudaFuncSetAttribute(mdrq_shared_pass_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, mdrq_shared_pass_kernel<true>, kSharedThreads,
-                                                          smem) != cudaSuccess)
+    // ---- grid shape: the persistent grid at the occupancy of the largest image; enough
+    // warp units to fill it (small tables get smaller units), at most kMaxUnitRows rows
+    // each, unless the table sets the unit size (mdrq_set_shared_config)
+    if (!S.smem_attr) {
+        const int most = (int)kMaxImageWords * 4;
+        if (cudaFuncSetAttribute(mdrq_shared_pass_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(mdrq_shared_pass_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most) !=
+                cudaSuccess)
             return cuda_status(cudaGetLastError());
-        S.grid_pass = t->sm_count * std::max(1, bps);
+        S.smem_attr = true;
         S.grid_scan = t->sm_count * 2;
     }
-    const uint64_t want_units = (uint64_t)S.grid_pass * kSharedWarps * 4 / std::max<size_t>(1, chunks.size());
-    uint64_t unit_rows = (t->n + want_units - 1) / std::max<uint64_t>(1, want_units);
-    unit_rows = std::min<uint64_t>(kMaxUnitRows, std::max<uint64_t>(kMinUnitRows, (unit_rows + 31) & ~31ull));
+    max_img = (max_img + 1023) & ~1023u;  // whole 4 KiB steps: few distinct launch shapes
+    const size_t smem = (size_t)max_img * 4;
+    int grid_pass = 0;
+    for (const auto &g : S.grid_for_words)
+        if (g.first == max_img)
+            grid_pass = g.second;
+    if (grid_pass == 0) {
+        int bps = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, mdrq_shared_pass_kernel<true>, kSharedThreads,
+                                                          smem) != cudaSuccess)
+            return cuda_status(cudaGetLastError());
+        grid_pass = t->sm_count * std::max(1, bps);
+        S.grid_for_words.emplace_back(max_img, grid_pass);
+    }
+    uint64_t unit_rows;
+    if (t->shared_unit_rows) {
+        unit_rows = std::max<uint64_t>(32, ((uint64_t)t->shared_unit_rows + 31) & ~31ull);
+    } else {
+        const uint64_t want_units = (uint64_t)grid_pass * kSharedWarps * 4 / std::max<size_t>(1, chunks.size());
+        unit_rows = (t->n + want_units - 1) / std::max<uint64_t>(1, want_units);
+        unit_rows = std::min<uint64_t>(kMaxUnitRows, std::max<uint64_t>(kMinUnitRows, (unit_rows + 31) & ~31ull));
+    }
 
     // ---- device buffers
     const uint64_t n_units = (t->n + unit_rows - 1) / unit_rows;
@@ -787,14 +811,14 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
     p.live_orig = S.live_orig;
     p.offsets = t->offsets_dev;
 
-    const size_t smem = (size_t)kChunkImageWords * 4;
-    const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)S.grid_pass, p.items);
+    const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)grid_pass, p.items);
     mdrq_shared_tables_kernel<<<(uint32_t)hdrs.size() * max_cols, 256, 0, s>>>(p, max_cols);
     mdrq_shared_pass_kernel<false><<<grid, kSharedThreads, smem, s>>>(p);
     mdrq_shared_scan_kernel<<<std::min<uint32_t>(nlive, (uint32_t)S.grid_scan), 1024, 0, s>>>(p);
     MDRQ_TRY_STATUS(cudaGetLastError());
     S.params = p;
     S.grid = grid;
+    S.smem = smem;
     S.ready = true;
     t->last_launches += 3;
     if (t->timing)
@@ -814,7 +838,7 @@ int shared_scan_write(mdrq_table *t, SharedScanState &S, uint32_t *ids, uint64_t
     p.capacity = capacity;
     if (csr)
         mdrq_shared_qbase_kernel<<<1, 1024, 0, s>>>(p);
-    mdrq_shared_pass_kernel<true><<<S.grid, kSharedThreads, (size_t)kChunkImageWords * 4, s>>>(p);
+    mdrq_shared_pass_kernel<true><<<S.grid, kSharedThreads, S.smem, s>>>(p);
     MDRQ_TRY_STATUS(cudaGetLastError());
     t->last_launches += csr ? 2 : 1;
     if (t->timing)

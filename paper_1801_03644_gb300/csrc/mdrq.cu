@@ -255,9 +255,10 @@ int launch_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t scanned_column
     const uint64_t resident = (uint64_t)t->sm_count * t->blocks_per_sm[ui];
     const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(resident, total_tiles));
 
-    // tags: one per lap of the ring; restart from a cleared ring before they wrap
+    // tags: one per lap of the ring; restart from a cleared ring before they wrap, and
+    // at every launch of a captured graph (its replays repeat the same tags)
     const uint32_t laps = (uint32_t)(total_tiles >> t->ring_bits) + 1;
-    if ((uint64_t)t->tag_next + laps > kTagLimit) {
+    if (t->graph_capture || (uint64_t)t->tag_next + laps > kTagLimit) {
         MDRQ_TRY(cudaMemsetAsync(t->tile_state, 0, ((size_t)1 << t->ring_bits) * 8, s));
         t->tag_next = 1;
     }
@@ -383,18 +384,17 @@ void reset_scratch(mdrq_table *t, cudaStream_t s)
     t->tag_next = 1;
 }
 
-int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, uint64_t capacity,
-              uint64_t *offsets, int ids_on_device, cudaStream_t s)
+// a2: every query of a batch encoded first, so that a bad argument launches nothing;
+// live = the queries that need a scan, in order; npreds = their predicates
+int encode_batch(const mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, std::vector<EncodedQuery> &enc,
+                 std::vector<uint32_t> &live, size_t &npreds)
 {
-    if (!t || !offsets || (nq > 0 && !qs) || (capacity > 0 && !ids))
-        return MDRQ_E_INVAL;
     for (uint32_t q = 0; q < nq; ++q)
         if (qs[q].reserved != 0)
             return MDRQ_E_INVAL;
-    // a2: encode every query first, so that a bad argument launches nothing
-    std::vector<EncodedQuery> enc(nq);
-    std::vector<uint32_t> live;  // queries that need a scan, in order
-    size_t npreds = 0;
+    enc.assign(nq, EncodedQuery());
+    live.clear();
+    npreds = 0;
     for (uint32_t q = 0; q < nq; ++q) {
         int st = encode_query(t, qs[q].preds, qs[q].npreds, enc[q]);
         if (st != MDRQ_OK)
@@ -404,14 +404,16 @@ int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, u
             npreds += enc[q].preds.size();
         }
     }
-    t->last_launches = 0;
-    t->last_bytes = 0;
-    MDRQ_TRY(cudaSetDevice(t->device));
-    if (t->inject_nomem) {
-        t->inject_nomem = 0;
-        return MDRQ_E_NOMEM;
-    }
+    return MDRQ_OK;
+}
 
+// Everything a batch does on the stream: the query tables to the device, the scan
+// launches of the table's batch mode, and the offsets and error word back to pinned
+// host memory. Asynchronous. It allocates nothing once the table's buffers have the
+// batch's sizes, which is what lets a prepared batch capture it as a graph.
+int enqueue_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std::vector<uint32_t> &live,
+                  uint32_t nq, size_t npreds, uint32_t *out, uint64_t capacity, cudaStream_t s)
+{
     const size_t nlive = live.size();
     const size_t dq_bytes = std::max<size_t>(1, nlive) * sizeof(DevQuery);
     const size_t dp_bytes = std::max<size_t>(1, npreds) * sizeof(DevPred);
@@ -426,13 +428,6 @@ int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, u
         st = grow_pinned((void **)&t->qstage_host, &t->qstage_host_cap, dq_bytes + dp_bytes);
     if (st != MDRQ_OK)
         return st;
-    uint32_t *out = ids;
-    if (!ids_on_device && capacity > 0) {
-        st = grow_device((void **)&t->ids_stage, &t->ids_stage_cap, (size_t)capacity * 4);
-        if (st != MDRQ_OK)
-            return st;
-        out = t->ids_stage;
-    }
 
     // the query tables go to the device in one copy (pinned staging)
     DevQuery *hq = reinterpret_cast<DevQuery *>(t->qstage_host);
@@ -473,7 +468,7 @@ int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, u
     const bool learned_mode = t->batch_mode == MDRQ_BATCH_LEARNED;
     const bool shared = !learned_mode && (t->batch_mode == MDRQ_BATCH_SHARED ||
                         (t->batch_mode == MDRQ_BATCH_AUTO && nlive >= kAutoSharedMinQueries &&
-                         t->n >= kAutoSharedMinRows));
+                         (t->auto_mode >= 0 ? t->auto_mode == MDRQ_BATCH_SHARED : t->n >= kAutoSharedMinRows)));
     if (shared) {
         cudaEvent_t *evp = nullptr;
         if (t->timing) {
@@ -513,6 +508,13 @@ int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, u
     MDRQ_TRY(cudaMemcpyAsync(t->offsets_host, t->offsets_dev, ((size_t)nq + 1) * 8,
                              cudaMemcpyDeviceToHost, s));
     MDRQ_TRY(cudaMemcpyAsync(t->error_host, t->error, sizeof(int), cudaMemcpyDeviceToHost, s));
+    return MDRQ_OK;
+}
+
+// Waits for a batch enqueued on s and fills the caller's offsets (nq + 1); a query
+// answered on the host (empty) ends where the previous one ends.
+int finish_batch(mdrq_table *t, const std::vector<uint32_t> &live, uint32_t nq, uint64_t *offsets, cudaStream_t s)
+{
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         reset_scratch(t, s);
@@ -522,16 +524,49 @@ int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, u
         reset_scratch(t, s);
         return MDRQ_E_TIMEOUT;
     }
-    // a query answered on the host (empty) ends where the previous one ends
     std::memcpy(offsets, t->offsets_host, ((size_t)nq + 1) * 8);
     offsets[0] = 0;
     size_t li = 0;
     for (uint32_t q = 0; q < nq; ++q) {
-        if (li < nlive && live[li] == q)
+        if (li < live.size() && live[li] == q)
             ++li;
         else
             offsets[q + 1] = offsets[q];
     }
+    return MDRQ_OK;
+}
+
+int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, uint64_t capacity,
+              uint64_t *offsets, int ids_on_device, cudaStream_t s)
+{
+    if (!t || !offsets || (nq > 0 && !qs) || (capacity > 0 && !ids))
+        return MDRQ_E_INVAL;
+    std::vector<EncodedQuery> enc;
+    std::vector<uint32_t> live;
+    size_t npreds = 0;
+    int st = encode_batch(t, qs, nq, enc, live, npreds);
+    if (st != MDRQ_OK)
+        return st;
+    t->last_launches = 0;
+    t->last_bytes = 0;
+    MDRQ_TRY(cudaSetDevice(t->device));
+    if (t->inject_nomem) {
+        t->inject_nomem = 0;
+        return MDRQ_E_NOMEM;
+    }
+    uint32_t *out = ids;
+    if (!ids_on_device && capacity > 0) {
+        st = grow_device((void **)&t->ids_stage, &t->ids_stage_cap, (size_t)capacity * 4);
+        if (st != MDRQ_OK)
+            return st;
+        out = t->ids_stage;
+    }
+    st = enqueue_batch(t, enc, live, nq, npreds, out, capacity, s);
+    if (st != MDRQ_OK)
+        return st;
+    st = finish_batch(t, live, nq, offsets, s);
+    if (st != MDRQ_OK)
+        return st;
     const uint64_t total = offsets[nq];
     // 4 bytes per id written
     t->last_bytes += 4ull * std::min<uint64_t>(total, capacity);
@@ -543,6 +578,21 @@ int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, u
         MDRQ_TRY(cudaStreamSynchronize(s));
     }
     return total > capacity ? MDRQ_E_CAPACITY : MDRQ_OK;
+}
+
+// scratch: claim counter, error word and a ring of 2^16 look-back states (512 KiB),
+// and the pinned error word
+int alloc_scratch(mdrq_table *t, cudaStream_t s)
+{
+    t->ring_bits = 16;
+    const size_t scratch_words = 2 + ((size_t)1 << t->ring_bits);
+    MDRQ_TRY(cudaMalloc(&t->scratch, scratch_words * 8));
+    t->ticket = t->scratch;
+    t->error = reinterpret_cast<int *>(t->scratch + 1);
+    t->tile_state = t->scratch + 2;
+    MDRQ_TRY(cudaMemsetAsync(t->scratch, 0, scratch_words * 8, s));
+    MDRQ_TRY(cudaMallocHost((void **)&t->error_host, sizeof(int)));
+    return MDRQ_OK;
 }
 
 void destroy(mdrq_table *t)
@@ -598,15 +648,11 @@ int load(const void *const *cols, const int32_t *types, uint32_t d, uint64_t n, 
         }
     }
 
-    // scratch: claim counter, error word and a ring of 2^16 look-back states (512 KiB)
-    t->ring_bits = 16;
-    const size_t scratch_words = 2 + ((size_t)1 << t->ring_bits);
-    MDRQ_TRY(cudaMalloc(&t->scratch, scratch_words * 8));
-    t->ticket = t->scratch;
-    t->error = reinterpret_cast<int *>(t->scratch + 1);
-    t->tile_state = t->scratch + 2;
-    MDRQ_TRY(cudaMemsetAsync(t->scratch, 0, scratch_words * 8, s));
-    MDRQ_TRY(cudaMallocHost((void **)&t->error_host, sizeof(int)));
+    {
+        const int st = alloc_scratch(t, s);
+        if (st != MDRQ_OK)
+            return st;
+    }
 
     if (n == 0)
         return cuda_status(cudaStreamSynchronize(s));

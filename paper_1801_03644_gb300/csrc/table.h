@@ -81,7 +81,13 @@ struct mdrq_table {
     // batched shared scan (mdrq_set_batch_mode, batched.cu)
     int batch_mode = MDRQ_BATCH_AUTO;
     mdrq::SharedScanState *shared = nullptr;
+    uint32_t shared_unit_rows = 0;    // rows per warp unit (0: built-in rule)
+    uint32_t shared_image_words = 0;  // shared-memory budget per chunk (0: built-in default)
+    int auto_mode = -1;               // mode AUTO takes for 32+ queries, once measured (-1: rule)
     mdrq::LearnedModel *learned = nullptr;
+
+    // set on the private table of a prepared batch while its launches are captured
+    bool graph_capture = false;
 
     // host-side fault injection for failure-detection tests (mdrq_inject_fault)
     uint64_t inject_skip_tiles = 0;  // next scan launch never claims its first tiles
@@ -105,6 +111,16 @@ double bound_value(uint32_t bits, int32_t type);
 int encode_query(const mdrq_table *t, const mdrq_pred *preds, uint32_t npreds, EncodedQuery &q);
 int grow_device(void **p, size_t *cap, size_t bytes);
 int grow_pinned(void **p, size_t *cap, size_t bytes);
+
+// mdrq.cu: the steps of a batch call (run_batch = encode, enqueue, finish)
+int encode_batch(const mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, std::vector<EncodedQuery> &enc,
+                 std::vector<uint32_t> &live, size_t &npreds);
+int enqueue_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std::vector<uint32_t> &live,
+                  uint32_t nq, size_t npreds, uint32_t *out, uint64_t capacity, cudaStream_t s);
+int finish_batch(mdrq_table *t, const std::vector<uint32_t> &live, uint32_t nq, uint64_t *offsets, cudaStream_t s);
+int alloc_scratch(mdrq_table *t, cudaStream_t s);
+void reset_scratch(mdrq_table *t, cudaStream_t s);
+void destroy(mdrq_table *t);
 
 // batched.cu: answer the live queries of a batch with the shared scan. enc/live as in
 // run_batch; writes offsets_dev[orig + 1] for every live query.

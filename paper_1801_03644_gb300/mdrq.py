@@ -33,6 +33,12 @@ class Pred(ctypes.Structure):
                 ("lo", ctypes.c_uint32), ("hi", ctypes.c_uint32)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("unit_rows", ctypes.c_uint32), ("image_kib", ctypes.c_uint32),
+                ("candidates", ctypes.c_uint32), ("plain_ms", ctypes.c_double),
+                ("shared_default_ms", ctypes.c_double), ("shared_ms", ctypes.c_double)]
+
+
 class QDesc(ctypes.Structure):
     _fields_ = [("preds", ctypes.POINTER(Pred)), ("npreds", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32)]
@@ -45,7 +51,9 @@ EXPORTS = ["mdrq_load_columns", "mdrq_query", "mdrq_query_batch", "mdrq_free",
            "mdrq_scan_timing", "mdrq_scan_timing_read", "mdrq_query_static",
            "mdrq_inject_fault", "mdrq_set_batch_mode", "mdrq_learn", "mdrq_learn_info",
            "mdrq_learn_window_rows", "mdrq_server_start", "mdrq_server_submit", "mdrq_server_wait",
-           "mdrq_server_release", "mdrq_server_stats", "mdrq_server_stop"]
+           "mdrq_server_release", "mdrq_server_stats", "mdrq_server_stop", "mdrq_prepare_batch",
+           "mdrq_prepared_launch", "mdrq_prepared_wait", "mdrq_prepared_kernels", "mdrq_prepared_free",
+           "mdrq_set_shared_config", "mdrq_autotune"]
 
 FAULT_SKIP_TILES, FAULT_NOMEM = 1, 2
 BATCH_AUTO, BATCH_PLAIN, BATCH_SHARED, BATCH_LEARNED = 0, 1, 2, 3
@@ -113,6 +121,21 @@ def lib():
         L.mdrq_query_static.restype = ctypes.c_int
         L.mdrq_query_static.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(i32), u32, u64,
                                         ctypes.POINTER(Pred), u32, vp, u64, ctypes.POINTER(u64), vp]
+        L.mdrq_set_shared_config.restype = ctypes.c_int
+        L.mdrq_set_shared_config.argtypes = [vp, u32, u32]
+        L.mdrq_autotune.restype = ctypes.c_int
+        L.mdrq_autotune.argtypes = [vp, ctypes.POINTER(QDesc), u32, vp, ctypes.POINTER(Tuning)]
+        L.mdrq_prepare_batch.restype = ctypes.c_int
+        L.mdrq_prepare_batch.argtypes = [vp, ctypes.POINTER(QDesc), u32, vp, u64, ctypes.POINTER(u64), vp,
+                                         ctypes.POINTER(vp)]
+        L.mdrq_prepared_launch.restype = ctypes.c_int
+        L.mdrq_prepared_launch.argtypes = [vp, vp]
+        L.mdrq_prepared_wait.restype = ctypes.c_int
+        L.mdrq_prepared_wait.argtypes = [vp, ctypes.POINTER(u64), vp]
+        L.mdrq_prepared_kernels.restype = ctypes.c_int
+        L.mdrq_prepared_kernels.argtypes = [vp, ctypes.POINTER(u64)]
+        L.mdrq_prepared_free.restype = None
+        L.mdrq_prepared_free.argtypes = [vp]
         _lib = L
     return _lib
 
@@ -327,6 +350,50 @@ class Table:
             raise MDRQError(st, "mdrq_query_batch")
         return out[: int(off[-1])], off
 
+    def set_shared_config(self, unit_rows: int = 0, image_kib: int = 0):
+        """``mdrq_set_shared_config``: the shared scan's rows per warp unit and chunk
+        shared-memory budget (0: built-in)."""
+        st = lib().mdrq_set_shared_config(self._h, int(unit_rows), int(image_kib))
+        if st != OK:
+            raise MDRQError(st, "mdrq_set_shared_config")
+
+    def autotune(self, queries, stream=None) -> dict:
+        """``mdrq_autotune`` on this batch; returns the ``mdrq_tuning`` fields."""
+        descs, _keep, nq = self.encode_batch(queries)
+        r = Tuning()
+        st = lib().mdrq_autotune(self._h, descs, nq, _stream_handle(stream), ctypes.byref(r))
+        if st != OK:
+            raise MDRQError(st, "mdrq_autotune")
+        return {k: getattr(r, k) for k, _ in Tuning._fields_}
+
+    def prepare(self, queries, out=None, stream=None) -> "Prepared":
+        """``mdrq_prepare_batch``: the batch recorded as a CUDA graph for replays. ``out``
+        (device int32 tensor) receives every replay's answer; by default one of the
+        exact size is made from a first run."""
+        import torch
+        enc = self.encode_batch(queries)
+        descs, _keep, nq = enc
+        off = np.zeros(nq + 1, dtype=np.uint64)
+        h = ctypes.c_void_p(0)
+
+        def attempt(buf):
+            return lib().mdrq_prepare_batch(self._h, descs, nq, buf.data_ptr(), buf.numel(),
+                                            off.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                            _stream_handle(stream), ctypes.byref(h))
+        if out is None:
+            probe = torch.empty(1, dtype=torch.int32, device="cuda")
+            st = attempt(probe)
+            if st == OK:
+                out = probe
+            elif st == E_CAPACITY:
+                out = torch.empty(max(1, int(off[-1])), dtype=torch.int32, device="cuda")
+                st = attempt(out)
+        else:
+            st = attempt(out)
+        if st != OK:
+            raise MDRQError(st, "mdrq_prepare_batch")
+        return Prepared(self, h.value, out, nq, off.copy())
+
     def learn(self, dims, model: int = MODEL_PLA, stream=None):
         """``mdrq_learn``: a learned range narrower over the Z-order key of ``dims`` (the
         rows must be sorted by that key). Returns ``learn_info()``."""
@@ -382,6 +449,61 @@ class Table:
         a, b = ctypes.c_uint64(0), ctypes.c_uint64(0)
         lib().mdrq_last_scan_stats(self._h, ctypes.byref(a), ctypes.byref(b))
         return int(a.value), int(b.value)
+
+
+class Prepared:
+    """A prepared batch (``mdrq_prepare_batch``): ``launch()`` enqueues a replay of its
+    graph, ``wait()`` returns the offsets; ``run()`` does both and returns
+    (ids tensor view, offsets). The table must outlive it."""
+
+    def __init__(self, table: "Table", handle: int, out, nq: int, first_offsets):
+        self.table = table
+        self._h = handle
+        self.out = out
+        self.nq = nq
+        self.first_offsets = first_offsets
+
+    def launch(self, stream=None):
+        st = lib().mdrq_prepared_launch(self._h, _stream_handle(stream))
+        if st != OK:
+            raise MDRQError(st, "mdrq_prepared_launch")
+
+    def wait(self, stream=None) -> np.ndarray:
+        off = np.zeros(self.nq + 1, dtype=np.uint64)
+        st = lib().mdrq_prepared_wait(self._h, off.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                      _stream_handle(stream))
+        if st != OK:
+            raise MDRQError(st, "mdrq_prepared_wait")
+        return off
+
+    def run(self, stream=None):
+        self.launch(stream)
+        off = self.wait(stream)
+        return self.out[: int(off[-1])], off
+
+    def kernels(self) -> int:
+        k = ctypes.c_uint64(0)
+        st = lib().mdrq_prepared_kernels(self._h, ctypes.byref(k))
+        if st != OK:
+            raise MDRQError(st, "mdrq_prepared_kernels")
+        return int(k.value)
+
+    def close(self):
+        if self._h:
+            lib().mdrq_prepared_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class _DeviceIds:

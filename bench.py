@@ -396,6 +396,31 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     ms = shards.max_over_ranks(ms)  # the slowest rank's time counts
     value = world * nq * args.steps / (ms / 1e3)
 
+    # ---- the same plain batch replayed as a prepared CUDA graph (no per-call host work)
+    def graph_steps(mode):
+        table.set_batch_mode(mode)
+        with table.prepare(wl.queries, out=ids) as p:
+            for _ in range(args.warmup):
+                p.launch()
+            p.wait()
+            barrier()
+            g0 = torch.cuda.Event(enable_timing=True)
+            g1 = torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            for _ in range(args.steps):
+                p.launch()
+            g1.record(stream)
+            off_g = p.wait()
+            barrier()
+            gms = shards.max_over_ranks(g0.elapsed_time(g1))
+            kernels = p.kernels()
+        return {"value": world * nq * args.steps / (gms / 1e3), "unit": UNIT, "ms_per_step": gms / args.steps,
+                "kernels_per_replay": kernels,
+                "answers_identical_to_plain": bool(int(off_g[-1]) == total_ids)}
+
+    plain_graph = graph_steps(mdrq.BATCH_PLAIN)
+    table.set_batch_mode(mdrq.BATCH_PLAIN)
+
     # ---- batched shared scan (the same batch, answers identical): speedup over plain
     batched = None
     if not args.no_batched:
@@ -420,6 +445,19 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
                            "128 queries, per-row query sets from elementary-interval tables, "
                            "two passes (count, write)",
                    "answers_identical_to_plain": bool(int(off_b[-1]) == total_ids)}
+        # autotuned shape (untimed search), then the tuned batch as a prepared graph
+        t_tune = time.perf_counter()
+        tune = table.autotune(wl.queries)
+        t_tune = time.perf_counter() - t_tune
+        tuned = graph_steps(mdrq.BATCH_SHARED)
+        tuned.update({"speedup_vs_plain": tuned["value"] / value, "unit_rows": tune["unit_rows"],
+                      "image_kib": tune["image_kib"], "candidates": tune["candidates"],
+                      "autotune_s": t_tune, "autotune_plain_ms": tune["plain_ms"],
+                      "autotune_shared_default_ms": tune["shared_default_ms"],
+                      "autotune_shared_best_ms": tune["shared_ms"],
+                      "mode": "shared scan, autotuned shape (0 = built-in rule), replayed as a "
+                              "prepared CUDA graph"})
+        batched["tuned_graph"] = tuned
         table.set_batch_mode(mdrq.BATCH_PLAIN)
 
     # ---- learned range narrower: on this table when it is Z-sorted, else on its own
@@ -498,7 +536,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": cfg, "clocks": clocks, "e2e": e2e,
             "gpu_launches": timing["kernel_launches"], "roofline": roofline,
-            "cpu_baseline": cpu, "answer_ids_per_step": total_ids, "batched": batched,
+            "cpu_baseline": cpu, "answer_ids_per_step": total_ids, "plain_graph": plain_graph,
+            "batched": batched,
             "learned": learned, "serving": serving,
         }), flush=True)
     table.close()

@@ -311,7 +311,7 @@ int mdrq_inject_fault(mdrq_table *t, int kind, uint64_t arg);
  *
  * No table is made: the caller passes its device columns and receives the answer in
  * its own device buffer. The scan's scratch lives in a fixed array in device memory
- * inside the library, 512 KiB + 32 bytes on every GPU that loads the library, held
+ * inside the library, about 516 KiB on every GPU that loads the library, held
  * until the process exits; it limits the table to MDRQ_STATIC_MAX_ROWS rows.
  *
  *  cols[j], types[j], d, n   as mdrq_load_columns with cols_on_device = 1 (device
@@ -338,6 +338,39 @@ int mdrq_inject_fault(mdrq_table *t, int kind, uint64_t arg);
 int mdrq_query_static(const void *const *cols, const int32_t *types, uint32_t d, uint64_t n,
                       const mdrq_pred *preds, uint32_t npreds, uint32_t *ids, uint64_t capacity,
                       uint64_t *count, void *stream);
+
+/*
+ * Zone maps. At load the library records, for every column and every 128 consecutive
+ * rows, the minimum and maximum value (8 bytes per 128 rows: 1.6% of the column). A
+ * scan then decides a 128-row group of a predicate without reading it when the group's
+ * range lies outside [lo, hi] (no row qualifies) or inside it (every row does) — a
+ * block-level form of the VA-file's cell approximation (Sec. 2.2.3). This pays where
+ * the row order clusters values (a table sorted by a key, data loaded in time order)
+ * and costs one 8-byte read per group and predicate elsewhere.
+ *
+ * It also keeps one (min, max) pair per 4096-row tile. When a plain-mode batch has a
+ * predicate with a zone map in use, each query first lists the tiles its tile ranges do
+ * not rule out (runs of candidate tiles, at most 1024 per query, else one run from the
+ * first to the last candidate) and the scan visits only those tiles.
+ *
+ * mdrq_set_zone_maps: MDRQ_ZONES_AUTO (default) uses a column's map when its zones'
+ * mean width is below half of the column's range; MDRQ_ZONES_ALL uses every map;
+ * MDRQ_ZONES_OFF none. Applies to the plain and the windowed (learned) scan; answers
+ * never change. Errors: MDRQ_E_INVAL.
+ *
+ * mdrq_zone_scan_info: rows and tiles the last zone-pruned launch visited (0 if none
+ * ran). Synchronous. Errors: MDRQ_E_INVAL, MDRQ_E_CUDA.
+ *
+ * mdrq_zone_map_info: *used = 1 when queries on dimension `dim` read its zone map
+ * under the current setting; *mean_width = the mean zone width over the column's
+ * range (0..1). Either pointer may be NULL. Errors: MDRQ_E_INVAL (t NULL, dim >= d).
+ */
+#define MDRQ_ZONES_OFF 0
+#define MDRQ_ZONES_AUTO 1
+#define MDRQ_ZONES_ALL 2
+int mdrq_set_zone_maps(mdrq_table *t, int mode);
+int mdrq_zone_map_info(const mdrq_table *t, uint32_t dim, int *used, double *mean_width);
+int mdrq_zone_scan_info(mdrq_table *t, uint64_t *rows, uint64_t *tiles);
 
 /*
  * Shared-scan configuration and the autotuner. The shared scan (MDRQ_BATCH_SHARED)

@@ -496,7 +496,7 @@ __device__ __forceinline__ ulonglong2 run_of_node(const BoxNode &x, uint32_t nd)
 //     it, the crossing nodes left are kept whole, covering keys outside the box that the
 //     scan rejects. Ranges are sorted and adjacent ones merged.
 // (2) Per range, its exact row run through the model (prove_run) and its tiles of
-//     tile_rows rows from the run's 4-aligned start; the query's last range gets one
+//     tile_rows rows from the run's 128-aligned start; the query's last range gets one
 //     tile even when empty, so that its answer is closed.
 // Writes the query's windows to slots[q * kRangesPerQuery + i] with tile_start local to
 // the query, the range count to counts[q] and the tile total to qtiles[q].
@@ -690,7 +690,7 @@ __global__ void __launch_bounds__(kBoxThreads) mdrq_box_windows_kernel(
         if (i < nr) {
             if (!none)
                 prove_run(mv, s_w, keys, eps, rng[i].x, rng[i].y, &lbs[k], &ubs[k], &probes);
-            const unsigned long long rows = ubs[k] > lbs[k] ? ubs[k] - (lbs[k] & ~3ull) : 0;
+            const unsigned long long rows = ubs[k] > lbs[k] ? ubs[k] - (lbs[k] & ~127ull) : 0;
             tl[k] = rows ? (uint32_t)((rows + tile_rows - 1) / tile_rows) : (i + 1 == nr ? 1u : 0u);
         }
         mytiles += tl[k];
@@ -703,7 +703,7 @@ __global__ void __launch_bounds__(kBoxThreads) mdrq_box_windows_kernel(
         const uint32_t i = threadIdx.x * kBoxPer + k;
         if (i < nr) {
             DevWindow w;
-            w.row_begin = lbs[k] & ~3ull;
+            w.row_begin = lbs[k] & ~127ull;  // 128-row groups, as the zone maps
             w.row_first = lbs[k];
             w.row_end = ubs[k];
             w.tile_start = tpos;
@@ -784,19 +784,29 @@ __global__ void __launch_bounds__(1024) mdrq_window_base_kernel(const uint32_t *
 
 // compaction: query q's windows from its slots to windows[wbase[q] ..], tile starts
 // made global (one block per query)
-__global__ void __launch_bounds__(256) mdrq_window_fill_kernel(const DevWindow *slots, const uint32_t *counts,
+__global__ void __launch_bounds__(256) mdrq_window_fill_kernel(const DevWindow *slots, uint32_t per_query,
+                                                               const uint32_t *counts,
                                                                const unsigned long long *wbase,
                                                                const unsigned long long *tbase, DevWindow *windows)
 {
     const uint32_t q = blockIdx.x;
     const uint32_t cnt = counts[q];
     const unsigned long long wb = wbase[q], tb = tbase[q];
-    const DevWindow *src = slots + (size_t)q * kRangesPerQuery;
+    const DevWindow *src = slots + (size_t)q * per_query;
     for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
         DevWindow w = src[i];
         w.tile_start += tb;
         windows[wb + i] = w;
     }
+}
+
+int window_list(uint32_t nq, uint32_t per_query, const uint32_t *counts, const uint32_t *qtiles,
+                unsigned long long *wbase, unsigned long long *tbase, const DevWindow *slots, DevWindow *windows,
+                unsigned long long *totals, cudaStream_t s)
+{
+    mdrq_window_base_kernel<<<1, 1024, 0, s>>>(counts, qtiles, nq, wbase, tbase, totals);
+    mdrq_window_fill_kernel<<<nq, 256, 0, s>>>(slots, per_query, counts, wbase, tbase, windows);
+    return cuda_status(cudaGetLastError());
 }
 
 // ---------------------------------------------------------------- host
@@ -987,12 +997,16 @@ int learned_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std
     constexpr uint32_t kTile = (uint32_t)kWarps * 4 * 128;
     mdrq_box_windows_kernel<<<nlive, kBoxThreads, kBoxSmem, s>>>(mv, m->keys, m->max_error, qcells, m->ndims, kTile,
                                                                  m->slots, counts, qtiles, m->scratch + 1);
-    mdrq_window_base_kernel<<<1, 1024, 0, s>>>(counts, qtiles, nlive, wbase, tbase, m->totals);
-    mdrq_window_fill_kernel<<<nlive, 256, 0, s>>>(m->slots, counts, wbase, tbase, m->windows);
-    MDRQ_TRY_STATUS(cudaGetLastError());
+    st = window_list(nlive, kRangesPerQuery, counts, qtiles, wbase, tbase, m->slots, m->windows, m->totals, s);
+    if (st != MDRQ_OK)
+        return st;
     m->have_windows = true;
-    return launch_window_scan(t, q0, nlive, max_windows, m->totals + 1, ids, capacity, base_in, m->windows,
-                              m->totals, s);
+    bool zones = false;
+    for (uint32_t i = 0; i < nlive; ++i)
+        for (const DevPred &dp : enc[live[q0 + i]].preds)
+            zones = zones || dp.zone != nullptr;
+    return launch_window_scan(t, q0, nlive, max_windows, m->totals + 1, zones, 0, 3, ids, capacity, base_in,
+                              m->windows, m->totals, s);
 }
 
 int learned_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *probes)

@@ -22,10 +22,12 @@ using namespace mdrq;
 
 namespace mdrq {
 
-// The scan over per-query row windows (the learned range narrower's exact check).
+// The scan over per-query row windows (the learned range narrower's exact check);
+// ZONES: some predicate carries a zone map.
+template <bool ZONES>
 __global__ void __launch_bounds__(kScanThreads, 7) mdrq_scan_window_kernel(const __grid_constant__ ScanParams p)
 {
-    scan_cta<4, true>(p);
+    scan_cta<4, true, ZONES>(p);
 }
 
 // NaN count, minimum and maximum of a column. out[0] += NaNs; out[1] / out[2] hold the
@@ -66,6 +68,82 @@ __global__ void __launch_bounds__(kBlock)
         atomicMin(&out[1], mn);
         atomicMax(&out[2], mx);
     }
+}
+
+// Zone map of a column: zone[z] = bits of the minimum and maximum of rows
+// [128z, 128z + 128) (exact column values, ordered by key_of); width_sum += the zones'
+// widths (max - min) * inv_range. One warp per zone, grid-stride.
+__global__ void __launch_bounds__(256) mdrq_zone_kernel(const uint32_t *col, uint64_t n, uint32_t type, uint2 *zone,
+                                                        double inv_range, double *width_sum)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t nz = (n + (1u << kZoneShift) - 1) >> kZoneShift;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    double width = 0.0;
+    for (uint64_t z = (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); z < nz; z += warps) {
+        unsigned long long mn = ~0ull, mx = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint64_t r = (z << kZoneShift) + 32u * k + lane;
+            if (r < n) {
+                const unsigned long long key = key_of(col[r], type);
+                mn = key < mn ? key : mn;
+                mx = key > mx ? key : mx;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long a = __shfl_xor_sync(0xffffffffu, mn, o);
+            const unsigned long long b = __shfl_xor_sync(0xffffffffu, mx, o);
+            mn = a < mn ? a : mn;
+            mx = b > mx ? b : mx;
+        }
+        // back from keys to the value bits
+        uint32_t lo, hi;
+        if (type == kTypeF32) {
+            lo = (mn & 0x80000000ull) ? (uint32_t)mn ^ 0x80000000u : ~(uint32_t)mn;
+            hi = (mx & 0x80000000ull) ? (uint32_t)mx ^ 0x80000000u : ~(uint32_t)mx;
+        } else {
+            lo = (uint32_t)mn ^ 0x80000000u;
+            hi = (uint32_t)mx ^ 0x80000000u;
+        }
+        if (lane == 0) {
+            zone[z] = make_uint2(lo, hi);
+            const double w = type == kTypeF32 ? ((double)__uint_as_float(hi) - (double)__uint_as_float(lo)) * inv_range
+                                              : ((double)(int)hi - (double)(int)lo) * inv_range;
+            width += w <= 1.0 ? w : 1.0;  // (a non-finite width counts as the whole range)
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        width += __shfl_xor_sync(0xffffffffu, width, o);
+    if (lane == 0 && width > 0.0)
+        atomicAdd(width_sum, width);
+}
+
+// Tile zone map: tzone[i] = bits of the minimum and maximum of the 32 zones of rows
+// [4096i, 4096i + 4096) (of the zones that exist). One thread per tile.
+__global__ void __launch_bounds__(256) mdrq_tile_zone_kernel(const uint2 *zone, uint64_t nz, uint32_t type,
+                                                             uint2 *tzone, uint64_t nt)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt)
+        return;
+    unsigned long long mn = ~0ull, mx = 0;
+    uint2 lo = make_uint2(0, 0), hi = make_uint2(0, 0);
+    for (uint64_t z = i * 32; z < nz && z < i * 32 + 32; ++z) {
+        const uint2 v = zone[z];
+        const unsigned long long a = key_of(v.x, type), b = key_of(v.y, type);
+        if (a < mn) {
+            mn = a;
+            lo = v;
+        }
+        if (b > mx) {
+            mx = b;
+            hi = v;
+        }
+    }
+    tzone[i] = make_uint2(lo.x, hi.y);
 }
 
 // out[s] = col[floor(s * n / S)] for s < S: a strided sample for selectivity estimates
@@ -196,6 +274,9 @@ int encode_query(const mdrq_table *t, const mdrq_pred *preds, uint32_t npreds, E
         q.dims.push_back(cd.dim);
         DevPred sp;
         sp.col = t->cols[cd.dim].ptr;
+        sp.zone = t->zone_mode == MDRQ_ZONES_ALL || (t->zone_mode == MDRQ_ZONES_AUTO && t->cols[cd.dim].zone_keep)
+                      ? t->cols[cd.dim].zone
+                      : nullptr;
         sp.type = (uint32_t)t->cols[cd.dim].type;
         sp.lo = bits[cd.dim].first;
         sp.hi = bits[cd.dim].second;
@@ -236,6 +317,26 @@ template <int U>
 constexpr uint64_t tile_rows()
 {
     return (uint64_t)kWarps * U * 128;
+}
+
+// With event timing on (mdrq_scan_timing): the next event pair of the table, its first
+// event recorded on s; *evp stays null when timing is off.
+int timing_begin(mdrq_table *t, cudaStream_t s, cudaEvent_t **evp)
+{
+    *evp = nullptr;
+    if (!t->timing)
+        return MDRQ_OK;
+    if (t->ev.size() < 2 * (t->ev_used + 1)) {
+        cudaEvent_t a, b;
+        MDRQ_TRY(cudaEventCreate(&a));
+        MDRQ_TRY(cudaEventCreate(&b));
+        t->ev.push_back(a);
+        t->ev.push_back(b);
+    }
+    *evp = &t->ev[2 * t->ev_used];
+    ++t->ev_used;
+    MDRQ_TRY(cudaEventRecord((*evp)[0], s));
+    return MDRQ_OK;
 }
 
 // Launch one scan over the queries qs[0 .. nq) (all non-empty), whose predicates are
@@ -292,17 +393,10 @@ int launch_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t scanned_column
     }
 
     cudaEvent_t *evp = nullptr;
-    if (t->timing) {
-        if (t->ev.size() < 2 * (t->ev_used + 1)) {
-            cudaEvent_t a, b;
-            MDRQ_TRY(cudaEventCreate(&a));
-            MDRQ_TRY(cudaEventCreate(&b));
-            t->ev.push_back(a);
-            t->ev.push_back(b);
-        }
-        evp = &t->ev[2 * t->ev_used];
-        ++t->ev_used;
-        MDRQ_TRY(cudaEventRecord(evp[0], s));
+    {
+        const int st = timing_begin(t, s, &evp);
+        if (st != MDRQ_OK)
+            return st;
     }
     if (ui == 2)
         mdrq_scan_kernel<4><<<grid, kScanThreads, 0, s>>>(p);
@@ -325,13 +419,13 @@ int launch_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t scanned_column
 }
 
 int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t max_windows,
-                       const unsigned long long *nwindows, uint32_t *ids, uint64_t capacity,
-                       const unsigned long long *base_in, const DevWindow *windows,
+                       const unsigned long long *nwindows, bool zones, uint64_t alg_bytes, uint32_t helper_kernels,
+                       uint32_t *ids, uint64_t capacity, const unsigned long long *base_in, const DevWindow *windows,
                        const unsigned long long *total_tiles, cudaStream_t s)
 {
     if (t->blocks_per_sm_window == 0) {
-        MDRQ_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->blocks_per_sm_window, mdrq_scan_window_kernel,
-                                                               kScanThreads, 0));
+        MDRQ_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->blocks_per_sm_window,
+                                                               mdrq_scan_window_kernel<true>, kScanThreads, 0));
         t->blocks_per_sm_window = std::max(1, t->blocks_per_sm_window);
     }
     // a query's windows are disjoint runs of the table; each adds at most one partial
@@ -340,7 +434,7 @@ int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t max_win
     const uint32_t grid = (uint32_t)std::max<uint64_t>(
         1, std::min<uint64_t>((uint64_t)t->sm_count * t->blocks_per_sm_window, max_tiles));
     const uint32_t laps = (uint32_t)(max_tiles >> t->ring_bits) + 1;
-    if ((uint64_t)t->tag_next + laps > kTagLimit) {
+    if (t->graph_capture || (uint64_t)t->tag_next + laps > kTagLimit) {
         MDRQ_TRY(cudaMemsetAsync(t->tile_state, 0, ((size_t)1 << t->ring_bits) * 8, s));
         t->tag_next = 1;
     }
@@ -364,12 +458,24 @@ int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t max_win
     p.windows = windows;
     p.nwindows_dev = nwindows;
     p.total_tiles_dev = total_tiles;
-    mdrq_scan_window_kernel<<<grid, kScanThreads, 0, s>>>(p);
+    cudaEvent_t *evp = nullptr;
+    {
+        const int st = timing_begin(t, s, &evp);
+        if (st != MDRQ_OK)
+            return st;
+    }
+    (zones ? mdrq_scan_window_kernel<true> : mdrq_scan_window_kernel<false>)<<<grid, kScanThreads, 0, s>>>(p);
     MDRQ_TRY(cudaGetLastError());
+    if (evp)
+        MDRQ_TRY(cudaEventRecord(evp[1], s));
     t->tag_next += laps;
     t->last_launches += 1;
-    if (t->timing)
-        t->acc_kernels += 4;  // box-windows, base, fill and scan kernels
+    t->last_bytes += alg_bytes;
+    if (t->timing) {
+        t->acc_scans += 1;
+        t->acc_kernels += 1 + helper_kernels;
+        t->acc_bytes += alg_bytes;
+    }
     return MDRQ_OK;
 }
 
@@ -496,10 +602,16 @@ int enqueue_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std
     for (size_t c0 = 0; !shared && !learned_mode && c0 < nlive; c0 += per_launch) {
         const uint32_t cnt = (uint32_t)std::min<uint64_t>(per_launch, nlive - c0);
         uint64_t cols = 0;
-        for (size_t i = c0; i < c0 + cnt; ++i)
+        bool zones = false;
+        for (size_t i = c0; i < c0 + cnt; ++i) {
             cols += enc[live[i]].scanned_columns;
+            for (const DevPred &dp : enc[live[i]].preds)
+                zones = zones || dp.zone != nullptr;
+        }
         const unsigned long long *base = c0 == 0 ? nullptr : t->offsets_dev + live[c0 - 1] + 1;
-        st = launch_scan(t, (uint32_t)c0, cnt, cols, out, capacity, base, s);
+        // zone maps in use: scan only the tiles they do not rule out
+        st = zones ? zone_batch(t, enc, live, (uint32_t)c0, cnt, cols, out, capacity, base, s)
+                   : launch_scan(t, (uint32_t)c0, cnt, cols, out, capacity, base, s);
         if (st != MDRQ_OK) {
             reset_scratch(t, s);
             return st;
@@ -603,9 +715,12 @@ void destroy(mdrq_table *t)
     cudaDeviceSynchronize();
     for (void *p : t->owned)
         cudaFree(p);
+    for (ColumnInfo &c : t->cols)
+        cudaFree(c.zone);
     cudaFree(t->scratch);
     cudaFree(t->offsets_dev);
     shared_scan_free(t);
+    zone_windows_free(t);
     learned_free(t);
     cudaFree(t->ids_stage);
     cudaFree(t->dq_dev);
@@ -617,6 +732,49 @@ void destroy(mdrq_table *t)
         cudaEventDestroy(e);
     (void)cudaGetLastError();
     delete t;
+}
+
+// Zone maps of every column (one read of the table) and their mean width relative to
+// the column's range; MDRQ_ZONES_AUTO uses a column's map when that mean is below
+// kZoneKeepWidth, i.e. when the row order clusters its values.
+constexpr double kZoneKeepWidth = 0.5;
+
+int build_zone_maps(mdrq_table *t, cudaStream_t s)
+{
+    const uint64_t nz = (t->n + (1u << kZoneShift) - 1) >> kZoneShift;
+    const uint64_t nt = (t->n + kZoneTileRows - 1) / kZoneTileRows;
+    double *sums = nullptr;
+    MDRQ_TRY(cudaMalloc(&sums, (size_t)t->d * 8));
+    int st = cuda_status(cudaMemsetAsync(sums, 0, (size_t)t->d * 8, s));
+    for (uint32_t j = 0; j < t->d && st == MDRQ_OK; ++j) {
+        ColumnInfo &c = t->cols[j];
+        // 128-row zones, then one per 4096-row tile after them
+        if ((st = cuda_status(cudaMalloc(&c.zone, (size_t)(nz + nt) * sizeof(uint2)))))
+            break;
+        const double range = bound_value(c.max_bits, c.type) - bound_value(c.min_bits, c.type);
+        const double inv = std::isfinite(range) && range > 0 ? 1.0 / range : 0.0;
+        const uint32_t grid = (uint32_t)std::min<uint64_t>((nz + 7) / 8, (uint64_t)t->sm_count * 16);
+        mdrq_zone_kernel<<<std::max(1u, grid), 256, 0, s>>>((const uint32_t *)c.ptr, t->n, (uint32_t)c.type, c.zone,
+                                                             inv, sums + j);
+        mdrq_tile_zone_kernel<<<(uint32_t)((nt + 255) / 256), 256, 0, s>>>(c.zone, nz, (uint32_t)c.type, c.zone + nz,
+                                                                           nt);
+        st = cuda_status(cudaGetLastError());
+    }
+    std::vector<double> h((size_t)t->d, 0.0);
+    if (st == MDRQ_OK)
+        st = cuda_status(cudaMemcpyAsync(h.data(), sums, (size_t)t->d * 8, cudaMemcpyDeviceToHost, s));
+    if (st == MDRQ_OK)
+        st = cuda_status(cudaStreamSynchronize(s));
+    cudaFree(sums);
+    if (st != MDRQ_OK)
+        return st;
+    for (uint32_t j = 0; j < t->d; ++j) {
+        ColumnInfo &c = t->cols[j];
+        const double range = bound_value(c.max_bits, c.type) - bound_value(c.min_bits, c.type);
+        c.zone_width = nz ? h[j] / (double)nz : 1.0;
+        c.zone_keep = std::isfinite(range) && c.zone_width < kZoneKeepWidth;
+    }
+    return MDRQ_OK;
 }
 
 int load(const void *const *cols, const int32_t *types, uint32_t d, uint64_t n, int cols_on_device,
@@ -705,7 +863,7 @@ int load(const void *const *cols, const int32_t *types, uint32_t d, uint64_t n, 
             c.sample[i] = bound_value(h_sample[(size_t)j * S + i], c.type);
         std::sort(c.sample.begin(), c.sample.end());
     }
-    return MDRQ_OK;
+    return build_zone_maps(t, s);
 }
 
 }  // namespace mdrq
@@ -845,6 +1003,26 @@ int mdrq_learn_info(const mdrq_table *t, uint64_t *max_error, uint32_t *segments
 int mdrq_learn_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *widenings)
 {
     return learned_window_rows(t, rows, widenings);
+}
+
+int mdrq_set_zone_maps(mdrq_table *t, int mode)
+{
+    if (!t || (mode != MDRQ_ZONES_OFF && mode != MDRQ_ZONES_AUTO && mode != MDRQ_ZONES_ALL))
+        return MDRQ_E_INVAL;
+    t->zone_mode = mode;
+    return MDRQ_OK;
+}
+
+int mdrq_zone_map_info(const mdrq_table *t, uint32_t dim, int *used, double *mean_width)
+{
+    if (!t || dim >= t->d)
+        return MDRQ_E_INVAL;
+    const mdrq::ColumnInfo &c = t->cols[dim];
+    if (used)
+        *used = t->n > 0 && (t->zone_mode == MDRQ_ZONES_ALL || (t->zone_mode == MDRQ_ZONES_AUTO && c.zone_keep));
+    if (mean_width)
+        *mean_width = c.zone_width;
+    return MDRQ_OK;
 }
 
 int mdrq_inject_fault(mdrq_table *t, int kind, uint64_t arg)

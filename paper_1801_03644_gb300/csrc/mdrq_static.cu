@@ -53,7 +53,7 @@ constexpr int kMaxDevices = 64;
 
 }  // namespace
 
-// The fixed scratch: (4 + 65536 + 2 + 384) * 8 bytes = 515.1 KiB per device that loads
+// The fixed scratch: (4 + 65536 + 2 + 512) * 8 bytes = 516.1 KiB per device that loads
 // the library, held until the process exits.
 static __device__ __align__(256) unsigned long long g_scan_scratch[kScratchWords];
 
@@ -163,6 +163,7 @@ extern "C" int mdrq_query_static(const void *const *cols, const int32_t *types, 
             lo_v[k] = lo;
             hi_v[k] = hi;
             pred[k].col = n > 0 ? cols[q.dim] : nullptr;
+            pred[k].zone = nullptr;
             pred[k].type = (uint32_t)types[q.dim];
             pred[k].lo = lb;
             pred[k].hi = hb;

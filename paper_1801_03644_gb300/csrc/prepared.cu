@@ -42,7 +42,10 @@ void release(mdrq_prepared *p)
         cudaGraphDestroy(p->graph);
     if (p->capture)
         cudaStreamDestroy(p->capture);
-    mdrq::destroy(p->shadow);  // owns no columns
+    if (p->shadow)
+        for (mdrq::ColumnInfo &c : p->shadow->cols)
+            c.zone = nullptr;  // the parent's
+    mdrq::destroy(p->shadow);  // owns no columns and no zone maps
     (void)cudaGetLastError();
     delete p;
 }
@@ -70,6 +73,7 @@ int prepare(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, uin
     sh->shared_unit_rows = t->shared_unit_rows;
     sh->shared_image_words = t->shared_image_words;
     sh->auto_mode = t->auto_mode;
+    sh->zone_mode = t->zone_mode;
     int st = alloc_scratch(sh, s);
     if (st != MDRQ_OK)
         return st;

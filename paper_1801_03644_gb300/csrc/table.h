@@ -19,6 +19,9 @@ struct ColumnInfo {
     int32_t type = MDRQ_F32;
     uint32_t min_bits = 0, max_bits = 0;  // exact column minimum / maximum (n > 0)
     std::vector<double> sample;           // sorted
+    uint2 *zone = nullptr;                // zone map (device, owned): min / max bits per 128 rows
+    double zone_width = 1.0;              // mean zone width / column range
+    bool zone_keep = false;               // MDRQ_ZONES_AUTO reads this column's map
 };
 
 // a2: one query after encoding
@@ -30,6 +33,7 @@ struct EncodedQuery {
 };
 
 struct SharedScanState;  // device buffers of the batched shared scan (batched.cu)
+struct ZoneWindows;      // device buffers of the zone-pruned scan (zones.cu)
 struct LearnedModel;     // learned range narrower (learned.cu)
 
 }  // namespace mdrq
@@ -86,6 +90,9 @@ struct mdrq_table {
     int auto_mode = -1;               // mode AUTO takes for 32+ queries, once measured (-1: rule)
     mdrq::LearnedModel *learned = nullptr;
 
+    int zone_mode = MDRQ_ZONES_AUTO;  // mdrq_set_zone_maps
+    mdrq::ZoneWindows *zwin = nullptr;
+
     // set on the private table of a prepared batch while its launches are captured
     bool graph_capture = false;
 
@@ -138,10 +145,27 @@ int shared_scan_write(mdrq_table *t, SharedScanState &S, uint32_t *ids, uint64_t
 
 // mdrq.cu: one windowed scan launch over nq live queries whose rows and tiles the device
 // holds in windows / total_tiles (written by earlier kernels on the same stream).
+// zones: compile the zone-map check in; alg_bytes: the launch's algorithmic bytes for
+// the timing counters; helper_kernels: kernels launched before it for its windows.
 int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t max_windows,
-                       const unsigned long long *nwindows, uint32_t *ids, uint64_t capacity,
-                       const unsigned long long *base_in, const DevWindow *windows,
+                       const unsigned long long *nwindows, bool zones, uint64_t alg_bytes, uint32_t helper_kernels,
+                       uint32_t *ids, uint64_t capacity, const unsigned long long *base_in, const DevWindow *windows,
                        const unsigned long long *total_tiles, cudaStream_t s);
+
+// learned.cu: the window list of nq queries from per-query slots (per_query windows
+// each; counts[q] used, qtiles[q] tiles, tile_start local to the query): exclusive
+// scans into wbase / tbase, totals[0] = tiles, totals[1] = windows, then compaction.
+int window_list(uint32_t nq, uint32_t per_query, const uint32_t *counts, const uint32_t *qtiles,
+                unsigned long long *wbase, unsigned long long *tbase, const DevWindow *slots, DevWindow *windows,
+                unsigned long long *totals, cudaStream_t s);
+
+// zones.cu: the plain scan of live queries q0 .. q0 + nlive restricted to the row tiles
+// their zone maps do not rule out (one windowed launch)
+int zone_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std::vector<uint32_t> &live, uint32_t q0,
+               uint32_t nlive, uint64_t scanned_columns, uint32_t *ids, uint64_t capacity,
+               const unsigned long long *base_in, cudaStream_t s);
+void zone_windows_free(mdrq_table *t);
+int zone_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *tiles);
 
 // learned.cu
 int learn(mdrq_table *t, const uint32_t *dims, uint32_t ndims, int kind, cudaStream_t s);

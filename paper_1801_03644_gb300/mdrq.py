@@ -53,11 +53,13 @@ EXPORTS = ["mdrq_load_columns", "mdrq_query", "mdrq_query_batch", "mdrq_free",
            "mdrq_learn_window_rows", "mdrq_server_start", "mdrq_server_submit", "mdrq_server_wait",
            "mdrq_server_release", "mdrq_server_stats", "mdrq_server_stop", "mdrq_prepare_batch",
            "mdrq_prepared_launch", "mdrq_prepared_wait", "mdrq_prepared_kernels", "mdrq_prepared_free",
-           "mdrq_set_shared_config", "mdrq_autotune"]
+           "mdrq_set_shared_config", "mdrq_autotune", "mdrq_set_zone_maps", "mdrq_zone_map_info",
+           "mdrq_zone_scan_info"]
 
 FAULT_SKIP_TILES, FAULT_NOMEM = 1, 2
 BATCH_AUTO, BATCH_PLAIN, BATCH_SHARED, BATCH_LEARNED = 0, 1, 2, 3
 MODEL_PLA, MODEL_MLP = 1, 2
+ZONES_OFF, ZONES_AUTO, ZONES_ALL = 0, 1, 2
 
 STATIC_MAX_ROWS = 1 << 28  # MDRQ_STATIC_MAX_ROWS
 
@@ -121,6 +123,12 @@ def lib():
         L.mdrq_query_static.restype = ctypes.c_int
         L.mdrq_query_static.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(i32), u32, u64,
                                         ctypes.POINTER(Pred), u32, vp, u64, ctypes.POINTER(u64), vp]
+        L.mdrq_set_zone_maps.restype = ctypes.c_int
+        L.mdrq_set_zone_maps.argtypes = [vp, ctypes.c_int]
+        L.mdrq_zone_map_info.restype = ctypes.c_int
+        L.mdrq_zone_map_info.argtypes = [vp, u32, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+        L.mdrq_zone_scan_info.restype = ctypes.c_int
+        L.mdrq_zone_scan_info.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]
         L.mdrq_set_shared_config.restype = ctypes.c_int
         L.mdrq_set_shared_config.argtypes = [vp, u32, u32]
         L.mdrq_autotune.restype = ctypes.c_int
@@ -349,6 +357,27 @@ class Table:
         if st != OK:
             raise MDRQError(st, "mdrq_query_batch")
         return out[: int(off[-1])], off
+
+    def set_zone_maps(self, mode: int):
+        """``mdrq_set_zone_maps``: ZONES_OFF, ZONES_AUTO or ZONES_ALL."""
+        st = lib().mdrq_set_zone_maps(self._h, int(mode))
+        if st != OK:
+            raise MDRQError(st, "mdrq_set_zone_maps")
+
+    def zone_map_info(self, dim: int) -> dict:
+        used, width = ctypes.c_int(0), ctypes.c_double(0)
+        st = lib().mdrq_zone_map_info(self._h, int(dim), ctypes.byref(used), ctypes.byref(width))
+        if st != OK:
+            raise MDRQError(st, "mdrq_zone_map_info")
+        return {"used": bool(used.value), "mean_width": width.value}
+
+    def zone_scan_info(self) -> tuple:
+        """(rows, tiles) the last zone-pruned launch visited."""
+        r, k = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        st = lib().mdrq_zone_scan_info(self._h, ctypes.byref(r), ctypes.byref(k))
+        if st != OK:
+            raise MDRQError(st, "mdrq_zone_scan_info")
+        return int(r.value), int(k.value)
 
     def set_shared_config(self, unit_rows: int = 0, image_kib: int = 0):
         """``mdrq_set_shared_config``: the shared scan's rows per warp unit and chunk

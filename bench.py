@@ -219,27 +219,46 @@ def timed_steps(torch, stream, step, steps, barrier):
     return e0.elapsed_time(e1), last
 
 
-def learned_leg(args, table, enc, step, plain_value, nq, total_ids, world, barrier, stream):
-    """Learned range narrower (PLA and MLP) on a Z-sorted table: queries/s, speedup over
-    the plain scan of the same batch, model error and window coverage."""
+def learned_leg(args, table, enc, step, nq, total_ids, world, barrier, stream):
+    """Learned range narrower (PLA and MLP) and zone-map tile pruning on a Z-sorted table:
+    queries/s and speedup over the plain scan of the same batch with zone maps off
+    (every tile read), model error and window coverage."""
     import torch
     from paper_1801_03644_gb300 import mdrq, shards
-    out = {}
-    for name, model in (("pla", mdrq.MODEL_PLA), ("mlp", mdrq.MODEL_MLP)):
-        info = table.learn([0, 1, 2, 3], model)
-        table.set_batch_mode(mdrq.BATCH_LEARNED)
+
+    def timed(mode, zones):
+        table.set_batch_mode(mode)
+        table.set_zone_maps(zones)
         for _ in range(args.warmup):
             step()
-        lms, off_l = timed_steps(torch, stream, step, args.steps, barrier)
-        lms = shards.max_over_ranks(lms)
+        ms, off = timed_steps(torch, stream, step, args.steps, barrier)
+        ms = shards.max_over_ranks(ms)
+        return world * nq * args.steps / (ms / 1e3), ms / args.steps, off
+
+    base, base_ms, off_b = timed(mdrq.BATCH_PLAIN, mdrq.ZONES_OFF)
+    zval, zms, off_z = timed(mdrq.BATCH_PLAIN, mdrq.ZONES_AUTO)
+    zrows, ztiles = table.zone_scan_info()
+    out = {"plain_no_zone_maps": {"value": base, "unit": UNIT, "ms_per_step": base_ms,
+                                  "answers_identical_to_plain": bool(int(off_b[-1]) == total_ids)},
+           "zone_pruned_plain": {"value": zval, "unit": UNIT, "ms_per_step": zms,
+                                 "speedup_vs_plain": zval / base, "rows_visited_per_query": zrows / nq,
+                                 "tiles_visited": ztiles,
+                                 "answers_identical_to_plain": bool(int(off_z[-1]) == total_ids)}}
+    for name, model in (("pla", mdrq.MODEL_PLA), ("mlp", mdrq.MODEL_MLP)):
+        info = table.learn([0, 1, 2, 3], model)
+        lvalue, lms, off_l = timed(mdrq.BATCH_LEARNED, mdrq.ZONES_AUTO)
         rows, widen = table.learn_window_rows()
-        lvalue = world * nq * args.steps / (lms / 1e3)
-        out[name] = {"value": lvalue, "unit": UNIT, "ms_per_step": lms / args.steps,
-                     "speedup_vs_plain": lvalue / plain_value, "max_error_rows": info["max_error"],
+        out[name] = {"value": lvalue, "unit": UNIT, "ms_per_step": lms,
+                     "speedup_vs_plain": lvalue / base, "speedup_vs_zone_pruned": lvalue / zval,
+                     "max_error_rows": info["max_error"],
                      "segments": info["segments"], "train_ms": info["train_ms"],
                      "window_rows_per_query": rows / nq, "window_widenings": widen,
                      "answers_identical_to_plain": bool(int(off_l[-1]) == total_ids)}
+        if name == "pla":
+            v0, ms0, _ = timed(mdrq.BATCH_LEARNED, mdrq.ZONES_OFF)
+            out[name]["without_zone_maps"] = {"value": v0, "ms_per_step": ms0}
     table.set_batch_mode(mdrq.BATCH_PLAIN)
+    table.set_zone_maps(mdrq.ZONES_AUTO)
     return out
 
 
@@ -265,14 +284,8 @@ def learned_workload_leg(args, world, barrier):
         return o
 
     nq = len(wl.queries)
-    for _ in range(args.warmup):
-        step()
-    ms, _ = timed_steps(torch, stream, step, args.steps, barrier)
-    ms = shards.max_over_ranks(ms)
-    plain = world * nq * args.steps / (ms / 1e3)
-    res = {"workload": wl.name, "recipe": wl.recipe, "plain_value": plain, "unit": UNIT,
-           "plain_ms_per_step": ms / args.steps, "answer_ids_per_step": total}
-    res.update(learned_leg(args, table, enc, step, plain, nq, total, world, barrier, stream))
+    res = {"workload": wl.name, "recipe": wl.recipe, "unit": UNIT, "answer_ids_per_step": total}
+    res.update(learned_leg(args, table, enc, step, nq, total, world, barrier, stream))
     table.close()
     return res
 
@@ -463,7 +476,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     # ---- learned range narrower: on this table when it is Z-sorted, else on its own
     learned = None
     if args.workload == "zorder_learned":
-        learned = learned_leg(args, table, enc, step, value, nq, total_ids, world, barrier, stream)
+        learned = learned_leg(args, table, enc, step, nq, total_ids, world, barrier, stream)
 
     # ---- end to end: host query descriptors in, host answers out (pinned)
     e2e = None

@@ -340,23 +340,18 @@ int mdrq_query_static(const void *const *cols, const int32_t *types, uint32_t d,
                       uint64_t *count, void *stream);
 
 /*
- * Zone maps. At load the library records, for every column and every 128 consecutive
- * rows, the minimum and maximum value (8 bytes per 128 rows: 1.6% of the column). A
- * scan then decides a 128-row group of a predicate without reading it when the group's
- * range lies outside [lo, hi] (no row qualifies) or inside it (every row does) — a
- * block-level form of the VA-file's cell approximation (Sec. 2.2.3). This pays where
- * the row order clusters values (a table sorted by a key, data loaded in time order)
- * and costs one 8-byte read per group and predicate elsewhere.
- *
- * It also keeps one (min, max) pair per 4096-row tile. When a plain-mode batch has a
- * predicate with a zone map in use, each query first lists the tiles its tile ranges do
- * not rule out (runs of candidate tiles, at most 1024 per query, else one run from the
- * first to the last candidate) and the scan visits only those tiles.
+ * Zone maps. At load the library records, for every column and every 4096-row tile,
+ * the minimum and maximum value (8 bytes per 4096 rows). When a plain-mode batch has a
+ * predicate whose column's zone map is in use, each query first lists the tiles whose
+ * ranges meet all of its intervals — the others cannot hold an answer; this is the
+ * VA-file's pruning of cells that miss the query (Sec. 2.2.3), applied to row tiles —
+ * as runs of candidate tiles (at most 1024 per query, else one run from the first to
+ * the last candidate), and the scan visits only those tiles. This pays where the row
+ * order clusters values (a table sorted by a key, data loaded in time order).
  *
  * mdrq_set_zone_maps: MDRQ_ZONES_AUTO (default) uses a column's map when its zones'
  * mean width is below half of the column's range; MDRQ_ZONES_ALL uses every map;
- * MDRQ_ZONES_OFF none. Applies to the plain and the windowed (learned) scan; answers
- * never change. Errors: MDRQ_E_INVAL.
+ * MDRQ_ZONES_OFF none (every tile is read). Answers never change. Errors: MDRQ_E_INVAL.
  *
  * mdrq_zone_scan_info: rows and tiles the last zone-pruned launch visited (0 if none
  * ran). Synchronous. Errors: MDRQ_E_INVAL, MDRQ_E_CUDA.

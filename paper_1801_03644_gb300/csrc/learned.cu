@@ -703,7 +703,7 @@ __global__ void __launch_bounds__(kBoxThreads) mdrq_box_windows_kernel(
         const uint32_t i = threadIdx.x * kBoxPer + k;
         if (i < nr) {
             DevWindow w;
-            w.row_begin = lbs[k] & ~127ull;  // 128-row groups, as the zone maps
+            w.row_begin = lbs[k] & ~127ull;  // whole 128-row groups (aligned 512-byte loads)
             w.row_first = lbs[k];
             w.row_end = ubs[k];
             w.tile_start = tpos;
@@ -1001,12 +1001,8 @@ int learned_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std
     if (st != MDRQ_OK)
         return st;
     m->have_windows = true;
-    bool zones = false;
-    for (uint32_t i = 0; i < nlive; ++i)
-        for (const DevPred &dp : enc[live[q0 + i]].preds)
-            zones = zones || dp.zone != nullptr;
-    return launch_window_scan(t, q0, nlive, max_windows, m->totals + 1, zones, 0, 3, ids, capacity, base_in,
-                              m->windows, m->totals, s);
+    return launch_window_scan(t, q0, nlive, max_windows, m->totals + 1, 0, 3, ids, capacity, base_in, m->windows,
+                              m->totals, s);
 }
 
 int learned_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *probes)

@@ -22,12 +22,11 @@ using namespace mdrq;
 
 namespace mdrq {
 
-// The scan over per-query row windows (the learned range narrower's exact check);
-// ZONES: some predicate carries a zone map.
-template <bool ZONES>
+// The scan over per-query row windows (the learned range narrower's exact check, and
+// the tiles the zone maps leave).
 __global__ void __launch_bounds__(kScanThreads, 7) mdrq_scan_window_kernel(const __grid_constant__ ScanParams p)
 {
-    scan_cta<4, true, ZONES>(p);
+    scan_cta<4, true>(p);
 }
 
 // NaN count, minimum and maximum of a column. out[0] += NaNs; out[1] / out[2] hold the
@@ -70,26 +69,23 @@ __global__ void __launch_bounds__(kBlock)
     }
 }
 
-// Zone map of a column: zone[z] = bits of the minimum and maximum of rows
-// [128z, 128z + 128) (exact column values, ordered by key_of); width_sum += the zones'
-// widths (max - min) * inv_range. One warp per zone, grid-stride.
+// Zone map of a column: zone[i] = bits of the minimum and maximum of rows
+// [4096i, 4096i + 4096) (exact column values, ordered by key_of); width_sum += the
+// zones' widths (max - min) * inv_range. One warp per zone, grid-stride.
 __global__ void __launch_bounds__(256) mdrq_zone_kernel(const uint32_t *col, uint64_t n, uint32_t type, uint2 *zone,
                                                         double inv_range, double *width_sum)
 {
     const int lane = threadIdx.x & 31;
-    const uint64_t nz = (n + (1u << kZoneShift) - 1) >> kZoneShift;
+    const uint64_t nz = (n + kZoneTileRows - 1) / kZoneTileRows;
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
     double width = 0.0;
     for (uint64_t z = (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); z < nz; z += warps) {
         unsigned long long mn = ~0ull, mx = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint64_t r = (z << kZoneShift) + 32u * k + lane;
-            if (r < n) {
-                const unsigned long long key = key_of(col[r], type);
-                mn = key < mn ? key : mn;
-                mx = key > mx ? key : mx;
-            }
+        const uint64_t r0 = z * kZoneTileRows, r1 = r0 + kZoneTileRows < n ? r0 + kZoneTileRows : n;
+        for (uint64_t r = r0 + lane; r < r1; r += 32) {
+            const unsigned long long key = key_of(col[r], type);
+            mn = key < mn ? key : mn;
+            mx = key > mx ? key : mx;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -119,31 +115,6 @@ __global__ void __launch_bounds__(256) mdrq_zone_kernel(const uint32_t *col, uin
         width += __shfl_xor_sync(0xffffffffu, width, o);
     if (lane == 0 && width > 0.0)
         atomicAdd(width_sum, width);
-}
-
-// Tile zone map: tzone[i] = bits of the minimum and maximum of the 32 zones of rows
-// [4096i, 4096i + 4096) (of the zones that exist). One thread per tile.
-__global__ void __launch_bounds__(256) mdrq_tile_zone_kernel(const uint2 *zone, uint64_t nz, uint32_t type,
-                                                             uint2 *tzone, uint64_t nt)
-{
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nt)
-        return;
-    unsigned long long mn = ~0ull, mx = 0;
-    uint2 lo = make_uint2(0, 0), hi = make_uint2(0, 0);
-    for (uint64_t z = i * 32; z < nz && z < i * 32 + 32; ++z) {
-        const uint2 v = zone[z];
-        const unsigned long long a = key_of(v.x, type), b = key_of(v.y, type);
-        if (a < mn) {
-            mn = a;
-            lo = v;
-        }
-        if (b > mx) {
-            mx = b;
-            hi = v;
-        }
-    }
-    tzone[i] = make_uint2(lo.x, hi.y);
 }
 
 // out[s] = col[floor(s * n / S)] for s < S: a strided sample for selectivity estimates
@@ -419,13 +390,13 @@ int launch_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t scanned_column
 }
 
 int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t max_windows,
-                       const unsigned long long *nwindows, bool zones, uint64_t alg_bytes, uint32_t helper_kernels,
+                       const unsigned long long *nwindows, uint64_t alg_bytes, uint32_t helper_kernels,
                        uint32_t *ids, uint64_t capacity, const unsigned long long *base_in, const DevWindow *windows,
                        const unsigned long long *total_tiles, cudaStream_t s)
 {
     if (t->blocks_per_sm_window == 0) {
-        MDRQ_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->blocks_per_sm_window,
-                                                               mdrq_scan_window_kernel<true>, kScanThreads, 0));
+        MDRQ_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&t->blocks_per_sm_window, mdrq_scan_window_kernel,
+                                                               kScanThreads, 0));
         t->blocks_per_sm_window = std::max(1, t->blocks_per_sm_window);
     }
     // a query's windows are disjoint runs of the table; each adds at most one partial
@@ -464,7 +435,7 @@ int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t max_win
         if (st != MDRQ_OK)
             return st;
     }
-    (zones ? mdrq_scan_window_kernel<true> : mdrq_scan_window_kernel<false>)<<<grid, kScanThreads, 0, s>>>(p);
+    mdrq_scan_window_kernel<<<grid, kScanThreads, 0, s>>>(p);
     MDRQ_TRY(cudaGetLastError());
     if (evp)
         MDRQ_TRY(cudaEventRecord(evp[1], s));
@@ -741,23 +712,19 @@ constexpr double kZoneKeepWidth = 0.5;
 
 int build_zone_maps(mdrq_table *t, cudaStream_t s)
 {
-    const uint64_t nz = (t->n + (1u << kZoneShift) - 1) >> kZoneShift;
-    const uint64_t nt = (t->n + kZoneTileRows - 1) / kZoneTileRows;
+    const uint64_t nz = (t->n + kZoneTileRows - 1) / kZoneTileRows;
     double *sums = nullptr;
     MDRQ_TRY(cudaMalloc(&sums, (size_t)t->d * 8));
     int st = cuda_status(cudaMemsetAsync(sums, 0, (size_t)t->d * 8, s));
     for (uint32_t j = 0; j < t->d && st == MDRQ_OK; ++j) {
         ColumnInfo &c = t->cols[j];
-        // 128-row zones, then one per 4096-row tile after them
-        if ((st = cuda_status(cudaMalloc(&c.zone, (size_t)(nz + nt) * sizeof(uint2)))))
+        if ((st = cuda_status(cudaMalloc(&c.zone, (size_t)nz * sizeof(uint2)))))
             break;
         const double range = bound_value(c.max_bits, c.type) - bound_value(c.min_bits, c.type);
         const double inv = std::isfinite(range) && range > 0 ? 1.0 / range : 0.0;
         const uint32_t grid = (uint32_t)std::min<uint64_t>((nz + 7) / 8, (uint64_t)t->sm_count * 16);
         mdrq_zone_kernel<<<std::max(1u, grid), 256, 0, s>>>((const uint32_t *)c.ptr, t->n, (uint32_t)c.type, c.zone,
                                                              inv, sums + j);
-        mdrq_tile_zone_kernel<<<(uint32_t)((nt + 255) / 256), 256, 0, s>>>(c.zone, nz, (uint32_t)c.type, c.zone + nz,
-                                                                           nt);
         st = cuda_status(cudaGetLastError());
     }
     std::vector<double> h((size_t)t->d, 0.0);

@@ -58,15 +58,13 @@ constexpr int kErrLookbackTimeout = 1;
 constexpr int kErrStageTimeout = 2;
 constexpr uint32_t kMaxPolls = 1u << 20;  // x <= 1 us backoff: bounded by about 1 s
 
-constexpr int kZoneShift = 7;  // zone maps: one (min, max) pair per 128 rows
-constexpr uint32_t kZoneTileRows = 4096;  // and one per 4096-row tile, stored after them
+constexpr uint32_t kZoneTileRows = 4096;  // zone maps: one (min, max) pair per 4096 rows
 
 // One predicate of one query, as the kernel reads it.
 struct DevPred {
     const void *col;    // device column (16-byte aligned)
-    const uint2 *zone;  // the column's zone map (device), or null: the bits of the
-                        // minimum and maximum of rows [128z, 128z + 128) at entry z,
-                        // then those of rows [4096i, 4096i + 4096) at entry nz + i
+    const uint2 *zone;  // the column's zone map (device), or null: entry i holds the
+                        // bits of the minimum and maximum of rows [4096i, 4096i + 4096)
     uint32_t type;      // kTypeF32 / kTypeI32
     uint32_t lo;        // bound bits, read as the column's type
     uint32_t hi;
@@ -233,7 +231,7 @@ __device__ __forceinline__ uint32_t in_range4(uint4 v, uint32_t type, uint32_t l
     return r;
 }
 
-// What a zone (the value range [min, max] of 128 rows) says about [lo, hi]: 0 no row
+// What a zone (the value range [min, max] of a row tile) says about [lo, hi]: 0 no row
 // of it can qualify, 2 every row qualifies, 1 its rows must be read
 __device__ __forceinline__ uint32_t zone_verdict(uint2 z, uint32_t type, uint32_t lo, uint32_t hi)
 {
@@ -364,7 +362,7 @@ constexpr unsigned long long kStopTile = ~0ull;  // "no more tiles" marker
 // claimed about one tile before it is processed and tiles are finished close to claim
 // order, which keeps look-back waits short. Slot reuse is safe with kStages + 1 slots:
 // a warp can run at most kStages iterations ahead of the output warp.
-template <int U, bool WINDOWED = false, bool ZONES = false>
+template <int U, bool WINDOWED = false>
 __device__ __forceinline__ void scan_cta(const ScanParams &p)
 {
     static_assert(U >= 1 && U <= 4, "8-bit packed counts hold at most 4 groups");
@@ -503,30 +501,11 @@ __device__ __forceinline__ void scan_cta(const ScanParams &p)
                     break;  // every row of this warp's chunk failed: read no more columns
                 const DevPred pr = p.preds[dq.first + i];
                 const uint32_t *col = (const uint32_t *)pr.col + row0 + 4 * lane;
-                // zone map: each 128-row group is approximated by its value range, as the
-                // VA-file approximates objects by cells (Sec. 2.2.3); a group whose range
-                // misses [lo, hi] fails without a load, one inside it passes without one
-                // (a lane reads a group's zone only while it has live rows there, so
-                // groups past the end of the table are never looked up)
-                // low 16 bits: rows still to read; high 16 bits: rows a zone passed
-                uint32_t nd = m;
-                if (ZONES && pr.zone) {
-                    const uint32_t z0 = (uint32_t)(row0 >> kZoneShift);
-#pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        const uint32_t mu = (m >> (4 * u)) & 0xfu;
-                        if (mu) {
-                            const uint32_t v = zone_verdict(pr.zone[z0 + u], pr.type, pr.lo, pr.hi);
-                            if (v != 1u)
-                                nd = (nd & ~(0xfu << (4 * u))) | (v == 2u ? mu << (16 + 4 * u) : 0u);
-                        }
-                    }
-                }
                 uint4 v[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     v[u] = make_uint4(0, 0, 0, 0);
-                    const uint32_t mu = (nd >> (4 * u)) & 0xfu;
+                    const uint32_t mu = (m >> (4 * u)) & 0xfu;
                     if (mu) {
                         if (full || mu == 0xfu) {
                             v[u] = ld_stream_v4(col + 128 * u);
@@ -543,7 +522,7 @@ __device__ __forceinline__ void scan_cta(const ScanParams &p)
 #pragma unroll
                 for (int u = 0; u < U; ++u)
                     keep |= in_range4(v[u], pr.type, pr.lo, pr.hi) << (4 * u);
-                m = (keep & nd & 0xffffu) | (nd >> 16);
+                m &= keep;
             }
 
             // rank the matches of this warp: row order is (u, lane, e)

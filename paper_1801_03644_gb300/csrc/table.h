@@ -19,7 +19,7 @@ struct ColumnInfo {
     int32_t type = MDRQ_F32;
     uint32_t min_bits = 0, max_bits = 0;  // exact column minimum / maximum (n > 0)
     std::vector<double> sample;           // sorted
-    uint2 *zone = nullptr;                // zone map (device, owned): min / max bits per 128 rows
+    uint2 *zone = nullptr;                // zone map (device, owned): min / max bits per 4096 rows
     double zone_width = 1.0;              // mean zone width / column range
     bool zone_keep = false;               // MDRQ_ZONES_AUTO reads this column's map
 };
@@ -145,10 +145,10 @@ int shared_scan_write(mdrq_table *t, SharedScanState &S, uint32_t *ids, uint64_t
 
 // mdrq.cu: one windowed scan launch over nq live queries whose rows and tiles the device
 // holds in windows / total_tiles (written by earlier kernels on the same stream).
-// zones: compile the zone-map check in; alg_bytes: the launch's algorithmic bytes for
-// the timing counters; helper_kernels: kernels launched before it for its windows.
+// alg_bytes: the launch's algorithmic bytes for the timing counters; helper_kernels:
+// kernels launched before it for its windows.
 int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t max_windows,
-                       const unsigned long long *nwindows, bool zones, uint64_t alg_bytes, uint32_t helper_kernels,
+                       const unsigned long long *nwindows, uint64_t alg_bytes, uint32_t helper_kernels,
                        uint32_t *ids, uint64_t capacity, const unsigned long long *base_in, const DevWindow *windows,
                        const unsigned long long *total_tiles, cudaStream_t s);
 

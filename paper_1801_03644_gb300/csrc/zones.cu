@@ -1,13 +1,13 @@
 // Zone-pruned plain scan: the row tiles a query's zone maps rule out are never visited.
 //
 // Every column carries, per 4096-row tile, the minimum and maximum of its values (built
-// at load, after the 128-row zones). A tile can hold an answer of a query only if, for
+// at load). A tile can hold an answer of a query only if, for
 // every predicate with a zone map, the tile's range meets [lo, hi] — the VA-file's
 // pruning of cells that cannot meet the query (Sec. 2.2.3), applied to row blocks of
 // the scan. One block per query turns its candidate tiles into runs (windows, at most
 // kZoneWindowsPerQuery; beyond that one window from the first to the last candidate),
-// and the windowed scan then evaluates every predicate on the windows' rows exactly,
-// with the 128-row zones inside them. Answers equal the plain scan's.
+// and the windowed scan then evaluates every predicate on the windows' rows exactly.
+// Answers equal the plain scan's.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -89,7 +89,7 @@ __device__ __forceinline__ uint32_t zw_scan(uint32_t v, uint32_t *s_warp, uint32
 // tile_start local to the query; counts[q] windows, qtiles[q] tiles. A query with no
 // candidate tile gets one empty window of one tile, which closes its answer.
 __global__ void __launch_bounds__(kZwThreads) mdrq_zone_windows_kernel(const DevQuery *queries, const DevPred *preds,
-                                                                       uint64_t nz, uint64_t n, uint64_t ntiles,
+                                                                       uint64_t n, uint64_t ntiles,
                                                                        DevWindow *slots, uint32_t *counts,
                                                                        uint32_t *qtiles)
 {
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kZwThreads) mdrq_zone_windows_kernel(const Dev
         for (uint32_t i = 0; i < dq.npred && k < kZwMaxPreds; ++i) {
             const DevPred pr = preds[dq.first + i];
             if (pr.zone)
-                s_zp[k++] = ZPred{pr.zone + nz, pr.type, pr.lo, pr.hi};
+                s_zp[k++] = ZPred{pr.zone, pr.type, pr.lo, pr.hi};
         }
         s_np = k;
         s_first = 0xffffffffu;
@@ -242,16 +242,15 @@ int zone_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std::v
     uint32_t *qtiles = counts + nlive;
     unsigned long long *wbase = reinterpret_cast<unsigned long long *>(qtiles + nlive);
     unsigned long long *tbase = wbase + nlive;
-    const uint64_t nz = (t->n + (1u << kZoneShift) - 1) >> kZoneShift;
     const uint64_t ntiles = (t->n + kZoneTileRows - 1) / kZoneTileRows;
-    mdrq_zone_windows_kernel<<<nlive, kZwThreads, 0, s>>>(t->dq_dev + q0, t->dp_dev, nz, t->n, ntiles, Z.slots,
-                                                          counts, qtiles);
+    mdrq_zone_windows_kernel<<<nlive, kZwThreads, 0, s>>>(t->dq_dev + q0, t->dp_dev, t->n, ntiles, Z.slots, counts,
+                                                          qtiles);
     MDRQ_TRY_STATUS(cudaGetLastError());
     st = window_list(nlive, kZoneWindowsPerQuery, counts, qtiles, wbase, tbase, Z.slots, Z.windows, Z.totals, s);
     if (st != MDRQ_OK)
         return st;
     Z.have = true;
-    return launch_window_scan(t, q0, nlive, max_windows, Z.totals + 1, true, scanned_columns * 4ull * t->n, 3, ids,
+    return launch_window_scan(t, q0, nlive, max_windows, Z.totals + 1, scanned_columns * 4ull * t->n, 3, ids,
                               capacity, base_in, Z.windows, Z.totals, s);
 }
 

@@ -1,6 +1,6 @@
-"""Zone maps (mdrq_set_zone_maps): a 128-row group decided from its value range gives the
-same answers as reading it, on clustered row orders with ragged tails, duplicated and
-special values; AUTO picks the clustered columns (needs a GB300)."""
+"""Zone maps (mdrq_set_zone_maps): row tiles ruled out by their value ranges are never
+visited, and the answers stay those of the oracle on clustered row orders with ragged
+tails, duplicated and special values; AUTO picks the clustered columns (needs a GB300)."""
 import numpy as np
 import pytest
 
@@ -54,7 +54,7 @@ def test_sorted_and_random_columns(M, n):
     a = np.sort(rng.random(n, dtype=np.float32))                       # sorted: zones narrow
     b = np.sort(rng.integers(-50, 50, size=n, dtype=np.int32))          # sorted ints, duplicates
     c = rng.random(n, dtype=np.float32)                                 # random: zones wide
-    d = np.repeat(rng.integers(0, 5, size=(n + 999) // 1000, dtype=np.int32), 1000)[:n]  # runs
+    d = np.repeat(rng.integers(0, 5, size=(n + 19_999) // 20_000, dtype=np.int32), 20_000)[:n]  # runs
     cols = [a, b, c, d]
     qs = [[(0, 0.25, 0.5)], [(1, -3, 7)], [(0, 0.1, 0.9), (2, 0.2, 0.4)], [(3, 2, 2)],
           [(1, -50, 49), (3, 0, 4)], [(0, 0.0, 1.0)], [(1, 10, 5)], [(2, 0.5, 0.5000001), (1, 0, 0)],

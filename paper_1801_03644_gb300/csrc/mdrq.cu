@@ -637,12 +637,23 @@ int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, u
         t->inject_nomem = 0;
         return MDRQ_E_NOMEM;
     }
+    // a host answer buffer that is page-locked is written by the scan itself, through
+    // its device mapping over the CPU-GPU link, while the scan runs; any other host
+    // buffer goes through a device staging buffer and one copy after the scan
     uint32_t *out = ids;
+    bool staged = false;
     if (!ids_on_device && capacity > 0) {
-        st = grow_device((void **)&t->ids_stage, &t->ids_stage_cap, (size_t)capacity * 4);
-        if (st != MDRQ_OK)
-            return st;
-        out = t->ids_stage;
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, ids) == cudaSuccess && a.type == cudaMemoryTypeHost && a.devicePointer) {
+            out = static_cast<uint32_t *>(a.devicePointer);
+        } else {
+            (void)cudaGetLastError();
+            st = grow_device((void **)&t->ids_stage, &t->ids_stage_cap, (size_t)capacity * 4);
+            if (st != MDRQ_OK)
+                return st;
+            out = t->ids_stage;
+            staged = true;
+        }
     }
     st = enqueue_batch(t, enc, live, nq, npreds, out, capacity, s);
     if (st != MDRQ_OK)
@@ -655,7 +666,7 @@ int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, u
     t->last_bytes += 4ull * std::min<uint64_t>(total, capacity);
     if (t->timing)
         t->acc_bytes += 4ull * std::min<uint64_t>(total, capacity);
-    if (!ids_on_device && capacity > 0 && total > 0) {
+    if (staged && total > 0) {
         MDRQ_TRY(cudaMemcpyAsync(ids, t->ids_stage, (size_t)std::min<uint64_t>(total, capacity) * 4,
                                  cudaMemcpyDeviceToHost, s));
         MDRQ_TRY(cudaStreamSynchronize(s));

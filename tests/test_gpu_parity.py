@@ -218,3 +218,34 @@ def test_repeat_calls_reuse_scratch(M):
     """Hundreds of launches on one table (tile-state epochs, claim counter) stay exact."""
     wl = W.uniform_small(n=250_000, nq=300)
     check_batch(M, wl.columns, wl.queries, mode=1)
+
+
+@pytest.mark.parametrize("mode", [1, 2], ids=["plain", "shared"])
+def test_pinned_host_answers_written_directly(M, mode):
+    """A page-locked host buffer receives the answers from the scan itself; the result
+    and the capacity rule are those of the device path; pageable memory still works."""
+    import torch
+    wl = W.mixed_clustered(n=1_000_003, nq=40)
+    want = [oracle.mdrq(wl.columns, q, 8) for q in wl.queries]
+    cat = np.concatenate(want)
+    total = cat.size
+    with M.Table(_device(wl.columns)) as t:
+        t.set_batch_mode(mode)
+        enc = t.encode_batch(wl.queries)
+        pinned = torch.full((total + 64,), -1, dtype=torch.int32, pin_memory=True)
+        st, off = t.query_batch_raw(enc, pinned.data_ptr(), total, False)
+        assert st == M.OK and int(off[-1]) == total
+        got = pinned.numpy().view(np.uint32)
+        assert np.array_equal(got[:total], cat)
+        assert np.all(pinned.numpy()[total:] == -1)
+        # too small: the first `cap` ids, nothing beyond
+        pinned.fill_(-1)
+        cap = total // 3
+        st, off = t.query_batch_raw(enc, pinned.data_ptr(), cap, False)
+        assert st == M.E_CAPACITY and int(off[-1]) == total
+        assert np.array_equal(pinned.numpy().view(np.uint32)[:cap], cat[:cap])
+        assert np.all(pinned.numpy()[cap:] == -1)
+        # pageable host memory (staged copy)
+        page = np.zeros(total, dtype=np.uint32)
+        st, off = t.query_batch_raw(enc, page.ctypes.data, total, False)
+        assert st == M.OK and np.array_equal(page, cat)

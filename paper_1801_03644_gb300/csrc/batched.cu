@@ -55,6 +55,9 @@ constexpr uint32_t kHintBuckets = 256;           // value buckets of a column's 
 constexpr int kCountPlanes = 4;                  // bit planes of the pass-1 lane counters
 constexpr unsigned long long kSkipQuery = ~0ull;  // qbase of a query pass 2 must not write
 constexpr int kPrefetchCols = 8;                 // column values per row kept in flight
+constexpr int kBallotQueries = 2;                // write pass: up to this many matching queries
+                                                 // per step are ranked by ballots, more by a
+                                                 // bit-matrix transpose
 
 // One column of a chunk's shared-memory image (kColWords words).
 struct ChunkCol {
@@ -330,11 +333,29 @@ __global__ void __launch_bounds__(kSharedThreads) mdrq_shared_pass_kernel(Shared
                 }
             }
             if (WRITE) {
-                // each query with matches in this step: rank its rows by lane, write ids
+                // the ids of this step's matches, query by query in row order. With few
+                // queries matching, each is ranked by a warp ballot; with more, the
+                // 32 x 32 (row, query) bit matrix is transposed so that lane l holds the
+                // rows of query 32g + l and writes them itself, one per iteration.
                 const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
                 for (int g = 0; g < kSharedG; ++g) {
                     uint32_t any = __reduce_or_sync(0xffffffffu, mask[g]);
+                    if (__popc(any) > kBallotQueries) {
+                        uint32_t rows = warp_transpose32(mask[g], lane);
+                        if (rows && off[g] != kSkipQuery) {
+                            unsigned long long o = off[g];
+                            do {
+                                const int e = __ffs(rows) - 1;
+                                rows &= rows - 1;
+                                if (o < p.capacity)
+                                    p.ids[o] = (uint32_t)(r0 + e);
+                                ++o;
+                            } while (rows);
+                            off[g] = o;
+                        }
+                        continue;
+                    }
                     while (any) {
                         const int q = __ffs(any) - 1;
                         any &= any - 1;

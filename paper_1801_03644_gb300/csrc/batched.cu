@@ -35,6 +35,7 @@
 #include <cstdint>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "mdrq.h"
@@ -212,7 +213,8 @@ __device__ __forceinline__ void flush_counts(uint32_t (&plane)[kSharedG][kCountP
 // Pass 1 (WRITE = false): per live query and unit, the number of matching rows.
 // Pass 2 (WRITE = true): the ids, at qbase[q] + counts[q][unit] (exclusive prefix).
 template <bool WRITE>
-__global__ void __launch_bounds__(kSharedThreads) mdrq_shared_pass_kernel(SharedParams p)
+// (64 registers, so that four blocks fit an SM: measured faster than 80 and three)
+__global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(SharedParams p)
 {
     extern __shared__ __align__(16) uint32_t s_img[];
     __shared__ uint32_t s_chunk;
@@ -518,7 +520,8 @@ struct SharedScanState {
     size_t stage_cap = 0;
     int grid_scan = 0;
     bool smem_attr = false;            // pass kernels opted in to kMaxImageWords
-    std::vector<std::pair<uint32_t, int>> grid_for_words;  // (image words, persistent grid)
+    // (image words, (count-pass grid, write-pass grid))
+    std::vector<std::pair<uint32_t, std::pair<int, int>>> grid_for_words;
     // the batch prepared by shared_scan_count, for shared_scan_write
     SharedParams params;
     uint32_t grid = 0;
@@ -765,17 +768,23 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
     }
     max_img = (max_img + 1023) & ~1023u;  // whole 4 KiB steps: few distinct launch shapes
     const size_t smem = (size_t)max_img * 4;
-    int grid_pass = 0;
+    // persistent grids of the two passes (their register budgets differ)
+    int grid_pass = 0, grid_write = 0;
     for (const auto &g : S.grid_for_words)
-        if (g.first == max_img)
-            grid_pass = g.second;
+        if (g.first == max_img) {
+            grid_pass = g.second.first;
+            grid_write = g.second.second;
+        }
     if (grid_pass == 0) {
-        int bps = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, mdrq_shared_pass_kernel<true>, kSharedThreads,
+        int bps = 0, bpw = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, mdrq_shared_pass_kernel<false>, kSharedThreads,
+                                                          smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpw, mdrq_shared_pass_kernel<true>, kSharedThreads,
                                                           smem) != cudaSuccess)
             return cuda_status(cudaGetLastError());
         grid_pass = t->sm_count * std::max(1, bps);
-        S.grid_for_words.emplace_back(max_img, grid_pass);
+        grid_write = t->sm_count * std::max(1, bpw);
+        S.grid_for_words.emplace_back(max_img, std::make_pair(grid_pass, grid_write));
     }
     uint64_t unit_rows;
     if (t->shared_unit_rows) {
@@ -838,7 +847,7 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
     mdrq_shared_scan_kernel<<<std::min<uint32_t>(nlive, (uint32_t)S.grid_scan), 1024, 0, s>>>(p);
     MDRQ_TRY_STATUS(cudaGetLastError());
     S.params = p;
-    S.grid = grid;
+    S.grid = (uint32_t)std::min<uint64_t>((uint64_t)grid_write, p.items);
     S.smem = smem;
     S.ready = true;
     t->last_launches += 3;

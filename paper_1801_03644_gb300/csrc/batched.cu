@@ -56,6 +56,7 @@ constexpr uint32_t kHintBuckets = 256;           // value buckets of a column's 
 constexpr int kCountPlanes = 4;                  // bit planes of the pass-1 lane counters
 constexpr unsigned long long kSkipQuery = ~0ull;  // qbase of a query pass 2 must not write
 constexpr int kPrefetchCols = 8;                 // column values per row kept in flight
+constexpr uint64_t kMaskBudgetBytes = 32ull << 30;  // largest row-mask store between the passes
 constexpr int kBallotQueries = 2;                // write pass: up to this many matching queries
                                                  // per step are ranked by ballots, more by a
                                                  // bit-matrix transpose
@@ -101,6 +102,7 @@ struct SharedParams {
     unsigned long long *offsets;    // offsets[orig + 1] <- CSR end of that query
     uint32_t *ids;
     uint64_t capacity;
+    uint4 *masks;                   // [chunk][row]: the row's query bits (CACHED passes)
 };
 
 // e(x) = number of cut points <= x, by a fixed-step binary search (uniform across lanes)
@@ -212,10 +214,13 @@ __device__ __forceinline__ void flush_counts(uint32_t (&plane)[kSharedG][kCountP
 
 // Pass 1 (WRITE = false): per live query and unit, the number of matching rows.
 // Pass 2 (WRITE = true): the ids, at qbase[q] + counts[q][unit] (exclusive prefix).
-template <bool WRITE>
+// CACHED: pass 1 also stores every row's 128 query bits of the chunk (16 bytes per row
+// and chunk) and pass 2 reads them instead of evaluating the columns again.
+template <bool WRITE, bool CACHED>
 // (64 registers, so that four blocks fit an SM: measured faster than 80 and three)
 __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(SharedParams p)
 {
+    constexpr bool kLoadMasks = WRITE && CACHED;
     extern __shared__ __align__(16) uint32_t s_img[];
     __shared__ uint32_t s_chunk;
     const int lane = threadIdx.x & 31;
@@ -275,7 +280,7 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
 
         // values of the first kPrefetchCols columns for the next 32-row step are loaded
         // while the current step is evaluated (software pipelining of the column reads)
-        const uint32_t npre = h.ncols < kPrefetchCols ? h.ncols : kPrefetchCols;
+        const uint32_t npre = kLoadMasks ? 0u : (h.ncols < kPrefetchCols ? h.ncols : kPrefetchCols);
         uint32_t xn[kPrefetchCols];
 #pragma unroll
         for (int i = 0; i < kPrefetchCols; ++i) {
@@ -287,45 +292,31 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
         for (uint64_t r0 = r_begin; r0 < r_end; r0 += 32) {
             const uint64_t r = r0 + lane;
             const bool valid = r < r_end;
-            uint32_t x[kPrefetchCols];
-#pragma unroll
-            for (int i = 0; i < kPrefetchCols; ++i) {
-                x[i] = xn[i];
-                const uint64_t rn = r + 32;
-                xn[i] = 0u;
-                if (i < (int)npre && rn < r_end)
-                    xn[i] = __ldg(reinterpret_cast<const ChunkCol *>(s_img + i * kColWords)->col + rn);
-            }
             uint32_t mask[kSharedG];
-#pragma unroll
-            for (int g = 0; g < kSharedG; ++g)
-                mask[g] = valid ? valid_words[g] : 0u;
-#pragma unroll
-            for (int i = 0; i < kPrefetchCols; ++i) {
-                if (i < (int)npre) {
-                    const ChunkCol *cc = reinterpret_cast<const ChunkCol *>(s_img + i * kColWords);
-                    const uint32_t e = interval_of(s_img, cc, x[i]);
-                    const uint4 t = *reinterpret_cast<const uint4 *>(s_img + cc->tab_off + e * kSharedG);
-                    mask[0] &= t.x;
-                    mask[1] &= t.y;
-                    mask[2] &= t.z;
-                    mask[3] &= t.w;
-                }
-            }
-            // columns beyond the prefetched ones: loaded together, then evaluated
-            for (uint32_t a0 = npre; a0 < h.ncols; a0 += kPrefetchCols) {
-                uint32_t y[kPrefetchCols];
+            if (kLoadMasks) {
+                const uint4 m4 = valid ? __ldcs(p.masks + (uint64_t)c * p.n + r) : make_uint4(0u, 0u, 0u, 0u);
+                mask[0] = m4.x;
+                mask[1] = m4.y;
+                mask[2] = m4.z;
+                mask[3] = m4.w;
+            } else {
+                uint32_t x[kPrefetchCols];
 #pragma unroll
                 for (int i = 0; i < kPrefetchCols; ++i) {
-                    y[i] = 0u;
-                    if (a0 + i < h.ncols && valid)
-                        y[i] = __ldg(reinterpret_cast<const ChunkCol *>(s_img + (a0 + i) * kColWords)->col + r);
+                    x[i] = xn[i];
+                    const uint64_t rn = r + 32;
+                    xn[i] = 0u;
+                    if (i < (int)npre && rn < r_end)
+                        xn[i] = __ldg(reinterpret_cast<const ChunkCol *>(s_img + i * kColWords)->col + rn);
                 }
 #pragma unroll
+                for (int g = 0; g < kSharedG; ++g)
+                    mask[g] = valid ? valid_words[g] : 0u;
+#pragma unroll
                 for (int i = 0; i < kPrefetchCols; ++i) {
-                    if (a0 + i < h.ncols) {
-                        const ChunkCol *cc = reinterpret_cast<const ChunkCol *>(s_img + (a0 + i) * kColWords);
-                        const uint32_t e = interval_of(s_img, cc, y[i]);
+                    if (i < (int)npre) {
+                        const ChunkCol *cc = reinterpret_cast<const ChunkCol *>(s_img + i * kColWords);
+                        const uint32_t e = interval_of(s_img, cc, x[i]);
                         const uint4 t = *reinterpret_cast<const uint4 *>(s_img + cc->tab_off + e * kSharedG);
                         mask[0] &= t.x;
                         mask[1] &= t.y;
@@ -333,6 +324,30 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
                         mask[3] &= t.w;
                     }
                 }
+                // columns beyond the prefetched ones: loaded together, then evaluated
+                for (uint32_t a0 = npre; a0 < h.ncols; a0 += kPrefetchCols) {
+                    uint32_t y[kPrefetchCols];
+#pragma unroll
+                    for (int i = 0; i < kPrefetchCols; ++i) {
+                        y[i] = 0u;
+                        if (a0 + i < h.ncols && valid)
+                            y[i] = __ldg(reinterpret_cast<const ChunkCol *>(s_img + (a0 + i) * kColWords)->col + r);
+                    }
+#pragma unroll
+                    for (int i = 0; i < kPrefetchCols; ++i) {
+                        if (a0 + i < h.ncols) {
+                            const ChunkCol *cc = reinterpret_cast<const ChunkCol *>(s_img + (a0 + i) * kColWords);
+                            const uint32_t e = interval_of(s_img, cc, y[i]);
+                            const uint4 t = *reinterpret_cast<const uint4 *>(s_img + cc->tab_off + e * kSharedG);
+                            mask[0] &= t.x;
+                            mask[1] &= t.y;
+                            mask[2] &= t.z;
+                            mask[3] &= t.w;
+                        }
+                    }
+                }
+                if (CACHED && valid)
+                    __stcs(p.masks + (uint64_t)c * p.n + r, make_uint4(mask[0], mask[1], mask[2], mask[3]));
             }
             if (WRITE) {
                 // the ids of this step's matches, query by query in row order. With few
@@ -520,7 +535,9 @@ struct SharedScanState {
     size_t stage_cap = 0;
     int grid_scan = 0;
     bool smem_attr = false;            // pass kernels opted in to kMaxImageWords
-    // (image words, (count-pass grid, write-pass grid))
+    uint4 *masks = nullptr;            // row masks between the passes
+    size_t masks_cap = 0;
+    // (image words | cached << 31, (count-pass grid, write-pass grid))
     std::vector<std::pair<uint32_t, std::pair<int, int>>> grid_for_words;
     // the batch prepared by shared_scan_count, for shared_scan_write
     SharedParams params;
@@ -569,6 +586,7 @@ void shared_state_free(SharedScanState *S)
     cudaFree(S->counts);
     cudaFree(S->totals);
     cudaFree(S->qbase);
+    cudaFree(S->masks);
     cudaFreeHost(S->stage);
     delete S;
 }
@@ -758,33 +776,49 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
     // each, unless the table sets the unit size (mdrq_set_shared_config)
     if (!S.smem_attr) {
         const int most = (int)kMaxImageWords * 4;
-        if (cudaFuncSetAttribute(mdrq_shared_pass_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(mdrq_shared_pass_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most) !=
-                cudaSuccess)
+        if (cudaFuncSetAttribute(mdrq_shared_pass_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 most) != cudaSuccess ||
+            cudaFuncSetAttribute(mdrq_shared_pass_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 most) != cudaSuccess ||
+            cudaFuncSetAttribute(mdrq_shared_pass_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 most) != cudaSuccess ||
+            cudaFuncSetAttribute(mdrq_shared_pass_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 most) != cudaSuccess)
             return cuda_status(cudaGetLastError());
         S.smem_attr = true;
         S.grid_scan = t->sm_count * 2;
+    }
+    // row masks kept between the passes when they fit: 16 bytes per row and chunk
+    const uint64_t mask_bytes = (uint64_t)chunks.size() * t->n * sizeof(uint4);
+    bool cached = S.masks_cap >= mask_bytes;
+    if (!cached && mask_bytes <= kMaskBudgetBytes) {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && mask_bytes <= free_b / 4)
+            cached = grow_device((void **)&S.masks, &S.masks_cap, (size_t)mask_bytes) == MDRQ_OK;
+        (void)cudaGetLastError();
     }
     max_img = (max_img + 1023) & ~1023u;  // whole 4 KiB steps: few distinct launch shapes
     const size_t smem = (size_t)max_img * 4;
     // persistent grids of the two passes (their register budgets differ)
     int grid_pass = 0, grid_write = 0;
+    const uint32_t key = max_img | (cached ? 0x80000000u : 0u);
     for (const auto &g : S.grid_for_words)
-        if (g.first == max_img) {
+        if (g.first == key) {
             grid_pass = g.second.first;
             grid_write = g.second.second;
         }
     if (grid_pass == 0) {
         int bps = 0, bpw = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, mdrq_shared_pass_kernel<false>, kSharedThreads,
-                                                          smem) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpw, mdrq_shared_pass_kernel<true>, kSharedThreads,
-                                                          smem) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &bps, cached ? mdrq_shared_pass_kernel<false, true> : mdrq_shared_pass_kernel<false, false>,
+                kSharedThreads, smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &bpw, cached ? mdrq_shared_pass_kernel<true, true> : mdrq_shared_pass_kernel<true, false>,
+                kSharedThreads, smem) != cudaSuccess)
             return cuda_status(cudaGetLastError());
         grid_pass = t->sm_count * std::max(1, bps);
         grid_write = t->sm_count * std::max(1, bpw);
-        S.grid_for_words.emplace_back(max_img, std::make_pair(grid_pass, grid_write));
+        S.grid_for_words.emplace_back(key, std::make_pair(grid_pass, grid_write));
     }
     uint64_t unit_rows;
     if (t->shared_unit_rows) {
@@ -843,7 +877,9 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
 
     const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)grid_pass, p.items);
     mdrq_shared_tables_kernel<<<(uint32_t)hdrs.size() * max_cols, 256, 0, s>>>(p, max_cols);
-    mdrq_shared_pass_kernel<false><<<grid, kSharedThreads, smem, s>>>(p);
+    p.masks = cached ? S.masks : nullptr;
+    (cached ? mdrq_shared_pass_kernel<false, true> : mdrq_shared_pass_kernel<false, false>)<<<grid, kSharedThreads,
+                                                                                                smem, s>>>(p);
     mdrq_shared_scan_kernel<<<std::min<uint32_t>(nlive, (uint32_t)S.grid_scan), 1024, 0, s>>>(p);
     MDRQ_TRY_STATUS(cudaGetLastError());
     S.params = p;
@@ -868,7 +904,8 @@ int shared_scan_write(mdrq_table *t, SharedScanState &S, uint32_t *ids, uint64_t
     p.capacity = capacity;
     if (csr)
         mdrq_shared_qbase_kernel<<<1, 1024, 0, s>>>(p);
-    mdrq_shared_pass_kernel<true><<<S.grid, kSharedThreads, S.smem, s>>>(p);
+    (p.masks ? mdrq_shared_pass_kernel<true, true> : mdrq_shared_pass_kernel<true, false>)<<<S.grid, kSharedThreads,
+                                                                                              S.smem, s>>>(p);
     MDRQ_TRY_STATUS(cudaGetLastError());
     t->last_launches += csr ? 2 : 1;
     if (t->timing)

@@ -189,10 +189,17 @@ int mdrq_scan_timing_read(mdrq_table *t, double *ms, uint64_t *scan_launches, ui
  *                     column is read once per group of up to 128 queries, and every
  *                     row's set of matching queries comes from per-column tables of the
  *                     queries' interval end points (two passes: count, then write).
+ *                     Between the passes the table keeps every row's query bits (16
+ *                     bytes per row and group of 128 queries) when that fits 32 GB and
+ *                     a quarter of the free device memory; the buffer stays with the
+ *                     table for later batches. Otherwise the write pass evaluates the
+ *                     columns again.
  *  MDRQ_BATCH_LEARNED every query scans only the rows its learned window allows (see
  *                     mdrq_learn); MDRQ_E_INVAL without a model.
  *  MDRQ_BATCH_AUTO    (default) shared when the batch has at least 32 queries that need
- *                     a scan and the table at least 4,000,000 rows, plain otherwise.
+ *                     a scan and the table at least 4,000,000 rows, plain otherwise;
+ *                     after mdrq_autotune, the faster of the two as measured there (for
+ *                     batches of 32 or more queries).
  * Both modes return identical answers. The paper answers one query at a time (Sec.
  * 7.1.2); the shared scan is this library's extension for batches.
  * Errors: MDRQ_E_INVAL (t NULL or unknown mode).

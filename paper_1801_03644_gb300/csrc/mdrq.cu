@@ -581,7 +581,7 @@ int enqueue_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std
         }
         const unsigned long long *base = c0 == 0 ? nullptr : t->offsets_dev + live[c0 - 1] + 1;
         // zone maps in use: scan only the tiles they do not rule out
-        st = zones ? zone_batch(t, enc, live, (uint32_t)c0, cnt, cols, out, capacity, base, s)
+        st = zones ? zone_batch(t, (uint32_t)c0, cnt, cols, out, capacity, base, s)
                    : launch_scan(t, (uint32_t)c0, cnt, cols, out, capacity, base, s);
         if (st != MDRQ_OK) {
             reset_scratch(t, s);

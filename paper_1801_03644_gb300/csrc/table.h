@@ -161,9 +161,8 @@ int window_list(uint32_t nq, uint32_t per_query, const uint32_t *counts, const u
 
 // zones.cu: the plain scan of live queries q0 .. q0 + nlive restricted to the row tiles
 // their zone maps do not rule out (one windowed launch)
-int zone_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std::vector<uint32_t> &live, uint32_t q0,
-               uint32_t nlive, uint64_t scanned_columns, uint32_t *ids, uint64_t capacity,
-               const unsigned long long *base_in, cudaStream_t s);
+int zone_batch(mdrq_table *t, uint32_t q0, uint32_t nlive, uint64_t scanned_columns, uint32_t *ids,
+               uint64_t capacity, const unsigned long long *base_in, cudaStream_t s);
 void zone_windows_free(mdrq_table *t);
 int zone_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *tiles);
 

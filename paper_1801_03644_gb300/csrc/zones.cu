@@ -215,12 +215,9 @@ __global__ void __launch_bounds__(kZwThreads) mdrq_zone_windows_kernel(const Dev
 
 }  // namespace
 
-int zone_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std::vector<uint32_t> &live, uint32_t q0,
-               uint32_t nlive, uint64_t scanned_columns, uint32_t *ids, uint64_t capacity,
-               const unsigned long long *base_in, cudaStream_t s)
+int zone_batch(mdrq_table *t, uint32_t q0, uint32_t nlive, uint64_t scanned_columns, uint32_t *ids,
+               uint64_t capacity, const unsigned long long *base_in, cudaStream_t s)
 {
-    (void)enc;
-    (void)live;
     if (nlive == 0)
         return MDRQ_OK;
     if (!t->zwin) {

@@ -689,6 +689,45 @@ int alloc_scratch(mdrq_table *t, cudaStream_t s)
     return MDRQ_OK;
 }
 
+// A private table over t's columns: the same rows, statistics, zone maps, batch mode and
+// shared-scan configuration, its own scratch and per-batch buffers. Owns nothing of t.
+int make_shadow(const mdrq_table *t, cudaStream_t s, mdrq_table **out)
+{
+    *out = nullptr;
+    mdrq_table *sh = new (std::nothrow) mdrq_table();
+    if (!sh)
+        return MDRQ_E_NOMEM;
+    sh->device = t->device;
+    sh->n = t->n;
+    sh->d = t->d;
+    sh->cols = t->cols;
+    sh->sm_count = t->sm_count;
+    for (int i = 0; i < 3; ++i)
+        sh->blocks_per_sm[i] = t->blocks_per_sm[i];
+    sh->blocks_per_sm_window = t->blocks_per_sm_window;
+    sh->batch_mode = t->batch_mode;
+    sh->shared_unit_rows = t->shared_unit_rows;
+    sh->shared_image_words = t->shared_image_words;
+    sh->auto_mode = t->auto_mode;
+    sh->zone_mode = t->zone_mode;
+    const int st = alloc_scratch(sh, s);
+    if (st != MDRQ_OK) {
+        free_shadow(sh);
+        return st;
+    }
+    *out = sh;
+    return MDRQ_OK;
+}
+
+void free_shadow(mdrq_table *sh)
+{
+    if (!sh)
+        return;
+    for (ColumnInfo &c : sh->cols)
+        c.zone = nullptr;  // the parent's
+    destroy(sh);
+}
+
 void destroy(mdrq_table *t)
 {
     if (!t)

@@ -42,10 +42,7 @@ void release(mdrq_prepared *p)
         cudaGraphDestroy(p->graph);
     if (p->capture)
         cudaStreamDestroy(p->capture);
-    if (p->shadow)
-        for (mdrq::ColumnInfo &c : p->shadow->cols)
-            c.zone = nullptr;  // the parent's
-    mdrq::destroy(p->shadow);  // owns no columns and no zone maps
+    mdrq::free_shadow(p->shadow);
     (void)cudaGetLastError();
     delete p;
 }
@@ -57,26 +54,11 @@ int prepare(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, uin
 {
     using namespace mdrq;
     MDRQ_TRY_STATUS(cudaSetDevice(t->device));
-    mdrq_table *sh = new (std::nothrow) mdrq_table();
-    if (!sh)
-        return MDRQ_E_NOMEM;
-    p->shadow = sh;
-    sh->device = t->device;
-    sh->n = t->n;
-    sh->d = t->d;
-    sh->cols = t->cols;
-    sh->sm_count = t->sm_count;
-    for (int i = 0; i < 3; ++i)
-        sh->blocks_per_sm[i] = t->blocks_per_sm[i];
-    sh->blocks_per_sm_window = t->blocks_per_sm_window;
-    sh->batch_mode = t->batch_mode;
-    sh->shared_unit_rows = t->shared_unit_rows;
-    sh->shared_image_words = t->shared_image_words;
-    sh->auto_mode = t->auto_mode;
-    sh->zone_mode = t->zone_mode;
-    int st = alloc_scratch(sh, s);
+    mdrq_table *sh = nullptr;
+    int st = make_shadow(t, s, &sh);
     if (st != MDRQ_OK)
         return st;
+    p->shadow = sh;
     std::vector<EncodedQuery> enc;
     size_t npreds = 0;
     st = encode_batch(sh, qs, nq, enc, p->live, npreds);

@@ -35,6 +35,13 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// Batches of at most this many queries are answered by the plain scan, whose cost
+// follows the columns the queries read; the shared scan's two passes over every row of
+// the table only pay for larger batches. Used when the scratch answer buffer of
+// kPlainServeMax * n ids per stream stays within kPlainServeScratchBytes.
+constexpr uint32_t kPlainServeMax = 4;
+constexpr uint64_t kPlainServeScratchBytes = 1ull << 30;
+
 struct Request {
     EncodedQuery enc;
     int status = 1;           // 1 waiting, 0 answered, < 0 failed
@@ -115,6 +122,11 @@ struct mdrq_server {
     cudaStream_t stream[2] = {nullptr, nullptr};
     cudaEvent_t done_ev[2] = {nullptr, nullptr};
     SharedScanState *state[2] = {nullptr, nullptr};
+    // small batches: a plain scan on a private table per stream into a scratch answer
+    // buffer of kPlainServeMax * n ids, then copies into the admitted queries' slots
+    mdrq_table *plain[2] = {nullptr, nullptr};
+    uint32_t *scratch_ids[2] = {nullptr, nullptr};
+    uint64_t scratch_cap = 0;
     unsigned long long *host_buf[2] = {nullptr, nullptr};  // pinned: totals, then bases
     size_t host_cap[2] = {0, 0};
     bool busy[2] = {false, false};
@@ -181,16 +193,33 @@ void scheduler_main(mdrq_server *S)
             live[i] = (uint32_t)i;
         const size_t nb = batch.size();
         cudaStream_t st = S->stream[k];
+        const bool plain = S->plain[k] && nb <= kPlainServeMax;
 
-        // count phase: exact answer sizes of the batch
-        int rc = grow_pinned((void **)&S->host_buf[k], &S->host_cap[k], nb * 8 * 2);
-        if (rc == MDRQ_OK)
-            rc = shared_scan_count(S->t, *S->state[k], enc, live, st);
+        // exact answer sizes of the batch: the shared scan's count phase, or for a small
+        // batch the whole plain scan into the scratch buffer
+        int rc = grow_pinned((void **)&S->host_buf[k], &S->host_cap[k], nb * 8 * 3 + 8);
         unsigned long long *totals = S->host_buf[k], *bases = S->host_buf[k] + nb;
-        if (rc == MDRQ_OK)
-            rc = cuda_status(cudaMemcpyAsync(totals, shared_state_totals(S->state[k]), nb * 8, cudaMemcpyDeviceToHost, st));
-        if (rc == MDRQ_OK)
-            rc = cuda_status(cudaStreamSynchronize(st));
+        uint64_t *offs = reinterpret_cast<uint64_t *>(S->host_buf[k] + 2 * nb);
+        if (plain) {
+            size_t npreds = 0;
+            for (const EncodedQuery &e : enc)
+                npreds += e.preds.size();
+            if (rc == MDRQ_OK)
+                rc = enqueue_batch(S->plain[k], enc, live, (uint32_t)nb, npreds, S->scratch_ids[k], S->scratch_cap,
+                                   st);
+            if (rc == MDRQ_OK)
+                rc = finish_batch(S->plain[k], live, (uint32_t)nb, offs, st);
+            for (size_t i = 0; rc == MDRQ_OK && i < nb; ++i)
+                totals[i] = offs[i + 1] - offs[i];
+        } else {
+            if (rc == MDRQ_OK)
+                rc = shared_scan_count(S->t, *S->state[k], enc, live, st);
+            if (rc == MDRQ_OK)
+                rc = cuda_status(
+                    cudaMemcpyAsync(totals, shared_state_totals(S->state[k]), nb * 8, cudaMemcpyDeviceToHost, st));
+            if (rc == MDRQ_OK)
+                rc = cuda_status(cudaStreamSynchronize(st));
+        }
 
         std::vector<uint64_t> admitted;
         bool wait_for_release = false;
@@ -261,10 +290,20 @@ void scheduler_main(mdrq_server *S)
             }
             continue;
         }
-        // write phase straight into the arena slots
-        rc = cuda_status(cudaMemcpyAsync(shared_state_qbase(S->state[k]), bases, nb * 8, cudaMemcpyHostToDevice, st));
-        if (rc == MDRQ_OK)
-            rc = shared_scan_write(S->t, *S->state[k], S->arena_dev, S->arena_words, false, st);
+        // write phase straight into the arena slots (small batches: copies of the
+        // admitted answers from the scratch buffer)
+        if (plain) {
+            rc = MDRQ_OK;
+            for (size_t i = 0; i < nb && rc == MDRQ_OK; ++i)
+                if (bases[i] != ~0ull)
+                    rc = cuda_status(cudaMemcpyAsync(S->arena_dev + bases[i], S->scratch_ids[k] + offs[i],
+                                                     (size_t)totals[i] * 4, cudaMemcpyDeviceToDevice, st));
+        } else {
+            rc = cuda_status(
+                cudaMemcpyAsync(shared_state_qbase(S->state[k]), bases, nb * 8, cudaMemcpyHostToDevice, st));
+            if (rc == MDRQ_OK)
+                rc = shared_scan_write(S->t, *S->state[k], S->arena_dev, S->arena_words, false, st);
+        }
         if (rc == MDRQ_OK)
             rc = cuda_status(cudaEventRecord(S->done_ev[k], st));
         std::lock_guard<std::mutex> lock(S->mu);
@@ -313,6 +352,8 @@ void server_destroy(mdrq_server *S)
     for (int k = 0; k < 2; ++k) {
         if (S->state[k])
             shared_state_free(S->state[k]);
+        free_shadow(S->plain[k]);
+        cudaFree(S->scratch_ids[k]);
         if (S->stream[k])
             cudaStreamDestroy(S->stream[k]);
         if (S->done_ev[k])
@@ -351,7 +392,17 @@ int mdrq_server_start(mdrq_table *t, uint64_t result_bytes, uint32_t max_batch, 
             if (!S->state[k])
                 rc = MDRQ_E_NOMEM;
         }
+        if (rc == MDRQ_OK && t->n > 0 && (uint64_t)kPlainServeMax * t->n * 4 <= kPlainServeScratchBytes) {
+            S->scratch_cap = (uint64_t)kPlainServeMax * t->n;
+            rc = make_shadow(t, S->stream[k], &S->plain[k]);
+            if (rc == MDRQ_OK) {
+                S->plain[k]->batch_mode = MDRQ_BATCH_PLAIN;
+                rc = cuda_status(cudaMalloc(&S->scratch_ids[k], S->scratch_cap * 4));
+            }
+        }
     }
+    if (rc == MDRQ_OK)
+        rc = cuda_status(cudaDeviceSynchronize());  // the private tables' scratch is cleared
     if (rc != MDRQ_OK) {
         server_destroy(S);
         return rc;

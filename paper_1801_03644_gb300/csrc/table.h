@@ -128,6 +128,10 @@ int finish_batch(mdrq_table *t, const std::vector<uint32_t> &live, uint32_t nq, 
 int alloc_scratch(mdrq_table *t, cudaStream_t s);
 void reset_scratch(mdrq_table *t, cudaStream_t s);
 void destroy(mdrq_table *t);
+// a private table over t's columns (own scratch; borrows columns, statistics and zone
+// maps), for prepared batches and the server's streams; released with free_shadow
+int make_shadow(const mdrq_table *t, cudaStream_t s, mdrq_table **out);
+void free_shadow(mdrq_table *sh);
 
 // batched.cu: answer the live queries of a batch with the shared scan. enc/live as in
 // run_batch; writes offsets_dev[orig + 1] for every live query.

@@ -105,3 +105,26 @@ def test_stop_answers_queued_queries(M):
             got = M.as_uint32_numpy(ids) if ids is not None else np.zeros(0, np.uint32)
             assert np.array_equal(got, oracle.mdrq(wl.columns, q, 4))
         assert srv.stop() == M.OK
+
+
+def test_small_batches_and_bursts(M):
+    """A slow stream (batches of one or two: the plain-scan path) and a burst (large
+    batches: the shared scan) on the same server; every answer exact."""
+    wl = W.serving_table(n=700_001, nq=120)
+    cols = _device(wl.columns)
+    with M.Table(cols) as t:
+        srv = M.Server(t, result_bytes=256 << 20, max_batch=64)
+        slow = _run_stream(M, srv, wl.queries[:30], rate=400)
+        burst = [srv.submit(q) for q in wl.queries[30:]]
+        res = []
+        for tk in burst:  # copied to the host while the server (and its arena) lives
+            st, ids, cnt, lat = srv.wait(tk)
+            res.append((st, M.as_uint32_numpy(ids).copy() if ids is not None else np.zeros(0, np.uint32)))
+        stats = srv.stats()
+        assert srv.stop() == M.OK
+    for i in range(30):
+        st, ids, cnt, lat = slow[i]
+        assert st == M.OK and np.array_equal(ids, oracle.mdrq(wl.columns, wl.queries[i], 8)), i
+    for j, (st, got) in enumerate(res):
+        assert st == M.OK and np.array_equal(got, oracle.mdrq(wl.columns, wl.queries[30 + j], 8)), j
+    assert stats["batches"] >= 20

@@ -259,7 +259,10 @@ int mdrq_learn_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *widenings);
  * result-buffer budget), writes the admitted answers into their arena slots, and lets
  * the rest wait, ahead of later arrivals. Two batches may be on the GPU at once (two
  * streams), so arrivals are admitted as slots and memory free up and their work
- * overlaps the batch in flight. While a server runs, t must not be used otherwise.
+ * overlaps the batch in flight. A batch of at most four queries is answered by the
+ * plain scan into a per-stream scratch buffer of 4n ids (allocated at start when it is
+ * at most 1 GiB, else small batches take the shared scan too) and copied into its
+ * arena slots. While a server runs, t must not be used otherwise.
  * Errors: MDRQ_E_INVAL (t or out NULL, result_bytes < 4, max_batch 0); MDRQ_E_NOMEM;
  * MDRQ_E_CUDA.
  */

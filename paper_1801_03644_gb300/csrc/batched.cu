@@ -57,6 +57,9 @@ constexpr int kCountPlanes = 4;                  // bit planes of the pass-1 lan
 constexpr unsigned long long kSkipQuery = ~0ull;  // qbase of a query pass 2 must not write
 constexpr int kPrefetchCols = 8;                 // column values per row kept in flight
 constexpr uint64_t kMaskBudgetBytes = 32ull << 30;  // largest row-mask store between the passes
+constexpr uint32_t kBlockSteps = 8;      // cached write pass: 32-row steps per id block (256 rows)
+constexpr uint32_t kBlockStride = kBlockSteps + 1;  // words per query in the block buffer (padded)
+constexpr size_t kBlockBufferBytes = (size_t)kSharedWarps * kSharedG * 32 * kBlockStride * 4;  // 36 KiB
 constexpr int kBallotQueries = 2;                // write pass: up to this many matching queries
                                                  // per step are ranked by ballots, more by a
                                                  // bit-matrix transpose
@@ -237,7 +240,7 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
             h = p.chunks[c];
             const uint4 *src = reinterpret_cast<const uint4 *>(p.plan + h.img_off);
             uint4 *dst = reinterpret_cast<uint4 *>(s_img);
-            for (uint32_t i = threadIdx.x; i < h.img_words / 4; i += blockDim.x)
+            for (uint32_t i = threadIdx.x; !kLoadMasks && i < h.img_words / 4; i += blockDim.x)
                 dst[i] = src[i];
             if (threadIdx.x == 0)
                 s_chunk = c;
@@ -289,6 +292,11 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
             if (i < (int)npre && r < r_end)
                 xn[i] = __ldg(reinterpret_cast<const ChunkCol *>(s_img + i * kColWords)->col + r);
         }
+        // cached write pass: this warp's block buffer of transposed step matrices
+        uint32_t *tb = s_img + (size_t)warp * kSharedG * 32 * kBlockStride;
+        uint32_t seen[kSharedG] = {0u, 0u, 0u, 0u};  // per lane: rows seen for its queries
+        uint32_t sb = 0;                             // steps in the block buffer
+        uint64_t block_row0 = r_begin;
         for (uint64_t r0 = r_begin; r0 < r_end; r0 += 32) {
             const uint64_t r = r0 + lane;
             const bool valid = r < r_end;
@@ -349,7 +357,57 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
                 if (CACHED && valid)
                     __stcs(p.masks + (uint64_t)c * p.n + r, make_uint4(mask[0], mask[1], mask[2], mask[3]));
             }
-            if (WRITE) {
+            if (kLoadMasks) {
+                // the step's (row, query) bit matrix, transposed (lane l: the rows of
+                // query 32g + l), goes to the warp's block buffer; every kBlockSteps steps
+                // the block's ids are written query by query by the whole warp
+#pragma unroll
+                for (int g = 0; g < kSharedG; ++g) {
+                    const uint32_t tr = __any_sync(0xffffffffu, mask[g]) ? warp_transpose32(mask[g], lane) : 0u;
+                    tb[(g * 32 + lane) * kBlockStride + sb] = tr;
+                    seen[g] |= tr;
+                }
+                if (++sb == kBlockSteps || r0 + 32 >= r_end) {
+                    __syncwarp();
+                    // lane i takes rows [8i, 8i + 8) of the block: byte i % 4 of step i / 4
+#pragma unroll
+                    for (int g = 0; g < kSharedG; ++g) {
+                        uint32_t qs = __ballot_sync(0xffffffffu, seen[g] != 0u);
+                        seen[g] = 0u;
+                        while (qs) {
+                            const int q = __ffs(qs) - 1;
+                            qs &= qs - 1;
+                            const uint32_t w = (uint32_t)(lane >> 2) < sb ? tb[(g * 32 + q) * kBlockStride + (lane >> 2)] : 0u;
+                            uint32_t bits = (w >> (8 * (lane & 3))) & 0xffu;
+                            const uint32_t c8 = __popc(bits);
+                            uint32_t incl = c8;
+#pragma unroll
+                            for (int o = 1; o < 32; o <<= 1) {
+                                const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+                                if (lane >= o)
+                                    incl += x;
+                            }
+                            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+                            const unsigned long long base = __shfl_sync(0xffffffffu, off[g], q);
+                            if (base != kSkipQuery) {
+                                unsigned long long pos = base + incl - c8;
+                                while (bits) {
+                                    const int e = __ffs(bits) - 1;
+                                    bits &= bits - 1;
+                                    if (pos < p.capacity)
+                                        p.ids[pos] = (uint32_t)(block_row0 + 8u * lane + e);
+                                    ++pos;
+                                }
+                                if (lane == q)
+                                    off[g] += total;
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    sb = 0;
+                    block_row0 = r0 + 32;
+                }
+            } else if (WRITE) {
                 // the ids of this step's matches, query by query in row order. With few
                 // queries matching, each is ranked by a warp ballot; with more, the
                 // 32 x 32 (row, query) bit matrix is transposed so that lane l holds the
@@ -799,6 +857,8 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
     }
     max_img = (max_img + 1023) & ~1023u;  // whole 4 KiB steps: few distinct launch shapes
     const size_t smem = (size_t)max_img * 4;
+    // the cached write pass holds no chunk image but the warps' id block buffers
+    const size_t smem_write = cached ? kBlockBufferBytes : smem;
     // persistent grids of the two passes (their register budgets differ)
     int grid_pass = 0, grid_write = 0;
     const uint32_t key = max_img | (cached ? 0x80000000u : 0u);
@@ -814,7 +874,7 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
                 kSharedThreads, smem) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                 &bpw, cached ? mdrq_shared_pass_kernel<true, true> : mdrq_shared_pass_kernel<true, false>,
-                kSharedThreads, smem) != cudaSuccess)
+                kSharedThreads, smem_write) != cudaSuccess)
             return cuda_status(cudaGetLastError());
         grid_pass = t->sm_count * std::max(1, bps);
         grid_write = t->sm_count * std::max(1, bpw);
@@ -884,7 +944,7 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
     MDRQ_TRY_STATUS(cudaGetLastError());
     S.params = p;
     S.grid = (uint32_t)std::min<uint64_t>((uint64_t)grid_write, p.items);
-    S.smem = smem;
+    S.smem = smem_write;
     S.ready = true;
     t->last_launches += 3;
     if (t->timing)

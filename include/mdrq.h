@@ -413,6 +413,13 @@ typedef struct {
 } mdrq_tuning;
 
 int mdrq_set_shared_config(mdrq_table *t, uint32_t unit_rows, uint32_t image_kib);
+
+/* mdrq_set_shared_bits_budget — the most device memory (bytes) the shared scan may keep
+ * for every row's query bits between its passes (16 bytes per row and group of 128
+ * queries); a batch that needs more, or max_bytes = 0, evaluates the columns again in
+ * the write pass. UINT64_MAX restores the default (32 GiB, and at most a quarter of the
+ * free device memory). Memory already held is kept. Errors: MDRQ_E_INVAL (t NULL). */
+int mdrq_set_shared_bits_budget(mdrq_table *t, uint64_t max_bytes);
 int mdrq_autotune(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, void *stream, mdrq_tuning *out);
 
 /*

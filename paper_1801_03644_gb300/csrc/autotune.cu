@@ -178,6 +178,14 @@ int mdrq_set_shared_config(mdrq_table *t, uint32_t unit_rows, uint32_t image_kib
     return MDRQ_OK;
 }
 
+int mdrq_set_shared_bits_budget(mdrq_table *t, uint64_t max_bytes)
+{
+    if (!t)
+        return MDRQ_E_INVAL;
+    t->shared_bits_budget = max_bytes;
+    return MDRQ_OK;
+}
+
 int mdrq_autotune(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, void *stream, mdrq_tuning *out)
 {
     if (!t || !out || (nq > 0 && !qs))

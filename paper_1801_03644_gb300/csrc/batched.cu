@@ -56,7 +56,7 @@ constexpr uint32_t kHintBuckets = 256;           // value buckets of a column's 
 constexpr int kCountPlanes = 4;                  // bit planes of the pass-1 lane counters
 constexpr unsigned long long kSkipQuery = ~0ull;  // qbase of a query pass 2 must not write
 constexpr int kPrefetchCols = 8;                 // column values per row kept in flight
-constexpr uint64_t kMaskBudgetBytes = 32ull << 30;  // largest row-mask store between the passes
+constexpr uint64_t kMaskBudgetBytes = 32ull << 30;  // default largest row-bit store between the passes
 constexpr uint32_t kBlockSteps = 8;      // cached write pass: 32-row steps per id block (256 rows)
 constexpr uint32_t kBlockStride = kBlockSteps + 1;  // words per query in the block buffer (padded)
 constexpr size_t kBlockBufferBytes = (size_t)kSharedWarps * kSharedG * 32 * kBlockStride * 4;  // 36 KiB
@@ -848,8 +848,9 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
     }
     // row masks kept between the passes when they fit: 16 bytes per row and chunk
     const uint64_t mask_bytes = (uint64_t)chunks.size() * t->n * sizeof(uint4);
-    bool cached = S.masks_cap >= mask_bytes;
-    if (!cached && mask_bytes <= kMaskBudgetBytes) {
+    const uint64_t budget_bytes = t->shared_bits_budget == ~0ull ? kMaskBudgetBytes : t->shared_bits_budget;
+    bool cached = mask_bytes <= budget_bytes && S.masks_cap >= mask_bytes;
+    if (!cached && mask_bytes <= budget_bytes) {
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && mask_bytes <= free_b / 4)
             cached = grow_device((void **)&S.masks, &S.masks_cap, (size_t)mask_bytes) == MDRQ_OK;

@@ -708,6 +708,7 @@ int make_shadow(const mdrq_table *t, cudaStream_t s, mdrq_table **out)
     sh->batch_mode = t->batch_mode;
     sh->shared_unit_rows = t->shared_unit_rows;
     sh->shared_image_words = t->shared_image_words;
+    sh->shared_bits_budget = t->shared_bits_budget;
     sh->auto_mode = t->auto_mode;
     sh->zone_mode = t->zone_mode;
     const int st = alloc_scratch(sh, s);

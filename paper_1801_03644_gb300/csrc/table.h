@@ -87,6 +87,7 @@ struct mdrq_table {
     mdrq::SharedScanState *shared = nullptr;
     uint32_t shared_unit_rows = 0;    // rows per warp unit (0: built-in rule)
     uint32_t shared_image_words = 0;  // shared-memory budget per chunk (0: built-in default)
+    uint64_t shared_bits_budget = ~0ull;  // row bits kept between the passes, bytes (~0: default)
     int auto_mode = -1;               // mode AUTO takes for 32+ queries, once measured (-1: rule)
     mdrq::LearnedModel *learned = nullptr;
 

@@ -53,8 +53,8 @@ EXPORTS = ["mdrq_load_columns", "mdrq_query", "mdrq_query_batch", "mdrq_free",
            "mdrq_learn_window_rows", "mdrq_server_start", "mdrq_server_submit", "mdrq_server_wait",
            "mdrq_server_release", "mdrq_server_stats", "mdrq_server_stop", "mdrq_prepare_batch",
            "mdrq_prepared_launch", "mdrq_prepared_wait", "mdrq_prepared_kernels", "mdrq_prepared_free",
-           "mdrq_set_shared_config", "mdrq_autotune", "mdrq_set_zone_maps", "mdrq_zone_map_info",
-           "mdrq_zone_scan_info"]
+           "mdrq_set_shared_config", "mdrq_set_shared_bits_budget", "mdrq_autotune",
+           "mdrq_set_zone_maps", "mdrq_zone_map_info", "mdrq_zone_scan_info"]
 
 FAULT_SKIP_TILES, FAULT_NOMEM = 1, 2
 BATCH_AUTO, BATCH_PLAIN, BATCH_SHARED, BATCH_LEARNED = 0, 1, 2, 3
@@ -131,6 +131,8 @@ def lib():
         L.mdrq_zone_scan_info.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]
         L.mdrq_set_shared_config.restype = ctypes.c_int
         L.mdrq_set_shared_config.argtypes = [vp, u32, u32]
+        L.mdrq_set_shared_bits_budget.restype = ctypes.c_int
+        L.mdrq_set_shared_bits_budget.argtypes = [vp, u64]
         L.mdrq_autotune.restype = ctypes.c_int
         L.mdrq_autotune.argtypes = [vp, ctypes.POINTER(QDesc), u32, vp, ctypes.POINTER(Tuning)]
         L.mdrq_prepare_batch.restype = ctypes.c_int
@@ -385,6 +387,13 @@ class Table:
         st = lib().mdrq_set_shared_config(self._h, int(unit_rows), int(image_kib))
         if st != OK:
             raise MDRQError(st, "mdrq_set_shared_config")
+
+    def set_shared_bits_budget(self, max_bytes: int):
+        """``mdrq_set_shared_bits_budget``: device bytes the shared scan may keep for row
+        query bits between its passes (0: never; ``2**64 - 1``: the default)."""
+        st = lib().mdrq_set_shared_bits_budget(self._h, int(max_bytes))
+        if st != OK:
+            raise MDRQError(st, "mdrq_set_shared_bits_budget")
 
     def autotune(self, queries, stream=None) -> dict:
         """``mdrq_autotune`` on this batch; returns the ``mdrq_tuning`` fields."""

@@ -41,13 +41,16 @@ def _check(M, t, queries, want):
         assert np.array_equal(got[int(off[q]):int(off[q + 1])], w), q
 
 
+@pytest.mark.parametrize("keep_bits", [True, False], ids=["bits_kept", "bits_recomputed"])
 @pytest.mark.parametrize("unit_rows,image_kib", [(32, 16), (96, 24), (1000, 0), (0, 16), (4096, 208),
                                                  (65536, 40)])
-def test_shared_configs_match_oracle(M, case, unit_rows, image_kib):
+def test_shared_configs_match_oracle(M, case, unit_rows, image_kib, keep_bits):
+    """Every shape, with the row bits kept between the passes and recomputed."""
     wl, want = case
     with M.Table(_device(wl.columns)) as t:
         t.set_batch_mode(M.BATCH_SHARED)
         t.set_shared_config(unit_rows, image_kib)
+        t.set_shared_bits_budget(2**64 - 1 if keep_bits else 0)
         _check(M, t, wl.queries, want)
 
 

@@ -51,8 +51,9 @@ constexpr uint64_t kMinUnitRows = 256;           // rows per warp unit, small ta
 constexpr int kSharedG = 4;                      // 32-bit mask words per chunk: 128 queries
 constexpr uint32_t kChunkImageWords = 14 * 1024; // default shared-memory budget of one chunk (56 KiB)
 constexpr uint32_t kMaxImageWords = 52 * 1024;   // largest budget a table may set (208 KiB)
-constexpr uint32_t kColWords = 10;               // words of one ChunkCol in an image
-constexpr uint32_t kHintBuckets = 256;           // value buckets of a column's search hint
+constexpr uint32_t kColWords = 8;                // words of one ChunkCol in an image
+constexpr uint32_t kHintBuckets = 1024;          // value buckets of a column's search hint
+constexpr uint32_t kMaxHintSteps = 15;           // most cut points one bucket may hold
 constexpr int kCountPlanes = 4;                  // bit planes of the pass-1 lane counters
 constexpr unsigned long long kSkipQuery = ~0ull;  // qbase of a query pass 2 must not write
 constexpr int kPrefetchCols = 8;                 // column values per row kept in flight
@@ -64,17 +65,18 @@ constexpr int kBallotQueries = 2;                // write pass: up to this many 
                                                  // per step are ranked by ballots, more by a
                                                  // bit-matrix transpose
 
-// One column of a chunk's shared-memory image (kColWords words).
+// One column of a chunk's shared-memory image (kColWords words). The first 16 bytes are
+// what the passes read for every row (one 128-bit shared-memory load):
+//   w0: image word of the cut points (bits 0-15), their number m (bits 16-24), the
+//       search hint's walk length (bits 25-28), type (bit 31: 1 = int32);
+//   w1: image word of the tables (bits 0-15) and of the hint (bits 16-31);
+//   w2, w3: the hint's bucket base and scale (float; scale 0: no hint).
 struct ChunkCol {
+    uint32_t w0, w1;
+    float base;           // search hint: bucket trunc((x - base) * scale), clamped
+    float scale;
     const uint32_t *col;  // device column
-    uint32_t type;        // kTypeF32 / kTypeI32
-    uint32_t m;           // cut points
-    uint32_t cut_off;     // image word of the first cut point
-    uint32_t tab_off;     // image word of T[0][0]; T[e][g] at tab_off + e * G + g
-    float base;           // search hint: bucket floor((x - base) * scale), clamped
-    float scale;          // 0: no hint (binary search)
-    uint32_t hint_off;    // image word of kHintBuckets 16-bit start positions
-    uint32_t pad;
+    uint32_t pad[2];
 };
 static_assert(sizeof(ChunkCol) == kColWords * 4, "ChunkCol layout");
 
@@ -128,33 +130,35 @@ __device__ __forceinline__ uint32_t elementary_interval(const uint32_t *cut, uin
     return pos;
 }
 
-// e(x) from the column's hint: start at the cut count of x's value bucket (computed in
-// float, so possibly a neighbouring bucket) and step with exact compares to the answer.
-template <typename T>
-__device__ __forceinline__ uint32_t walk_to_interval(const uint32_t *cut, uint32_t m, uint32_t pos, T x)
+// e(x) from the column's hint. The bucket function trunc((x - base) * scale) is
+// monotone in x, and the hint holds, per bucket, the number of cut points in lower
+// buckets; the cut points in x's own bucket (at most `steps`, computed on the host
+// with the same float arithmetic) are then compared in order until one exceeds x.
+__device__ __forceinline__ uint32_t interval_of(const uint32_t *img, uint4 hot, uint32_t xbits)
 {
-    while (pos > 0 && *reinterpret_cast<const T *>(&cut[pos - 1]) > x)
-        --pos;
-    while (pos < m && *reinterpret_cast<const T *>(&cut[pos]) <= x)
-        ++pos;
-    return pos;
-}
-
-__device__ __forceinline__ uint32_t interval_of(const uint32_t *img, const ChunkCol *cc, uint32_t xbits)
-{
-    const uint32_t *cut = img + cc->cut_off;
-    const uint32_t m = cc->m;
-    if (cc->scale == 0.0f)
-        return elementary_interval(cut, m, xbits, cc->type);
-    const bool f32 = cc->type == kTypeF32;
+    const uint32_t *cut = img + (hot.x & 0xffffu);
+    const uint32_t m = (hot.x >> 16) & 0x1ffu;
+    const bool f32 = (hot.x >> 31) == 0u;
+    const float scale = __uint_as_float(hot.w);
+    if (scale == 0.0f)
+        return elementary_interval(cut, m, xbits, f32 ? kTypeF32 : kTypeI32);
+    const uint32_t steps = (hot.x >> 25) & 0xfu;
     const float xf = f32 ? __uint_as_float(xbits) : (float)(int)xbits;
-    int b = __float2int_rz((xf - cc->base) * cc->scale);
+    int b = __float2int_rz((xf - __uint_as_float(hot.z)) * scale);
     b = b < 0 ? 0 : (b >= (int)kHintBuckets ? (int)kHintBuckets - 1 : b);
-    const uint32_t h = img[cc->hint_off + (b >> 1)];
-    const uint32_t start = (b & 1) ? (h >> 16) : (h & 0xffffu);
-    if (f32)
-        return walk_to_interval<float>(cut, m, start, __uint_as_float(xbits));
-    return walk_to_interval<int>(cut, m, start, (int)xbits);
+    const uint32_t h = img[(hot.y >> 16) + (b >> 1)];
+    uint32_t pos = (b & 1) ? (h >> 16) : (h & 0xffffu);
+    const uint32_t end = pos + steps < m ? pos + steps : m;  // the bucket's cuts lie below end
+    if (f32) {
+        const float x = __uint_as_float(xbits);
+        while (pos < end && __uint_as_float(cut[pos]) <= x)
+            ++pos;
+    } else {
+        const int x = (int)xbits;
+        while (pos < end && (int)cut[pos] <= x)
+            ++pos;
+    }
+    return pos;
 }
 
 // T[e][g] for every elementary interval of every (chunk, column): bit i of word g is
@@ -170,7 +174,8 @@ __global__ void __launch_bounds__(256) mdrq_shared_tables_kernel(SharedParams p,
     uint32_t *img = p.plan_rw + h.img_off;
     const ChunkCol cc = *reinterpret_cast<const ChunkCol *>(img + a * kColWords);
     const uint32_t *iv = p.plan + h.iv_off + (uint64_t)a * h.nq;
-    const uint32_t words = (cc.m + 1) * kSharedG;
+    const uint32_t m = (cc.w0 >> 16) & 0x1ffu, tab_off = cc.w1 & 0xffffu;
+    const uint32_t words = (m + 1) * kSharedG;
     for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) {
         const uint32_t e = w / kSharedG, g = w % kSharedG;
         uint32_t bits = 0;
@@ -182,7 +187,7 @@ __global__ void __launch_bounds__(256) mdrq_shared_tables_kernel(SharedParams p,
                     bits |= 1u << i;
             }
         }
-        img[cc.tab_off + w] = bits;
+        img[tab_off + w] = bits;
     }
 }
 
@@ -323,9 +328,9 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
 #pragma unroll
                 for (int i = 0; i < kPrefetchCols; ++i) {
                     if (i < (int)npre) {
-                        const ChunkCol *cc = reinterpret_cast<const ChunkCol *>(s_img + i * kColWords);
-                        const uint32_t e = interval_of(s_img, cc, x[i]);
-                        const uint4 t = *reinterpret_cast<const uint4 *>(s_img + cc->tab_off + e * kSharedG);
+                        const uint4 hot = *reinterpret_cast<const uint4 *>(s_img + i * kColWords);
+                        const uint32_t e = interval_of(s_img, hot, x[i]);
+                        const uint4 t = *reinterpret_cast<const uint4 *>(s_img + (hot.y & 0xffffu) + e * kSharedG);
                         mask[0] &= t.x;
                         mask[1] &= t.y;
                         mask[2] &= t.z;
@@ -344,9 +349,9 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
 #pragma unroll
                     for (int i = 0; i < kPrefetchCols; ++i) {
                         if (a0 + i < h.ncols) {
-                            const ChunkCol *cc = reinterpret_cast<const ChunkCol *>(s_img + (a0 + i) * kColWords);
-                            const uint32_t e = interval_of(s_img, cc, y[i]);
-                            const uint4 t = *reinterpret_cast<const uint4 *>(s_img + cc->tab_off + e * kSharedG);
+                            const uint4 hot = *reinterpret_cast<const uint4 *>(s_img + (a0 + i) * kColWords);
+                            const uint32_t e = interval_of(s_img, hot, y[i]);
+                            const uint4 t = *reinterpret_cast<const uint4 *>(s_img + (hot.y & 0xffffu) + e * kSharedG);
                             mask[0] &= t.x;
                             mask[1] &= t.y;
                             mask[2] &= t.z;
@@ -679,7 +684,7 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
                     add_cols += per_dim[j] == 0;
                 // upper bound of the image: columns + 2 cuts per pair + (cuts + 1) * G table words
                 const uint32_t nc = ncols + add_cols, np = pairs + (uint32_t)e.dims.size();
-                const uint64_t words = (uint64_t)nc * (kColWords + kHintBuckets / 2) + 2ull * np + 4 +
+                const uint64_t words = (uint64_t)nc * kColWords + 2ull * np + 4 +
                                        (2ull * np + nc) * kSharedG + 4ull * nc;
                 if (ch.nq > 0 && words > budget)
                     break;
@@ -735,67 +740,102 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
             plan.push_back(0);
         const uint64_t img_off = plan.size();
         uint32_t w = ncols * kColWords;
-        std::vector<ChunkCol> cc(ncols);
+        struct ColLayout {
+            uint32_t type = 0, m = 0, cut_off = 0, tab_off = 0, hint_off = 0, steps = 0;
+            float base = 0.0f, scale = 0.0f;
+            const uint32_t *col = nullptr;
+        };
+        std::vector<ColLayout> cl(ncols);
         std::vector<std::vector<uint32_t>> hint(ncols);
         for (uint32_t a = 0; a < ncols; ++a) {
             const ColumnInfo &ci_ = t->cols[cols[a].dim];
-            cc[a].col = static_cast<const uint32_t *>(ci_.ptr);
-            cc[a].type = (uint32_t)ci_.type;
-            cc[a].m = (uint32_t)cols[a].cuts.size();
-            cc[a].pad = 0;
-            // search hint over [min, max] in kHintBuckets equal value buckets: bucket b
-            // starts at the number of cuts <= min + b * (max - min) / kHintBuckets; used
-            // when the cut points spread out enough for the walk to stay short
+            cl[a].col = static_cast<const uint32_t *>(ci_.ptr);
+            cl[a].type = (uint32_t)ci_.type;
+            cl[a].m = (uint32_t)cols[a].cuts.size();
+            // search hint over [min, max] in kHintBuckets equal value buckets, with the
+            // bucket function the device evaluates (float: trunc((x - base) * scale),
+            // clamped): bucket b starts at the number of cuts in lower buckets, and the
+            // walk covers the most cuts one bucket holds; used when that stays short
             const std::vector<double> &cut = cols[a].cuts;
             const double mn = bound_value(ci_.min_bits, ci_.type), mx = bound_value(ci_.max_bits, ci_.type);
             const double range = mx - mn;
-            cc[a].base = 0.0f;
-            cc[a].scale = 0.0f;
-            cc[a].hint_off = 0;
-            if (std::isfinite(range) && range > 0 && cc[a].m > 8 &&
-                std::isfinite((float)(kHintBuckets / range)) && (float)(kHintBuckets / range) > 0.0f) {
-                std::vector<uint32_t> start(kHintBuckets);
-                uint32_t densest = 0;
-                for (uint32_t b = 0; b < kHintBuckets; ++b) {
-                    const double edge = mn + (double)b * range / kHintBuckets;
-                    start[b] = (uint32_t)(std::upper_bound(cut.begin(), cut.end(), edge) - cut.begin());
-                    if (b > 0)
-                        densest = std::max(densest, start[b] - start[b - 1]);
-                }
-                densest = std::max(densest, cc[a].m - start[kHintBuckets - 1]);
-                if (densest <= 6) {
-                    cc[a].base = (float)mn;
-                    cc[a].scale = (float)(kHintBuckets / range);
+            const float base = (float)mn, scale = (float)(kHintBuckets / range);
+            if (std::isfinite(range) && range > 0 && cl[a].m > 8 && std::isfinite(base) && std::isfinite(scale) &&
+                scale > 0.0f) {
+                auto bucket = [&](double v) {
+                    const float xf = cl[a].type == MDRQ_F32 ? (float)v : (float)(int32_t)v;
+                    const float tq = (xf - base) * scale;
+                    if (!(tq >= 1.0f))
+                        return 0u;  // negative, below one, or NaN
+                    if (tq >= (float)(kHintBuckets - 1))
+                        return kHintBuckets - 1;
+                    return (uint32_t)tq;  // truncation, as __float2int_rz
+                };
+                std::vector<uint32_t> in_bucket(kHintBuckets, 0);
+                for (double c : cut)
+                    ++in_bucket[bucket(c)];
+                uint32_t steps = 0;
+                for (uint32_t b = 0; b < kHintBuckets; ++b)
+                    steps = std::max(steps, in_bucket[b]);
+                if (steps <= kMaxHintSteps) {
+                    cl[a].base = base;
+                    cl[a].scale = scale;
+                    cl[a].steps = steps;
                     hint[a].assign(kHintBuckets / 2, 0);
-                    for (uint32_t b = 0; b < kHintBuckets; ++b)
-                        hint[a][b >> 1] |= start[b] << ((b & 1) * 16);
+                    uint32_t below = 0;
+                    for (uint32_t b = 0; b < kHintBuckets; ++b) {
+                        hint[a][b >> 1] |= below << ((b & 1) * 16);
+                        below += in_bucket[b];
+                    }
                 }
             }
-            if (!hint[a].empty()) {
-                cc[a].hint_off = w;
+        }
+        // hints where the image budget leaves room for them (the rest search by bisection)
+        {
+            uint64_t base_words = (uint64_t)ncols * kColWords + 8;
+            for (uint32_t a = 0; a < ncols; ++a)
+                base_words += cl[a].m + (uint64_t)(cl[a].m + 1) * kSharedG;
+            for (uint32_t a = 0; a < ncols; ++a) {
+                if (hint[a].empty())
+                    continue;
+                if (base_words + kHintBuckets / 2 > budget) {
+                    hint[a].clear();
+                    cl[a].base = cl[a].scale = 0.0f;
+                    cl[a].steps = 0;
+                    continue;
+                }
+                base_words += kHintBuckets / 2;
+                cl[a].hint_off = w;
                 w += kHintBuckets / 2;
             }
         }
         for (uint32_t a = 0; a < ncols; ++a) {
-            cc[a].cut_off = w;
-            w += cc[a].m;
+            cl[a].cut_off = w;
+            w += cl[a].m;
         }
         w = (w + 3) & ~3u;
         for (uint32_t a = 0; a < ncols; ++a) {
-            cc[a].tab_off = w;
-            w += (cc[a].m + 1) * kSharedG;
+            cl[a].tab_off = w;
+            w += (cl[a].m + 1) * kSharedG;
         }
         const uint32_t img_words = (w + 3) & ~3u;
-        if (img_words > budget)
+        if (img_words > budget || img_words > 0xffffu)
             return MDRQ_E_INVAL;  // cannot happen: the chunking bounded it
         max_img = std::max(max_img, img_words);
         plan.resize(img_off + img_words, 0);
         for (uint32_t a = 0; a < ncols; ++a) {
-            std::memcpy(&plan[img_off + a * kColWords], &cc[a], sizeof(ChunkCol));
+            ChunkCol cc;
+            std::memset(&cc, 0, sizeof(cc));
+            cc.w0 = cl[a].cut_off | (cl[a].m << 16) | (cl[a].steps << 25) | ((cl[a].type == MDRQ_I32 ? 1u : 0u) << 31);
+            cc.w1 = cl[a].tab_off | (cl[a].hint_off << 16);
+            cc.base = cl[a].base;
+            cc.scale = cl[a].scale;
+            cc.col = cl[a].col;
+            std::memcpy(&plan[img_off + a * kColWords], &cc, sizeof(ChunkCol));
             for (size_t i = 0; i < hint[a].size(); ++i)
-                plan[img_off + cc[a].hint_off + i] = hint[a][i];
-            for (uint32_t i = 0; i < cc[a].m; ++i)
-                plan[img_off + cc[a].cut_off + i] = to_bits(cols[a].cuts[i], (int32_t)cc[a].type);
+                plan[img_off + cl[a].hint_off + i] = hint[a][i];
+            for (uint32_t i = 0; i < cl[a].m; ++i)
+                plan[img_off + cl[a].cut_off + i] = to_bits(cols[a].cuts[i], (int32_t)cl[a].type);
         }
         // intervals: word [a][k] = elo | ehi << 16, the elementary intervals query k accepts on column a
         const uint64_t iv_off = plan.size();

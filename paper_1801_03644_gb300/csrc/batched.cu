@@ -58,9 +58,11 @@ constexpr int kCountPlanes = 4;                  // bit planes of the pass-1 lan
 constexpr unsigned long long kSkipQuery = ~0ull;  // qbase of a query pass 2 must not write
 constexpr int kPrefetchCols = 8;                 // column values per row kept in flight
 constexpr uint64_t kMaskBudgetBytes = 32ull << 30;  // default largest row-bit store between the passes
-constexpr uint32_t kBlockSteps = 8;      // cached write pass: 32-row steps per id block (256 rows)
+constexpr uint32_t kBlockSteps = 16;     // cached write pass: 32-row steps per id block
 constexpr uint32_t kBlockStride = kBlockSteps + 1;  // words per query in the block buffer (padded)
-constexpr size_t kBlockBufferBytes = (size_t)kSharedWarps * kSharedG * 32 * kBlockStride * 4;  // 36 KiB
+constexpr uint32_t kLanesPerWord = 32 / kBlockSteps;  // lanes sharing one step's word in a flush
+constexpr uint32_t kLaneBits = kBlockSteps == 32 ? 0xffffffffu : (1u << kBlockSteps) - 1u;
+constexpr size_t kBlockBufferBytes = (size_t)kSharedWarps * kSharedG * 32 * kBlockStride * 4;
 constexpr int kBallotQueries = 2;                // write pass: up to this many matching queries
                                                  // per step are ranked by ballots, more by a
                                                  // bit-matrix transpose
@@ -374,7 +376,8 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
                 }
                 if (++sb == kBlockSteps || r0 + 32 >= r_end) {
                     __syncwarp();
-                    // lane i takes rows [8i, 8i + 8) of the block: byte i % 4 of step i / 4
+                    // lane i takes rows [Bi, Bi + B) of the block (B = kBlockSteps): bits
+                    // B (i % (32 / B)) .. of step i / (32 / B)
 #pragma unroll
                     for (int g = 0; g < kSharedG; ++g) {
                         uint32_t qs = __ballot_sync(0xffffffffu, seen[g] != 0u);
@@ -382,8 +385,9 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
                         while (qs) {
                             const int q = __ffs(qs) - 1;
                             qs &= qs - 1;
-                            const uint32_t w = (uint32_t)(lane >> 2) < sb ? tb[(g * 32 + q) * kBlockStride + (lane >> 2)] : 0u;
-                            uint32_t bits = (w >> (8 * (lane & 3))) & 0xffu;
+                            const uint32_t word = (uint32_t)lane / kLanesPerWord;
+                            const uint32_t w = word < sb ? tb[(g * 32 + q) * kBlockStride + word] : 0u;
+                            uint32_t bits = (w >> (kBlockSteps * ((uint32_t)lane % kLanesPerWord))) & kLaneBits;
                             const uint32_t c8 = __popc(bits);
                             uint32_t incl = c8;
 #pragma unroll
@@ -400,7 +404,7 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
                                     const int e = __ffs(bits) - 1;
                                     bits &= bits - 1;
                                     if (pos < p.capacity)
-                                        p.ids[pos] = (uint32_t)(block_row0 + 8u * lane + e);
+                                        p.ids[pos] = (uint32_t)(block_row0 + kBlockSteps * lane + e);
                                     ++pos;
                                 }
                                 if (lane == q)

@@ -259,10 +259,10 @@ int mdrq_learn_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *widenings);
  * result-buffer budget), writes the admitted answers into their arena slots, and lets
  * the rest wait, ahead of later arrivals. Two batches may be on the GPU at once (two
  * streams), so arrivals are admitted as slots and memory free up and their work
- * overlaps the batch in flight. A batch of at most four queries is answered by the
- * plain scan into a per-stream scratch buffer of 4n ids (allocated at start when it is
- * at most 1 GiB, else small batches take the shared scan too) and copied into its
- * arena slots. While a server runs, t must not be used otherwise.
+ * overlaps the batch in flight. A batch of at most b queries is answered by the plain
+ * scan into a per-stream scratch buffer of b * n ids and copied into its arena slots,
+ * with b = min(12, 2^28 / n) (the buffer stays within 1 GiB; b = 0, no plain path, on
+ * tables of more than 2^28 rows). While a server runs, t must not be used otherwise.
  * Errors: MDRQ_E_INVAL (t or out NULL, result_bytes < 4, max_batch 0); MDRQ_E_NOMEM;
  * MDRQ_E_CUDA.
  */
@@ -286,6 +286,20 @@ int mdrq_server_wait(mdrq_server *s, uint64_t ticket, int64_t timeout_us, const 
 
 /* mdrq_server_release — return an answered query's arena memory (its ids pointer dies). */
 int mdrq_server_release(mdrq_server *s, uint64_t ticket);
+
+/* mdrq_server_submit_batch — submit nq queries at once (one lock, one wake-up of the
+ * scheduler); tickets (host, nq entries) receive their tickets in order. Every query is
+ * encoded first: a bad one submits none of them. Errors: as mdrq_server_submit. */
+int mdrq_server_submit_batch(mdrq_server *s, const mdrq_qdesc *qs, uint32_t nq, uint64_t *tickets);
+
+/* mdrq_server_wait_many — wait until every one of the n tickets is answered (or
+ * timeout_us, when >= 0, passes: MDRQ_E_TIMEOUT, nothing reported), then fill status,
+ * counts and latency_us (host arrays of n entries, each may be NULL) as
+ * mdrq_server_wait does per ticket; with release != 0 the answers are released as by
+ * mdrq_server_release (for callers that need the sizes only, or that drain the server).
+ * Errors: MDRQ_E_INVAL (s NULL, an unknown ticket); the per-ticket status otherwise. */
+int mdrq_server_wait_many(mdrq_server *s, const uint64_t *tickets, uint32_t n, int64_t timeout_us, int *status,
+                          uint64_t *counts, double *latency_us, int release);
 
 /* mdrq_server_stats — answered queries, batches run, deferrals (a query sent back to
  * wait for memory counts once per time), and the median and 99th percentile of the

@@ -37,9 +37,10 @@ using Clock = std::chrono::steady_clock;
 
 // Batches of at most this many queries are answered by the plain scan, whose cost
 // follows the columns the queries read; the shared scan's two passes over every row of
-// the table only pay for larger batches. Used when the scratch answer buffer of
-// kPlainServeMax * n ids per stream stays within kPlainServeScratchBytes.
-constexpr uint32_t kPlainServeMax = 4;
+// the table only pay for larger batches. The scratch answer buffer of a stream holds
+// (that many) * n ids within kPlainServeScratchBytes, which lowers the limit on large
+// tables (no plain path when not even one answer fits).
+constexpr uint32_t kPlainServeMax = 12;
 constexpr uint64_t kPlainServeScratchBytes = 1ull << 30;
 
 struct Request {
@@ -127,6 +128,7 @@ struct mdrq_server {
     mdrq_table *plain[2] = {nullptr, nullptr};
     uint32_t *scratch_ids[2] = {nullptr, nullptr};
     uint64_t scratch_cap = 0;
+    uint32_t plain_max = 0;  // batches up to this size take the plain scan
     unsigned long long *host_buf[2] = {nullptr, nullptr};  // pinned: totals, then bases
     size_t host_cap[2] = {0, 0};
     bool busy[2] = {false, false};
@@ -193,7 +195,7 @@ void scheduler_main(mdrq_server *S)
             live[i] = (uint32_t)i;
         const size_t nb = batch.size();
         cudaStream_t st = S->stream[k];
-        const bool plain = S->plain[k] && nb <= kPlainServeMax;
+        const bool plain = S->plain[k] && nb <= S->plain_max;
 
         // exact answer sizes of the batch: the shared scan's count phase, or for a small
         // batch the whole plain scan into the scratch buffer
@@ -392,8 +394,9 @@ int mdrq_server_start(mdrq_table *t, uint64_t result_bytes, uint32_t max_batch, 
             if (!S->state[k])
                 rc = MDRQ_E_NOMEM;
         }
-        if (rc == MDRQ_OK && t->n > 0 && (uint64_t)kPlainServeMax * t->n * 4 <= kPlainServeScratchBytes) {
-            S->scratch_cap = (uint64_t)kPlainServeMax * t->n;
+        S->plain_max = t->n > 0 ? (uint32_t)std::min<uint64_t>(kPlainServeMax, kPlainServeScratchBytes / (t->n * 4)) : 0;
+        if (rc == MDRQ_OK && S->plain_max > 0) {
+            S->scratch_cap = (uint64_t)S->plain_max * t->n;
             rc = make_shadow(t, S->stream[k], &S->plain[k]);
             if (rc == MDRQ_OK) {
                 S->plain[k]->batch_mode = MDRQ_BATCH_PLAIN;
@@ -469,6 +472,87 @@ int mdrq_server_wait(mdrq_server *S, uint64_t ticket, int64_t timeout_us, const 
     if (latency_us)
         *latency_us = std::chrono::duration<double, std::micro>(r.t_done - r.t_submit).count();
     return r.status;
+}
+
+int mdrq_server_submit_batch(mdrq_server *S, const mdrq_qdesc *qs, uint32_t nq, uint64_t *tickets)
+{
+    if (!S || (nq > 0 && (!qs || !tickets)))
+        return MDRQ_E_INVAL;
+    std::vector<EncodedQuery> enc(nq);
+    for (uint32_t i = 0; i < nq; ++i) {
+        if (qs[i].reserved != 0)
+            return MDRQ_E_INVAL;
+        const int rc = encode_query(S->t, qs[i].preds, qs[i].npreds, enc[i]);
+        if (rc != MDRQ_OK)
+            return rc;
+    }
+    std::lock_guard<std::mutex> lock(S->mu);
+    if (S->stopping)
+        return MDRQ_E_INVAL;
+    if (S->fatal != MDRQ_OK)
+        return S->fatal;
+    const Clock::time_point now = Clock::now();
+    for (uint32_t i = 0; i < nq; ++i) {
+        const uint64_t tk = S->next_ticket++;
+        Request &r = S->reqs[tk];
+        r.t_submit = now;
+        if (enc[i].empty || S->t->n == 0) {
+            finish(S, tk, MDRQ_OK, now);
+        } else {
+            r.enc = std::move(enc[i]);
+            S->pending.push_back(tk);
+        }
+        tickets[i] = tk;
+    }
+    S->cv_sched.notify_one();
+    return MDRQ_OK;
+}
+
+int mdrq_server_wait_many(mdrq_server *S, const uint64_t *tickets, uint32_t n, int64_t timeout_us, int *status,
+                          uint64_t *counts, double *latency_us, int release)
+{
+    if (!S || (n > 0 && !tickets))
+        return MDRQ_E_INVAL;
+    std::unique_lock<std::mutex> lock(S->mu);
+    for (uint32_t i = 0; i < n; ++i)
+        if (S->reqs.find(tickets[i]) == S->reqs.end())
+            return MDRQ_E_INVAL;
+    auto all_done = [&] {
+        for (uint32_t i = 0; i < n; ++i) {
+            auto f = S->reqs.find(tickets[i]);
+            if (f != S->reqs.end() && f->second.status == 1)
+                return false;
+        }
+        return true;
+    };
+    if (timeout_us < 0)
+        S->cv_done.wait(lock, all_done);
+    else if (!S->cv_done.wait_for(lock, std::chrono::microseconds(timeout_us), all_done))
+        return MDRQ_E_TIMEOUT;
+    bool freed = false;
+    for (uint32_t i = 0; i < n; ++i) {
+        auto it = S->reqs.find(tickets[i]);
+        if (it == S->reqs.end()) {
+            if (status)
+                status[i] = MDRQ_E_INVAL;  // released meanwhile by another thread
+            continue;
+        }
+        const Request &r = it->second;
+        if (status)
+            status[i] = r.status;
+        if (counts)
+            counts[i] = r.count;
+        if (latency_us)
+            latency_us[i] = std::chrono::duration<double, std::micro>(r.t_done - r.t_submit).count();
+        if (release) {
+            S->arena.release(r.slot, r.words);
+            S->reqs.erase(it);
+            freed = true;
+        }
+    }
+    if (freed)
+        S->cv_sched.notify_all();
+    return MDRQ_OK;
 }
 
 int mdrq_server_release(mdrq_server *S, uint64_t ticket)

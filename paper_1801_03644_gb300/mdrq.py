@@ -54,7 +54,8 @@ EXPORTS = ["mdrq_load_columns", "mdrq_query", "mdrq_query_batch", "mdrq_free",
            "mdrq_server_release", "mdrq_server_stats", "mdrq_server_stop", "mdrq_prepare_batch",
            "mdrq_prepared_launch", "mdrq_prepared_wait", "mdrq_prepared_kernels", "mdrq_prepared_free",
            "mdrq_set_shared_config", "mdrq_set_shared_bits_budget", "mdrq_autotune",
-           "mdrq_set_zone_maps", "mdrq_zone_map_info", "mdrq_zone_scan_info"]
+           "mdrq_set_zone_maps", "mdrq_zone_map_info", "mdrq_zone_scan_info",
+           "mdrq_server_submit_batch", "mdrq_server_wait_many"]
 
 FAULT_SKIP_TILES, FAULT_NOMEM = 1, 2
 BATCH_AUTO, BATCH_PLAIN, BATCH_SHARED, BATCH_LEARNED = 0, 1, 2, 3
@@ -123,6 +124,11 @@ def lib():
         L.mdrq_query_static.restype = ctypes.c_int
         L.mdrq_query_static.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(i32), u32, u64,
                                         ctypes.POINTER(Pred), u32, vp, u64, ctypes.POINTER(u64), vp]
+        L.mdrq_server_submit_batch.restype = ctypes.c_int
+        L.mdrq_server_submit_batch.argtypes = [vp, ctypes.POINTER(QDesc), u32, ctypes.POINTER(u64)]
+        L.mdrq_server_wait_many.restype = ctypes.c_int
+        L.mdrq_server_wait_many.argtypes = [vp, ctypes.POINTER(u64), u32, ctypes.c_int64, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_double), ctypes.c_int]
         L.mdrq_set_zone_maps.restype = ctypes.c_int
         L.mdrq_set_zone_maps.argtypes = [vp, ctypes.c_int]
         L.mdrq_zone_map_info.restype = ctypes.c_int
@@ -587,6 +593,32 @@ class Server:
         if st == OK and cnt.value:
             ids = torch.as_tensor(_DeviceIds(int(ptr.value), int(cnt.value)), device="cuda")
         return st, ids, int(cnt.value), lat.value
+
+    def submit_batch(self, encoded) -> np.ndarray:
+        """``mdrq_server_submit_batch`` of a batch from ``Table.encode_batch``; returns the
+        tickets (uint64)."""
+        descs, _keep, nq = encoded
+        tk = np.zeros(max(1, nq), dtype=np.uint64)
+        st = lib().mdrq_server_submit_batch(self._h, descs, nq, tk.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+        if st != OK:
+            raise MDRQError(st, "mdrq_server_submit_batch")
+        return tk[:nq]
+
+    def wait_many(self, tickets, release: bool = True, timeout_us: int = -1):
+        """``mdrq_server_wait_many``: (status int32, counts uint64, latency_us float64)
+        arrays for the tickets, answers released when ``release``."""
+        tk = np.ascontiguousarray(np.asarray(tickets, dtype=np.uint64))
+        n = tk.size
+        status = np.zeros(max(1, n), dtype=np.int32)
+        counts = np.zeros(max(1, n), dtype=np.uint64)
+        lat = np.zeros(max(1, n), dtype=np.float64)
+        st = lib().mdrq_server_wait_many(self._h, tk.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), n,
+                                         int(timeout_us), status.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                         counts.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                         lat.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1 if release else 0)
+        if st != OK:
+            raise MDRQError(st, "mdrq_server_wait_many")
+        return status[:n], counts[:n], lat[:n]
 
     def release(self, ticket: int):
         st = lib().mdrq_server_release(self._h, int(ticket))

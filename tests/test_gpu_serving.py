@@ -128,3 +128,29 @@ def test_small_batches_and_bursts(M):
     for j, (st, got) in enumerate(res):
         assert st == M.OK and np.array_equal(got, oracle.mdrq(wl.columns, wl.queries[30 + j], 8)), j
     assert stats["batches"] >= 20
+
+
+def test_bulk_submit_and_wait_many(M):
+    """mdrq_server_submit_batch / mdrq_server_wait_many: the same answers (sizes) as one
+    query at a time, answers released by the wait; a bad query submits nothing."""
+    wl = W.serving_table(n=400_003, nq=300)
+    cols = _device(wl.columns)
+    with M.Table(cols) as t:
+        sizes = [t.query(q).numel() for q in wl.queries]
+        srv = M.Server(t, result_bytes=64 << 20, max_batch=64)
+        enc = t.encode_batch(wl.queries)
+        tk = srv.submit_batch(enc)
+        assert tk.size == len(wl.queries) and np.all(np.diff(tk.astype(np.int64)) == 1)
+        status, counts, lat = srv.wait_many(tk[:150], release=True)
+        assert np.all(status == M.OK) and np.array_equal(counts, np.asarray(sizes[:150], np.uint64))
+        assert np.all(lat > 0)
+        # the rest: waited without release, then read one by one
+        status, counts, lat = srv.wait_many(tk[150:], release=False)
+        assert np.all(status == M.OK)
+        for k, q in zip(tk[150:160], wl.queries[150:160]):
+            st, ids, cnt, _ = srv.wait(int(k))
+            got = M.as_uint32_numpy(ids).copy() if ids is not None else np.zeros(0, np.uint32)
+            assert np.array_equal(got, oracle.mdrq(wl.columns, q, 8))
+        with pytest.raises(M.MDRQError):
+            srv.wait_many(tk[:1])  # already released
+        assert srv.stop() == M.OK

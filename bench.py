@@ -127,6 +127,9 @@ def gpu_smi_id(torch, dev: int) -> str:
 
 # ----------------------------------------------------------------------------- peaks, traffic
 
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
+
+
 def measured_peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -528,6 +531,23 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
                       "mode": "shared scan, autotuned shape (0 = built-in rule), replayed as a "
                               "prepared CUDA graph"})
         batched["tuned_graph"] = tuned
+        # the shared scan's two bounds: ALU issue for the per-predicate work (two compares
+        # and an AND per constrained value, rows x predicates x 3 simple operations at
+        # SMs x 128 lanes x the SM clock), and HBM for the least bytes a batch needs
+        # (every constrained column once, plus the ids)
+        ops = 3.0 * wl.n * sum(len({p[0] for p in q}) for q in wl.queries)
+        sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+        alu_peak = torch.cuda.get_device_properties(dev).multi_processor_count * 128 * sm_mhz * 1e6
+        cols = len({p[0] for q in wl.queries for p in q})
+        least_bytes = 4.0 * wl.n * cols + 4.0 * total_ids
+        for leg in (batched, tuned):
+            t_s = leg["ms_per_step"] / 1e3
+            leg["alu_frac"] = ops / t_s / alu_peak
+            leg["hbm_frac_least_bytes"] = least_bytes / t_s / 1e9 / measured_peaks()["hbm_gbs"]
+        batched["bounds"] = {"ops_per_batch": ops, "alu_peak_ops_per_s": alu_peak,
+                             "least_bytes_per_batch": least_bytes,
+                             "note": "per-predicate operation count; the shared scan's own "
+                                     "operations are interval lookups per column and chunk"}
         table.set_batch_mode(mdrq.BATCH_PLAIN)
 
     # ---- learned range narrower: on this table when it is Z-sorted, else on its own
@@ -578,7 +598,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
                 "kernel": "mdrq_scan_kernel",
                 "alg_bytes_per_launch": alg_per_launch,
                 "avg_launch_ms": avg_launch_s * 1e3,
-                "scan_launches": timing["scan_launches"]}
+                "scan_launches": timing["scan_launches"],
+                "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+                "dram_gbs_moved": traffic / avg_launch_s / 1e9 if traffic and avg_launch_s > 0 else None}
 
     # ---- CPU baseline: the oracle as it stands, on the host cores (rank 0, N = 1)
     cpu = None

@@ -581,8 +581,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
         e2e = {"value": world * nq * args.steps / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": 16 * npreds + 16 * nq,
                "d2h_bytes_per_step": 8 * (nq + 1) + 4 * total_ids,
-               "path": "mdrq_query_batch with host query descriptors; the scan writes the ids "
-                       "into a pinned host buffer through its device mapping; host wall clock"}
+               "path": "mdrq_query_batch with host query descriptors and a pinned host answer "
+                       "buffer (each launch's ids copied while the next runs); host wall clock"}
 
     # ---- roofline of the scan kernel (algorithmic bytes / event-timed duration)
     peaks = measured_peaks()

@@ -110,11 +110,12 @@ int mdrq_load_columns(const void *const *cols, const int32_t *types, uint32_t d,
  *  preds, npreds  host array of predicates; npreds = 0 is the full-domain query
  *                 (all n ids). At most 128 distinct dimensions may be constrained.
  *  ids            output, `capacity` uint32 slots; device memory when
- *                 ids_on_device = 1, host memory when 0. A page-locked host buffer
- *                 (cudaHostAlloc / cudaHostRegister, e.g. a pinned torch tensor) is
- *                 written by the scan directly through its device mapping, while the
- *                 scan runs; other host memory receives one copy after the scan from
- *                 a device staging buffer the table keeps.
+ *                 ids_on_device = 1, host memory when 0. Host answers go through a
+ *                 device staging buffer of `capacity` ids that the table keeps; a plain
+ *                 batch runs as several launches and the ids of each are copied out
+ *                 (on a second stream) while the next one runs. Page-locked host memory
+ *                 (cudaHostAlloc / cudaHostRegister, a pinned torch tensor) copies
+ *                 fastest.
  *  count          host; receives the length of the answer (also when it exceeds
  *                 capacity).
  *

@@ -131,6 +131,8 @@ namespace mdrq {
 
 constexpr size_t kAutoSharedMinQueries = 32;       // MDRQ_BATCH_AUTO: shared scan from this many
 constexpr uint64_t kAutoSharedMinRows = 4000000;   // queries, on tables of at least this many rows
+constexpr size_t kSinkLaunches = 8;  // plain batches answering into host memory: launches, each
+                                     // one's ids copied out while the next one runs
 
 int cuda_status(cudaError_t e)
 {
@@ -484,6 +486,26 @@ int encode_batch(const mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, std::ve
     return MDRQ_OK;
 }
 
+// Host answers: copy the ids of the launch awaiting its copy (if any) to the host
+// buffer, once it has finished; the launch after it may already be running.
+static int sink_flush(mdrq_table *t)
+{
+    HostSink &k = *t->sink;
+    if (!k.pending)
+        return MDRQ_OK;
+    k.pending = false;
+    MDRQ_TRY(cudaStreamWaitEvent(k.copy, k.pending_done, 0));
+    MDRQ_TRY(cudaMemcpyAsync(k.end_host, t->offsets_dev + k.pending_last + 1, 8, cudaMemcpyDeviceToHost, k.copy));
+    MDRQ_TRY(cudaStreamSynchronize(k.copy));
+    const uint64_t end = std::min<uint64_t>(*k.end_host, k.capacity);
+    if (end > k.copied) {
+        MDRQ_TRY(cudaMemcpyAsync(k.host + k.copied, t->ids_stage + k.copied, (end - k.copied) * 4,
+                                 cudaMemcpyDeviceToHost, k.copy));
+        k.copied = end;
+    }
+    return MDRQ_OK;
+}
+
 // Everything a batch does on the stream: the query tables to the device, the scan
 // launches of the table's batch mode, and the offsets and error word back to pinned
 // host memory. Asynchronous. It allocates nothing once the table's buffers have the
@@ -568,8 +590,12 @@ int enqueue_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std
             t->acc_scans += 1;
         }
     }
-    // one launch per chunk of queries whose ids fit the 40-bit state values
-    const uint64_t per_launch = std::max<uint64_t>(1, kValueMask / std::max<uint64_t>(1, t->n));
+    // one launch per chunk of queries whose ids fit the 40-bit state values; with the
+    // answers bound for host memory, four launches at least, each one's ids copied out
+    // while the next runs
+    uint64_t per_launch = std::max<uint64_t>(1, kValueMask / std::max<uint64_t>(1, t->n));
+    if (t->sink)
+        per_launch = std::min<uint64_t>(per_launch, std::max<size_t>(1, (nlive + kSinkLaunches - 1) / kSinkLaunches));
     for (size_t c0 = 0; !shared && !learned_mode && c0 < nlive; c0 += per_launch) {
         const uint32_t cnt = (uint32_t)std::min<uint64_t>(per_launch, nlive - c0);
         uint64_t cols = 0;
@@ -583,6 +609,13 @@ int enqueue_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std
         // zone maps in use: scan only the tiles they do not rule out
         st = zones ? zone_batch(t, (uint32_t)c0, cnt, cols, out, capacity, base, s)
                    : launch_scan(t, (uint32_t)c0, cnt, cols, out, capacity, base, s);
+        if (st == MDRQ_OK && t->sink) {
+            st = sink_flush(t);  // the previous launch's ids, while this one runs
+            if (st == MDRQ_OK)
+                st = cuda_status(cudaEventRecord(t->sink->pending_done, s));
+            t->sink->pending = true;
+            t->sink->pending_last = live[c0 + cnt - 1];
+        }
         if (st != MDRQ_OK) {
             reset_scratch(t, s);
             return st;
@@ -637,40 +670,52 @@ int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, u
         t->inject_nomem = 0;
         return MDRQ_E_NOMEM;
     }
-    // a host answer buffer that is page-locked is written by the scan itself, through
-    // its device mapping over the CPU-GPU link, while the scan runs; any other host
-    // buffer goes through a device staging buffer and one copy after the scan
+    // host answers: the scan writes a device staging buffer, and the ids of each finished
+    // launch are copied to the host on a second stream while the next launch runs
     uint32_t *out = ids;
-    bool staged = false;
+    HostSink sink;
     if (!ids_on_device && capacity > 0) {
-        cudaPointerAttributes a;
-        if (cudaPointerGetAttributes(&a, ids) == cudaSuccess && a.type == cudaMemoryTypeHost && a.devicePointer) {
-            out = static_cast<uint32_t *>(a.devicePointer);
-        } else {
-            (void)cudaGetLastError();
-            st = grow_device((void **)&t->ids_stage, &t->ids_stage_cap, (size_t)capacity * 4);
-            if (st != MDRQ_OK)
-                return st;
-            out = t->ids_stage;
-            staged = true;
+        st = grow_device((void **)&t->ids_stage, &t->ids_stage_cap, (size_t)capacity * 4);
+        if (st == MDRQ_OK && !t->sink_copy) {
+            st = cuda_status(cudaStreamCreateWithFlags(&t->sink_copy, cudaStreamNonBlocking));
+            if (st == MDRQ_OK)
+                st = cuda_status(cudaEventCreateWithFlags(&t->sink_done, cudaEventDisableTiming));
+            if (st == MDRQ_OK)
+                st = grow_pinned((void **)&t->sink_end, &t->sink_end_cap, 8);
         }
+        if (st != MDRQ_OK)
+            return st;
+        out = t->ids_stage;
+        sink.host = ids;
+        sink.capacity = capacity;
+        sink.copy = t->sink_copy;
+        sink.end_host = t->sink_end;
+        sink.pending_done = t->sink_done;
+        t->sink = &sink;
     }
     st = enqueue_batch(t, enc, live, nq, npreds, out, capacity, s);
+    if (st == MDRQ_OK)
+        st = finish_batch(t, live, nq, offsets, s);
+    const uint64_t total = st == MDRQ_OK ? offsets[nq] : 0;
+    if (t->sink) {
+        // the rest of the ids (the last launch's, or all of a shared or learned batch)
+        sink.pending = false;
+        if (st == MDRQ_OK && std::min<uint64_t>(total, capacity) > sink.copied) {
+            const uint64_t end = std::min<uint64_t>(total, capacity);
+            st = cuda_status(cudaMemcpyAsync(ids + sink.copied, t->ids_stage + sink.copied, (end - sink.copied) * 4,
+                                             cudaMemcpyDeviceToHost, sink.copy));
+        }
+        const int cs = cuda_status(cudaStreamSynchronize(sink.copy));
+        t->sink = nullptr;
+        if (st == MDRQ_OK)
+            st = cs;
+    }
     if (st != MDRQ_OK)
         return st;
-    st = finish_batch(t, live, nq, offsets, s);
-    if (st != MDRQ_OK)
-        return st;
-    const uint64_t total = offsets[nq];
     // 4 bytes per id written
     t->last_bytes += 4ull * std::min<uint64_t>(total, capacity);
     if (t->timing)
         t->acc_bytes += 4ull * std::min<uint64_t>(total, capacity);
-    if (staged && total > 0) {
-        MDRQ_TRY(cudaMemcpyAsync(ids, t->ids_stage, (size_t)std::min<uint64_t>(total, capacity) * 4,
-                                 cudaMemcpyDeviceToHost, s));
-        MDRQ_TRY(cudaStreamSynchronize(s));
-    }
     return total > capacity ? MDRQ_E_CAPACITY : MDRQ_OK;
 }
 
@@ -745,6 +790,11 @@ void destroy(mdrq_table *t)
     zone_windows_free(t);
     learned_free(t);
     cudaFree(t->ids_stage);
+    if (t->sink_copy)
+        cudaStreamDestroy(t->sink_copy);
+    if (t->sink_done)
+        cudaEventDestroy(t->sink_done);
+    cudaFreeHost(t->sink_end);
     cudaFree(t->dq_dev);
     cudaFree(t->dp_dev);
     cudaFreeHost(t->qstage_host);

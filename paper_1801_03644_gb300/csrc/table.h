@@ -34,6 +34,19 @@ struct EncodedQuery {
 
 struct SharedScanState;  // device buffers of the batched shared scan (batched.cu)
 struct ZoneWindows;      // device buffers of the zone-pruned scan (zones.cu)
+
+// A batch answering into host memory: the ids go to the device staging buffer and are
+// copied to `host` on the copy stream, a finished launch's range while the next runs.
+struct HostSink {
+    uint32_t *host = nullptr;
+    uint64_t capacity = 0;
+    cudaStream_t copy = nullptr;
+    unsigned long long *end_host = nullptr;  // pinned: a launch's CSR end, read back
+    uint64_t copied = 0;                      // ids copied so far
+    bool pending = false;                     // a launch whose ids are still to be copied
+    cudaEvent_t pending_done = nullptr;
+    uint32_t pending_last = 0;                // the caller's index of its last query
+};
 struct LearnedModel;     // learned range narrower (learned.cu)
 
 }  // namespace mdrq
@@ -67,6 +80,10 @@ struct mdrq_table {
     size_t offsets_host_cap = 0;
     uint32_t *ids_stage = nullptr;  // device staging for host-side answers
     size_t ids_stage_cap = 0;
+    cudaStream_t sink_copy = nullptr;  // copies of host answers out of the staging buffer
+    cudaEvent_t sink_done = nullptr;
+    unsigned long long *sink_end = nullptr;  // pinned
+    size_t sink_end_cap = 0;
     int *error_host = nullptr;      // pinned
 
     int sm_count = 0;
@@ -92,6 +109,7 @@ struct mdrq_table {
     mdrq::LearnedModel *learned = nullptr;
 
     int zone_mode = MDRQ_ZONES_AUTO;  // mdrq_set_zone_maps
+    mdrq::HostSink *sink = nullptr;   // set while a batch answers into host memory (run_batch)
     mdrq::ZoneWindows *zwin = nullptr;
 
     // set on the private table of a prepared batch while its launches are captured

@@ -221,9 +221,10 @@ def test_repeat_calls_reuse_scratch(M):
 
 
 @pytest.mark.parametrize("mode", [1, 2], ids=["plain", "shared"])
-def test_pinned_host_answers_written_directly(M, mode):
-    """A page-locked host buffer receives the answers from the scan itself; the result
-    and the capacity rule are those of the device path; pageable memory still works."""
+def test_host_answers_pinned_and_pageable(M, mode):
+    """Host answers (staged; a plain batch's launches copied out one by one while the next
+    runs): the result and the capacity rule are those of the device path, for a
+    page-locked and a pageable buffer, with the capacity cut inside a middle launch."""
     import torch
     wl = W.mixed_clustered(n=1_000_003, nq=40)
     want = [oracle.mdrq(wl.columns, q, 8) for q in wl.queries]

@@ -52,8 +52,9 @@ def make_workload(name: str, rows=None, queries=None):
         wl = W.zorder_learned(**kw)
     else:
         raise SystemExit("unknown workload %s" % name)
-    if queries:
+    if queries and int(queries) < len(wl.queries):
         wl.queries = wl.queries[: int(queries)]
+        wl.recipe += "; the first %d of them" % int(queries)
     return wl
 
 

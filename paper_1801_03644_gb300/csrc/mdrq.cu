@@ -131,7 +131,7 @@ namespace mdrq {
 
 constexpr size_t kAutoSharedMinQueries = 32;       // MDRQ_BATCH_AUTO: shared scan from this many
 constexpr uint64_t kAutoSharedMinRows = 4000000;   // queries, on tables of at least this many rows
-constexpr size_t kSinkLaunches = 8;  // plain batches answering into host memory: launches, each
+constexpr size_t kSinkLaunches = 16;  // plain batches answering into host memory: launches, each
                                      // one's ids copied out while the next one runs
 
 int cuda_status(cudaError_t e)

@@ -596,7 +596,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
                 "frac": achieved / peaks["hbm_gbs"],
                 "traffic": traffic,
                 "peak_source": peaks["source"] + " (HBM copy bandwidth)",
-                "kernel": "mdrq_scan_kernel",
+                "kernel": ("mdrq_scan_window_kernel (plain batch over the tiles the zone maps leave)"
+                           if args.workload == "zorder_learned" else "mdrq_scan_kernel"),
                 "alg_bytes_per_launch": alg_per_launch,
                 "avg_launch_ms": avg_launch_s * 1e3,
                 "scan_launches": timing["scan_launches"],

@@ -218,17 +218,20 @@ int mdrq_set_batch_mode(mdrq_table *t, int mode);
  *
  * The table's rows must already be sorted by the 32-bit Z-order (Morton) key of the
  * float32 columns dims[0 .. ndims) (1 <= ndims <= 4): with cell(x) = clamp(floor(x *
- * 256), 0, 255) in float32, key bit 4b + j is bit b of cell(x_dims[j]). Every object in
- * a query box then has a key between the keys of the box's corners, so it lies in one
- * run of rows of the sorted table. The model predicts that run from the corner keys:
+ * 256), 0, 255) in float32, key bit 4b + j is bit b of cell(x_dims[j]). The cells of a
+ * query box then form key ranges, each one run of rows of the sorted table. Per batch
+ * the GPU splits every query's box into at most 1024 such ranges (the key-bit tree
+ * expanded level by level, largest runs first; the ranges left at the budget cover
+ * some cells outside the box, whose rows the scan rejects), and the model predicts
+ * each range's run from its end keys:
  *  MDRQ_MODEL_PLA  piecewise-linear, 4096 segments through evenly spaced (key, row)
  *                  pairs of the sorted keys, FP32;
  *  MDRQ_MODEL_MLP  1-32-32-1 ReLU network, FP32, trained on the GPU (Adam, 3000 steps
  *                  of 8192 pairs from a 2^20-pair sample).
- * Its largest error over all n keys is measured exhaustively (mdrq_learn_info). A
- * query's window is proven against the key column (widened until the keys just outside
- * it lie outside the query's key range) before it is scanned with every predicate, so
- * answers equal the full scan's whatever the model. Training and the key column (4
+ * Its largest error over all n keys is measured exhaustively (mdrq_learn_info). Each
+ * predicted window is proven against the key column (widened until the keys just
+ * outside it lie outside the range) and narrowed to the range's exact run before it is
+ * scanned with every predicate, so answers equal the full scan's whatever the model. Training and the key column (4
  * bytes per row) stay with the table; calling again replaces the model.
  *
  * Errors: MDRQ_E_INVAL (bad dims or model, a dim that is not float32, n = 0, or rows not

@@ -252,7 +252,12 @@ def learned_leg(args, table, enc, step, nq, total_ids, world, barrier, stream):
         info = table.learn([0, 1, 2, 3], model)
         lvalue, lms, off_l = timed(mdrq.BATCH_LEARNED, mdrq.ZONES_AUTO)
         rows, widen = table.learn_window_rows()
+        # bytes as the learned narrower's roofline counts them: 16 per window row (the
+        # four key columns) plus the ids
+        lbytes = 16.0 * rows + 4.0 * total_ids
         out[name] = {"value": lvalue, "unit": UNIT, "ms_per_step": lms,
+                     "window_gbs": lbytes / (lms / 1e3) / 1e9,
+                     "window_frac": lbytes / (lms / 1e3) / 1e9 / measured_peaks()["hbm_gbs"],
                      "speedup_vs_plain": lvalue / base, "speedup_vs_zone_pruned": lvalue / zval,
                      "max_error_rows": info["max_error"],
                      "segments": info["segments"], "train_ms": info["train_ms"],

@@ -78,15 +78,17 @@ SIZES = [0, 1, 2, 3, 4, 5, 31, 32, 33, 127, 128, 129, 511, 512, 513, 1023, 1024,
 
 @pytest.mark.parametrize("n", SIZES)
 @pytest.mark.parametrize("on_device", [True, False], ids=["device_cols", "host_cols"])
-def test_edge_sizes(M, n, on_device):
+@pytest.mark.parametrize("mode", [1, 2], ids=["plain", "shared"])
+def test_edge_sizes(M, n, on_device, mode):
     rng = np.random.default_rng(1000 + n)
     cols = [rng.random(n, dtype=np.float32),
             rng.integers(-40, 40, size=n, dtype=np.int32),
             np.floor(rng.random(n, dtype=np.float32) * 16).astype(np.float32) / 16]
-    check_batch(M, cols, edge_queries(cols, rng), on_device=on_device)
+    check_batch(M, cols, edge_queries(cols, rng), on_device=on_device, mode=mode)
 
 
-def test_mixed_types_and_special_values(M):
+@pytest.mark.parametrize("mode", [1, 2], ids=["plain", "shared"])
+def test_mixed_types_and_special_values(M, mode):
     rng = np.random.default_rng(5)
     n = 70_001
     x = rng.standard_normal(n).astype(np.float32)
@@ -104,10 +106,41 @@ def test_mixed_types_and_special_values(M):
         [(2, 3, 3), (2, 2, 5)], [(2, 3, 5), (2, 6, 7)], [(0, -1.0, 1.0), (0, -0.5, 2.0), (2, 1, 6)],
         [(2, 0, 7)], [(2, 8, 100)], [(2, -5, -1)], [(1, 0, -1)],
     ]
-    check_batch(M, cols, qs)
+    check_batch(M, cols, qs, mode=mode)
 
 
 MODES = pytest.mark.parametrize("mode", [1, 2], ids=["plain", "shared"])
+
+
+def test_shared_hints_on_wide_and_integer_columns(M):
+    """The shared scan's bucket hints on columns whose ranges stress the float bucket
+    function: int32 over the whole range, floats spanning 1e-30 .. 1e30 and tiny ranges
+    near 1.0, with many queries so that hints are built; plain and shared agree with the
+    oracle."""
+    rng = np.random.default_rng(77)
+    n = 200_003
+    wide_i = rng.integers(-2**31, 2**31 - 1, size=n, dtype=np.int64).astype(np.int32)
+    wide_i[:3] = [-2**31, 2**31 - 1, 0]
+    wide_f = (10.0 ** rng.uniform(-30, 30, size=n) * rng.choice([-1, 1], size=n)).astype(np.float32)
+    narrow_f = (1.0 + rng.integers(0, 200, size=n) * np.float32(2 ** -23)).astype(np.float32)
+    cols = [wide_i, wide_f, narrow_f]
+    qs = []
+    for k in range(300):
+        a, b = sorted(rng.choice(n, size=2, replace=False))
+        c0 = np.sort(wide_i[[a, b]])
+        c1 = np.sort(wide_f[[a, b]])
+        c2 = np.sort(narrow_f[[a, b]])
+        pick = k % 4
+        q = []
+        if pick in (0, 3):
+            q.append((0, int(c0[0]), int(c0[1])))
+        if pick in (1, 3):
+            q.append((1, float(c1[0]), float(c1[1])))
+        if pick in (2, 3):
+            q.append((2, float(c2[0]), float(c2[1])))
+        qs.append(q)
+    check_batch(M, cols, qs, mode=1)
+    check_batch(M, cols, qs, mode=2)
 
 
 @MODES

@@ -92,3 +92,32 @@ def test_learn_rejects_unsorted_rows_and_missing_model(M):
     with M.Table(icol) as t:
         with pytest.raises(M.MDRQError):
             t.learn([0], 1)  # key dimensions must be float32
+
+
+@pytest.mark.parametrize("model", [1, 2], ids=["pla", "mlp"])
+@pytest.mark.parametrize("dims", [(1,), (2, 0), (0, 2, 1), (3, 1, 0, 2)], ids=["1d", "2d", "3d", "4d_permuted"])
+def test_learned_key_widths_and_orders(M, model, dims):
+    """Keys over 1 to 4 of the columns, in any column order (the table sorted by that
+    key), with boxes inside, across and outside the unit cube; answers equal the
+    oracle's and the plain scan's."""
+    rng = np.random.default_rng(100 + len(dims))
+    n = 300_007
+    cols = [rng.random(n, dtype=np.float32) for _ in range(4)]
+    cols[3] = (cols[3] ** 3).astype(np.float32)  # a skewed column
+    key = W.zorder_key([cols[j] for j in dims])
+    o = np.argsort(key, kind="stable")
+    cols = [c[o] for c in cols]
+    qs = []
+    for k in range(64):
+        q = []
+        for j in range(4):
+            if rng.random() < 0.7:
+                lo = float(rng.uniform(-0.1, 1.0))
+                hi = lo + float(rng.uniform(0.0, 0.5))
+                q.append((j, lo, hi))
+        qs.append(q)
+    qs += [[(dims[0], 0.5, 0.5)], [(dims[0], 1.2, 2.0)], [(dims[0], -1.0, -0.5)], [(dims[-1], 0.0, 0.99999994)]]
+    info, got, off, plain, off_p = _learned_answers(M, cols, qs, model, dims=dims)
+    assert np.array_equal(off, off_p) and np.array_equal(got, plain)
+    for q, query in enumerate(qs):
+        assert np.array_equal(got[int(off[q]):int(off[q + 1])], oracle.mdrq(cols, query, 4)), q

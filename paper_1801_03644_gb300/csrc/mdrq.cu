@@ -22,6 +22,21 @@ using namespace mdrq;
 
 namespace mdrq {
 
+// The window of every tile of a windowed launch: map[tile_start + i] = w for the tiles
+// of window w (one warp per window, grid-stride; windows without tiles write nothing).
+__global__ void __launch_bounds__(256) mdrq_tile_map_kernel(const DevWindow *windows,
+                                                            const unsigned long long *nwindows, uint32_t *map)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned long long nw = *nwindows;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    for (uint64_t w = (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); w < nw; w += warps) {
+        const unsigned long long t0 = windows[w].tile_start, nt = windows[w].tiles;
+        for (unsigned long long i = lane; i < nt; i += 32)
+            map[t0 + i] = (uint32_t)w;
+    }
+}
+
 // The scan over per-query row windows (the learned range narrower's exact check, and
 // the tiles the zone maps leave).
 __global__ void __launch_bounds__(kScanThreads, 7) mdrq_scan_window_kernel(const __grid_constant__ ScanParams p)
@@ -411,10 +426,18 @@ int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t max_win
         MDRQ_TRY(cudaMemsetAsync(t->tile_state, 0, ((size_t)1 << t->ring_bits) * 8, s));
         t->tag_next = 1;
     }
+    // the window of every tile, so that a claim finds its window with one load
+    {
+        const int st = grow_device((void **)&t->tile_map, &t->tile_map_cap, (size_t)max_tiles * 4);
+        if (st != MDRQ_OK)
+            return st;
+    }
+    mdrq_tile_map_kernel<<<(uint32_t)t->sm_count * 8, 256, 0, s>>>(windows, nwindows, t->tile_map);
     MDRQ_TRY(cudaMemsetAsync(t->ticket, 0, sizeof(unsigned long long), s));
     ScanParams p;
     std::memset(&p, 0, sizeof(p));
     p.queries = t->dq_dev + q0;
+    p.tile_map = t->tile_map;
     p.preds = t->dp_dev;
     p.nq = nq;
     p.n = t->n;
@@ -446,7 +469,7 @@ int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t max_win
     t->last_bytes += alg_bytes;
     if (t->timing) {
         t->acc_scans += 1;
-        t->acc_kernels += 1 + helper_kernels;
+        t->acc_kernels += 2 + helper_kernels;  // the tile map and the scan
         t->acc_bytes += alg_bytes;
     }
     return MDRQ_OK;
@@ -790,6 +813,7 @@ void destroy(mdrq_table *t)
     zone_windows_free(t);
     learned_free(t);
     cudaFree(t->ids_stage);
+    cudaFree(t->tile_map);
     if (t->sink_copy)
         cudaStreamDestroy(t->sink_copy);
     if (t->sink_done)

@@ -113,6 +113,7 @@ struct ScanParams {
     const DevWindow *windows;        // windowed launches: row runs and their tiles (device)
     const unsigned long long *nwindows_dev;  // windowed launches: number of windows (device)
     const unsigned long long *total_tiles_dev;  // windowed launches: tile count (device)
+    const uint32_t *tile_map;        // windowed launches: the window of every tile (device)
 };
 
 // Where tile t of a launch lies: its query, its first row, the end of the rows it may
@@ -125,23 +126,14 @@ struct TilePlace {
     unsigned long long row_end;
 };
 
-// WINDOWED = false: the query of tile t; true: the window of tile t.
+// WINDOWED = false: the query of tile t; true: the window of tile t (from the tile map
+// the launch builds before the scan).
 template <bool WINDOWED>
 __device__ __forceinline__ uint32_t query_of_tile(const ScanParams &p, unsigned long long t)
 {
     if (!WINDOWED)
         return (uint32_t)(t / p.tiles_per_query);
-    // the last window whose first tile is <= t (windows without tiles share the first
-    // tile of the next window and come before it, so they are never chosen)
-    uint32_t lo = 0, hi = (uint32_t)*p.nwindows_dev;
-    while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (p.windows[mid].tile_start <= t)
-            lo = mid;
-        else
-            hi = mid;
-    }
-    return lo;
+    return p.tile_map[t];
 }
 
 template <bool WINDOWED>

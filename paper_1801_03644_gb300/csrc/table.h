@@ -80,6 +80,8 @@ struct mdrq_table {
     size_t offsets_host_cap = 0;
     uint32_t *ids_stage = nullptr;  // device staging for host-side answers
     size_t ids_stage_cap = 0;
+    uint32_t *tile_map = nullptr;   // windowed launches: the window of every tile
+    size_t tile_map_cap = 0;
     cudaStream_t sink_copy = nullptr;  // copies of host answers out of the staging buffer
     cudaEvent_t sink_done = nullptr;
     unsigned long long *sink_end = nullptr;  // pinned

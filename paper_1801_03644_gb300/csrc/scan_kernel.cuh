@@ -223,6 +223,73 @@ __device__ __forceinline__ uint32_t in_range4(uint4 v, uint32_t type, uint32_t l
     return r;
 }
 
+// lo <= x <= hi for one value read as the column's type (ordered compares): all ones if
+// it holds, else zero, so that a single AND with a constant places the row's bit
+template <bool F32>
+__device__ __forceinline__ uint32_t in_range_ones(uint32_t x, uint32_t lo, uint32_t hi)
+{
+    uint32_t d;
+    if (F32)
+        asm("{\n\t.reg .pred p;\n\tsetp.ge.f32 p, %1, %2;\n\tset.le.and.u32.f32 %0, %1, %3, p;\n\t}"
+            : "=r"(d)
+            : "f"(__uint_as_float(x)), "f"(__uint_as_float(lo)), "f"(__uint_as_float(hi)));
+    else
+        asm("{\n\t.reg .pred p;\n\tsetp.ge.s32 p, %1, %2;\n\tset.le.and.u32.s32 %0, %1, %3, p;\n\t}"
+            : "=r"(d)
+            : "r"(x), "r"(lo), "r"(hi));
+    return d;
+}
+
+// One predicate over a lane's U groups of 4 rows when every row of the warp lies in the
+// table: a group whose rows have all failed issues no load. Returns the surviving mask.
+template <int U, bool F32>
+__device__ __forceinline__ uint32_t filter_full(const uint32_t *col, uint32_t m, uint32_t lo, uint32_t hi)
+{
+    uint4 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        v[u] = make_uint4(0, 0, 0, 0);
+        if ((m >> (4 * u)) & 0xfu)
+            v[u] = ld_stream_v4(col + 128 * u);
+    }
+    uint32_t keep = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        keep |= in_range_ones<F32>(v[u].x, lo, hi) & (1u << (4 * u));
+        keep |= in_range_ones<F32>(v[u].y, lo, hi) & (2u << (4 * u));
+        keep |= in_range_ones<F32>(v[u].z, lo, hi) & (4u << (4 * u));
+        keep |= in_range_ones<F32>(v[u].w, lo, hi) & (8u << (4 * u));
+    }
+    return m & keep;
+}
+
+// The same at the ragged end of the table or of a window: only rows whose bit is set
+// in m are read (they all lie inside the table).
+template <int U>
+__device__ __forceinline__ uint32_t filter_ragged(const uint32_t *col, uint32_t m, uint32_t type, uint32_t lo,
+                                                  uint32_t hi)
+{
+    uint4 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        v[u] = make_uint4(0, 0, 0, 0);
+        const uint32_t mu = (m >> (4 * u)) & 0xfu;
+        if (mu == 0xfu) {
+            v[u] = ld_stream_v4(col + 128 * u);
+        } else if (mu) {
+            if (mu & 1u) v[u].x = ld_stream_u32(col + 128 * u + 0);
+            if (mu & 2u) v[u].y = ld_stream_u32(col + 128 * u + 1);
+            if (mu & 4u) v[u].z = ld_stream_u32(col + 128 * u + 2);
+            if (mu & 8u) v[u].w = ld_stream_u32(col + 128 * u + 3);
+        }
+    }
+    uint32_t keep = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+        keep |= in_range4(v[u], type, lo, hi) << (4 * u);
+    return m & keep;
+}
+
 // What a zone (the value range [min, max] of a row tile) says about [lo, hi]: 0 no row
 // of it can qualify, 2 every row qualifies, 1 its rows must be read
 __device__ __forceinline__ uint32_t zone_verdict(uint2 z, uint32_t type, uint32_t lo, uint32_t hi)
@@ -493,28 +560,13 @@ __device__ __forceinline__ void scan_cta(const ScanParams &p)
                     break;  // every row of this warp's chunk failed: read no more columns
                 const DevPred pr = p.preds[dq.first + i];
                 const uint32_t *col = (const uint32_t *)pr.col + row0 + 4 * lane;
-                uint4 v[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    v[u] = make_uint4(0, 0, 0, 0);
-                    const uint32_t mu = (m >> (4 * u)) & 0xfu;
-                    if (mu) {
-                        if (full || mu == 0xfu) {
-                            v[u] = ld_stream_v4(col + 128 * u);
-                        } else {
-                            // ragged end of the table: only rows < n may be read
-                            if (mu & 1u) v[u].x = ld_stream_u32(col + 128 * u + 0);
-                            if (mu & 2u) v[u].y = ld_stream_u32(col + 128 * u + 1);
-                            if (mu & 4u) v[u].z = ld_stream_u32(col + 128 * u + 2);
-                            if (mu & 8u) v[u].w = ld_stream_u32(col + 128 * u + 3);
-                        }
-                    }
-                }
-                uint32_t keep = 0;
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-                    keep |= in_range4(v[u], pr.type, pr.lo, pr.hi) << (4 * u);
-                m &= keep;
+                // the branches on the warp's extent and the column type are warp-uniform
+                if (!full)
+                    m = filter_ragged<U>(col, m, pr.type, pr.lo, pr.hi);
+                else if (pr.type == kTypeF32)
+                    m = filter_full<U, true>(col, m, pr.lo, pr.hi);
+                else
+                    m = filter_full<U, false>(col, m, pr.lo, pr.hi);
             }
 
             // rank the matches of this warp: row order is (u, lane, e)

@@ -175,6 +175,19 @@ def time_oracle(wl, budget_s: float, nthreads: int, min_queries: int = 2):
     return done, time.perf_counter() - t0
 
 
+def host_cpu_model() -> str:
+    """The host CPU's model name as lscpu prints it (the machine the oracle runs on)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def run_reference(args, rank: int, world: int) -> None:
     """The CPU oracle on the host cores: each step a bounded sample of the same batch."""
     if rank != 0:
@@ -201,7 +214,7 @@ def run_reference(args, rank: int, world: int) -> None:
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "config": cfg,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
-                         "sample": desc},
+                         "sample": desc, "host_cpu": host_cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -616,7 +629,12 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
         m, secs = time_oracle(wl, args.cpu_seconds, nthreads)
         cpu = {"value": m / secs, "unit": UNIT, "cores": nthreads, "kind": "oracle",
                "sample": "first %d of the %d queries, whole table (%d rows), %d threads over "
-                         "contiguous horizontal partitions" % (m, nq, wl.n, nthreads)}
+                         "contiguous horizontal partitions" % (m, nq, wl.n, nthreads),
+               "host_cpu": host_cpu_model()}
+        # Listing 1 as written: one thread, the same queries from the first (a shorter sample)
+        m1, secs1 = time_oracle(wl, args.cpu_seconds / 3.0, 1, min_queries=1)
+        cpu["single_thread"] = {"value": m1 / secs1, "unit": UNIT, "cores": 1,
+                                "sample": "first %d of the %d queries, whole table, 1 thread" % (m1, nq)}
 
     # ---- the learned narrower and the server, each on its own table
     if args.workload != "zorder_learned" and not args.no_learned:

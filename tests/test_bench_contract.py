@@ -24,6 +24,7 @@ def test_reference_arm_prints_one_json_line():
     assert d["higher_is_better"] is True and d["scaling"] == "weak"
     assert d["config"]["workload"].startswith("mixed_clustered") and d["config"]["n"] == 100000
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["host_cpu"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
 
 

@@ -112,8 +112,11 @@ int mdrq_load_columns(const void *const *cols, const int32_t *types, uint32_t d,
  *  ids            output, `capacity` uint32 slots; device memory when
  *                 ids_on_device = 1, host memory when 0. Host answers go through a
  *                 device staging buffer of `capacity` ids that the table keeps; a plain
- *                 batch runs as several launches and the ids of each are copied out
- *                 (on a second stream) while the next one runs. Page-locked host memory
+ *                 batch that scans at least 2 GiB of columns runs as several launches
+ *                 (up to 16, of equal query counts, on average at least 1 GiB of
+ *                 columns each) and the ids of each are copied
+ *                 out (on a second stream) while the next one runs; a smaller batch is
+ *                 one launch followed by one copy. Page-locked host memory
  *                 (cudaHostAlloc / cudaHostRegister, a pinned torch tensor) copies
  *                 fastest.
  *  count          host; receives the length of the answer (also when it exceeds

@@ -146,8 +146,12 @@ namespace mdrq {
 
 constexpr size_t kAutoSharedMinQueries = 32;       // MDRQ_BATCH_AUTO: shared scan from this many
 constexpr uint64_t kAutoSharedMinRows = 4000000;   // queries, on tables of at least this many rows
-constexpr size_t kSinkLaunches = 16;  // plain batches answering into host memory: launches, each
-                                     // one's ids copied out while the next one runs
+// Plain batches answering into host memory run as several launches, each one's ids
+// copied out while the next one runs: at most kSinkLaunches, and each launch scans at
+// least kSinkLaunchBytes of columns, so that its scan outlasts the host's wait for the
+// previous launch (a small batch is one launch and one copy).
+constexpr size_t kSinkLaunches = 16;
+constexpr uint64_t kSinkLaunchBytes = 1ull << 30;
 
 int cuda_status(cudaError_t e)
 {
@@ -614,11 +618,17 @@ int enqueue_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std
         }
     }
     // one launch per chunk of queries whose ids fit the 40-bit state values; with the
-    // answers bound for host memory, four launches at least, each one's ids copied out
-    // while the next runs
+    // answers bound for host memory, up to kSinkLaunches launches of at least
+    // kSinkLaunchBytes of columns each, each one's ids copied out while the next runs
     uint64_t per_launch = std::max<uint64_t>(1, kValueMask / std::max<uint64_t>(1, t->n));
-    if (t->sink)
-        per_launch = std::min<uint64_t>(per_launch, std::max<size_t>(1, (nlive + kSinkLaunches - 1) / kSinkLaunches));
+    if (t->sink && !shared && !learned_mode) {
+        uint64_t scan_bytes = 0;
+        for (size_t i = 0; i < nlive; ++i)
+            scan_bytes += enc[live[i]].scanned_columns * 4ull * t->n;
+        const uint64_t launches =
+            std::max<uint64_t>(1, std::min<uint64_t>(kSinkLaunches, scan_bytes / kSinkLaunchBytes));
+        per_launch = std::min<uint64_t>(per_launch, std::max<uint64_t>(1, (nlive + launches - 1) / launches));
+    }
     for (size_t c0 = 0; !shared && !learned_mode && c0 < nlive; c0 += per_launch) {
         const uint32_t cnt = (uint32_t)std::min<uint64_t>(per_launch, nlive - c0);
         uint64_t cols = 0;

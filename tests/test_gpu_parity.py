@@ -257,9 +257,10 @@ def test_repeat_calls_reuse_scratch(M):
 def test_host_answers_pinned_and_pageable(M, mode):
     """Host answers (staged; a plain batch's launches copied out one by one while the next
     runs): the result and the capacity rule are those of the device path, for a
-    page-locked and a pageable buffer, with the capacity cut inside a middle launch."""
+    page-locked and a pageable buffer, with the capacity cut inside a middle launch.
+    The batch scans more than 2 GiB of columns, so it is split into several launches."""
     import torch
-    wl = W.mixed_clustered(n=1_000_003, nq=40)
+    wl = W.mixed_clustered(n=3_000_017, nq=64)
     want = [oracle.mdrq(wl.columns, q, 8) for q in wl.queries]
     cat = np.concatenate(want)
     total = cat.size
@@ -269,6 +270,9 @@ def test_host_answers_pinned_and_pageable(M, mode):
         pinned = torch.full((total + 64,), -1, dtype=torch.int32, pin_memory=True)
         st, off = t.query_batch_raw(enc, pinned.data_ptr(), total, False)
         assert st == M.OK and int(off[-1]) == total
+        if mode == 1:
+            launches, scanned = t.last_scan_stats()
+            assert launches >= 2 and scanned >= 2 << 30, (launches, scanned)
         got = pinned.numpy().view(np.uint32)
         assert np.array_equal(got[:total], cat)
         assert np.all(pinned.numpy()[total:] == -1)

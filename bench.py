@@ -158,6 +158,20 @@ def dram_traffic_per_launch(workload: str, alg_bytes_per_launch: float):
     return ratio * alg_bytes_per_launch, ratio
 
 
+def selectivity_summary(offsets, n: int) -> dict:
+    """Achieved selectivity of a batch's queries (answer size / rows), from the batch's
+    CSR offsets (nq + 1 entries); the recipes only target a selectivity (Sec. 2.1: on
+    correlated dimensions the product of per-dimension shares misses it)."""
+    counts = np.diff(np.asarray(offsets, dtype=np.int64))
+    out = {"queries": int(counts.size)}
+    if counts.size == 0 or n <= 0:
+        return out
+    sel = counts / float(n)
+    out.update({"mean": float(sel.mean()), "median": float(np.median(sel)), "min": float(sel.min()),
+                "max": float(sel.max()), "empty_queries": int((counts == 0).sum())})
+    return out
+
+
 # ----------------------------------------------------------------------------- oracle timing
 
 def time_oracle(wl, budget_s: float, nthreads: int, min_queries: int = 2):
@@ -427,6 +441,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     if st not in (mdrq.OK, mdrq.E_CAPACITY):
         raise mdrq.MDRQError(st, "mdrq_query_batch")
     total_ids = int(off[-1])
+    achieved = selectivity_summary(off, wl.n)
     ids = torch.empty(max(1, total_ids), dtype=torch.int32, device="cuda")
 
     def step():
@@ -665,7 +680,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": cfg, "clocks": clocks, "e2e": e2e,
             "gpu_launches": timing["kernel_launches"], "roofline": roofline,
-            "cpu_baseline": cpu, "answer_ids_per_step": total_ids, "cold_l2": cold, "plain_graph": plain_graph,
+            "cpu_baseline": cpu, "answer_ids_per_step": total_ids, "achieved_selectivity": achieved,
+            "cold_l2": cold, "plain_graph": plain_graph,
             "batched": batched,
             "learned": learned, "serving": serving,
         }), flush=True)

@@ -45,3 +45,18 @@ def test_reference_arm_under_torchrun_prints_once():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+
+
+def test_selectivity_summary_from_offsets():
+    """The bench's achieved-selectivity summary reads answer sizes off the CSR offsets."""
+    import importlib.util
+    import numpy as np
+    spec = importlib.util.spec_from_file_location("bench_module", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    off = np.array([0, 10, 10, 40, 1040], dtype=np.uint64)  # answers of 10, 0, 30, 1000 ids
+    s = bench.selectivity_summary(off, 1000)
+    assert s["queries"] == 4 and s["empty_queries"] == 1
+    assert s["min"] == 0.0 and s["max"] == 1.0 and s["median"] == 0.02
+    assert abs(s["mean"] - 1040 / 4000) < 1e-12
+    assert bench.selectivity_summary(np.zeros(1, dtype=np.uint64), 1000) == {"queries": 0}

@@ -441,7 +441,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     if st not in (mdrq.OK, mdrq.E_CAPACITY):
         raise mdrq.MDRQError(st, "mdrq_query_batch")
     total_ids = int(off[-1])
-    achieved = selectivity_summary(off, wl.n)
+    selectivity = selectivity_summary(off, wl.n)
     ids = torch.empty(max(1, total_ids), dtype=torch.int32, device="cuda")
 
     def step():
@@ -680,7 +680,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": cfg, "clocks": clocks, "e2e": e2e,
             "gpu_launches": timing["kernel_launches"], "roofline": roofline,
-            "cpu_baseline": cpu, "answer_ids_per_step": total_ids, "achieved_selectivity": achieved,
+            "cpu_baseline": cpu, "answer_ids_per_step": total_ids, "achieved_selectivity": selectivity,
             "cold_l2": cold, "plain_graph": plain_graph,
             "batched": batched,
             "learned": learned, "serving": serving,

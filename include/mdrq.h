@@ -287,7 +287,10 @@ int mdrq_server_submit(mdrq_server *s, const mdrq_pred *preds, uint32_t npreds, 
  * its batch. Returns the query's status: MDRQ_OK; MDRQ_E_CAPACITY (its answer, of
  * *count ids, can never fit the arena, or the server stopped while it waited for
  * memory); MDRQ_E_TIMEOUT (not answered within timeout_us; still queued); MDRQ_E_INVAL
- * (unknown or released ticket). */
+ * (unknown or released ticket); the CUDA or allocation error (MDRQ_E_CUDA,
+ * MDRQ_E_NOMEM, MDRQ_E_TIMEOUT from a device wait) that stopped the server, for the
+ * queries of the failed batch and every query still queued behind it. After such a
+ * failure mdrq_server_submit returns that error. */
 int mdrq_server_wait(mdrq_server *s, uint64_t ticket, int64_t timeout_us, const uint32_t **ids, uint64_t *count,
                      double *latency_us);
 

@@ -174,11 +174,23 @@ void scheduler_main(mdrq_server *S)
         {
             std::unique_lock<std::mutex> lock(S->mu);
             S->cv_sched.wait(lock, [&] {
-                return (S->stopping && S->pending.empty()) ||
-                       (!S->pending.empty() && (!S->busy[0] || !S->busy[1]) && S->fatal == MDRQ_OK);
+                return (S->stopping && S->pending.empty()) || S->fatal != MDRQ_OK ||
+                       (!S->pending.empty() && (!S->busy[0] || !S->busy[1]));
             });
-            if (S->pending.empty() || S->fatal != MDRQ_OK)
-                return;  // stopping, nothing left (or the GPU failed)
+            if (S->fatal != MDRQ_OK) {
+                // the GPU failed (here or in the completer): no further batch runs, and
+                // the queries still waiting end with the failure's status instead of
+                // leaving their waiters blocked; submit refuses new queries from now on
+                const Clock::time_point now = Clock::now();
+                while (!S->pending.empty()) {
+                    finish(S, S->pending.front(), S->fatal, now);
+                    S->pending.pop_front();
+                }
+                S->cv_done.notify_all();
+                return;
+            }
+            if (S->pending.empty())
+                return;  // stopping, nothing left
             k = S->busy[0] ? 1 : 0;
             batch.clear();
             while (!S->pending.empty() && batch.size() < S->max_batch) {

@@ -36,6 +36,17 @@ MUTANTS = {
     "partitions_concatenated_backwards": (
         "for (int t = 0; t < nthreads; ++t) {\n                if (w[t].part.len)",
         "for (int t = nthreads - 1; t >= 0; --t) {\n                if (w[t].part.len)"),
+    "float_read_as_int": ("return (double)((const float *)q->cols[j])[i];",
+                          "return (double)((const int32_t *)q->cols[j])[i];"),
+    "type_dispatch_inverted": ("if (q->types[j] == ORACLE_F32)\n        return",
+                               "if (q->types[j] != ORACLE_F32)\n        return"),
+    "skips_last_row": ("for (uint64_t i = begin; i < end; ++i)",
+                       "for (uint64_t i = begin; i + 1 < end; ++i)"),
+    "partitions_overwrite": ("                at += w[t].part.len;\n", ""),
+    "last_partition_short": ("w[t].end = n * (uint64_t)(t + 1) / (uint64_t)nthreads;",
+                             "w[t].end = n * (uint64_t)(t + 1) / (uint64_t)nthreads"
+                             " - (uint64_t)(t + 1 == nthreads && n > 1);"),
+    "first_predicate_lower_bound_for_all": ("q->lo[p] <= x", "q->lo[0] <= x"),
 }
 
 

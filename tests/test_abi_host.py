@@ -88,3 +88,44 @@ def test_bound_encoding():
         mdrq.encode_query([(2, 0, 1)], [mdrq.F32, mdrq.F32])
     with pytest.raises(ValueError):
         mdrq.encode_query([(0, 0, 2**31)], [mdrq.I32])
+
+
+def test_static_entry_checks_arguments_before_cuda(L):
+    """mdrq_query_static rejects every bad argument, and answers a provably empty query
+    (an empty interval, or an empty table) with count 0, before its first CUDA call.
+    The column addresses are fake, aligned and never dereferenced."""
+    def call(cols, types, d, n, preds, count=True):
+        c = (ctypes.c_void_p * max(1, len(cols)))(*cols)
+        t = (ctypes.c_int32 * max(1, len(types)))(*types)
+        p = mdrq.encode_query(preds, types) if preds else (mdrq.Pred * 1)()
+        cnt = ctypes.c_uint64(12345)
+        st = L.mdrq_query_static(c, t, d, n, p, len(preds), None, 0,
+                                 ctypes.byref(cnt) if count else None, None)
+        return st, cnt.value
+
+    cols, types = [0x10000, 0x20000], [mdrq.F32, mdrq.I32]
+    nan = float("nan")
+    assert call(cols, types, 2, mdrq.STATIC_MAX_ROWS + 1, [(0, 0.0, 1.0)])[0] == mdrq.E_INVAL
+    assert call([0x10004, 0x20000], types, 2, 10, [(0, 0.0, 1.0)])[0] == mdrq.E_INVAL  # misaligned
+    assert call([0, 0x20000], types, 2, 10, [(0, 0.0, 1.0)])[0] == mdrq.E_INVAL        # null column
+    assert call(cols, [mdrq.F32, 7], 2, 10, [(0, 0.0, 1.0)])[0] == mdrq.E_INVAL        # unknown type
+    assert call(cols, types, 0, 10, [])[0] == mdrq.E_INVAL                             # d = 0
+    assert call(cols, types, 2, 10, [(0, nan, 1.0)])[0] == mdrq.E_INVAL                # NaN bound
+    assert call(cols, types, 2, 10, [(0, 0.0, 1.0)], count=False)[0] == mdrq.E_INVAL   # count NULL
+    bad_dim = mdrq.encode_query([(0, 0.0, 1.0)], types)
+    bad_dim[0].dim = 2
+    cnt = ctypes.c_uint64(0)
+    assert L.mdrq_query_static((ctypes.c_void_p * 2)(*cols), (ctypes.c_int32 * 2)(*types), 2, 10, bad_dim, 1,
+                               None, 0, ctypes.byref(cnt), None) == mdrq.E_INVAL
+    bad_dim[0].dim = 0
+    bad_dim[0].reserved = 1
+    assert L.mdrq_query_static((ctypes.c_void_p * 2)(*cols), (ctypes.c_int32 * 2)(*types), 2, 10, bad_dim, 1,
+                               None, 0, ctypes.byref(cnt), None) == mdrq.E_INVAL
+    # more than 128 distinct constrained dimensions
+    many = [0x10000 * (j + 1) for j in range(130)]
+    ftypes = [mdrq.F32] * 130
+    assert call(many, ftypes, 130, 10, [(j, 0.0, 1.0) for j in range(129)])[0] == mdrq.E_INVAL
+    # provably empty: answered on the host with count 0
+    assert call(cols, types, 2, 10, [(0, 1.0, 0.0)]) == (mdrq.OK, 0)
+    assert call(cols, types, 2, 10, [(1, 5, 9), (1, 10, 20)]) == (mdrq.OK, 0)  # repeated dim, disjoint
+    assert call(cols, types, 2, 0, [(0, 0.0, 1.0)]) == (mdrq.OK, 0)            # empty table

@@ -129,3 +129,47 @@ def test_static_entry_checks_arguments_before_cuda(L):
     assert call(cols, types, 2, 10, [(0, 1.0, 0.0)]) == (mdrq.OK, 0)
     assert call(cols, types, 2, 10, [(1, 5, 9), (1, 10, 20)]) == (mdrq.OK, 0)  # repeated dim, disjoint
     assert call(cols, types, 2, 0, [(0, 0.0, 1.0)]) == (mdrq.OK, 0)            # empty table
+
+
+def test_every_handle_call_rejects_null(L):
+    """Each call taking a table, server or prepared-batch handle returns MDRQ_E_INVAL for
+    a NULL handle (stop and free are no-ops), before any CUDA call."""
+    u64, u32, dbl, i32 = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double, ctypes.c_int
+    a, b, c = u64(0), u64(0), u64(0)
+    s, d1, d2 = u32(0), dbl(0), dbl(0)
+    p = (mdrq.Pred * 1)()
+    q = (mdrq.QDesc * 1)()
+    h = ctypes.c_void_p()
+    tick = (u64 * 1)(1)
+    st = (i32 * 1)()
+    tune = mdrq.Tuning()
+    ms = dbl(0)
+    E = mdrq.E_INVAL
+    assert L.mdrq_set_batch_mode(None, mdrq.BATCH_PLAIN) == E
+    assert L.mdrq_learn(None, (u32 * 1)(0), 1, mdrq.MODEL_PLA, None) == E
+    assert L.mdrq_learn_info(None, ctypes.byref(a), ctypes.byref(s), ctypes.byref(d1)) == E
+    assert L.mdrq_learn_window_rows(None, ctypes.byref(a), ctypes.byref(b)) == E
+    assert L.mdrq_server_start(None, 1 << 20, 16, ctypes.byref(h)) == E and h.value is None
+    assert L.mdrq_server_submit(None, p, 1, ctypes.byref(a)) == E
+    assert L.mdrq_server_submit_batch(None, q, 1, tick) == E
+    assert L.mdrq_server_wait(None, 1, 0, None, ctypes.byref(a), ctypes.byref(d1)) == E
+    assert L.mdrq_server_wait_many(None, tick, 1, 0, st, None, None, 0) == E
+    assert L.mdrq_server_release(None, 1) == E
+    assert L.mdrq_server_stats(None, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d1),
+                               ctypes.byref(d2)) == E
+    assert L.mdrq_server_stop(None) == mdrq.OK
+    off = (u64 * 2)()
+    assert L.mdrq_prepare_batch(None, q, 1, None, 0, off, None, ctypes.byref(h)) == E and h.value is None
+    assert L.mdrq_prepared_launch(None, None) == E
+    assert L.mdrq_prepared_wait(None, off, None) == E
+    assert L.mdrq_prepared_kernels(None, ctypes.byref(a)) == E
+    L.mdrq_prepared_free(None)
+    assert L.mdrq_set_shared_config(None, 0, 0) == E
+    assert L.mdrq_set_shared_bits_budget(None, 0) == E
+    assert L.mdrq_autotune(None, q, 1, None, ctypes.byref(tune)) == E
+    assert L.mdrq_set_zone_maps(None, mdrq.ZONES_AUTO) == E
+    assert L.mdrq_zone_map_info(None, 0, None, None) == E
+    assert L.mdrq_zone_scan_info(None, ctypes.byref(a), ctypes.byref(b)) == E
+    assert L.mdrq_scan_timing(None, 1) == E
+    assert L.mdrq_scan_timing_read(None, ctypes.byref(ms), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), 0) == E
+    assert L.mdrq_inject_fault(None, mdrq.FAULT_NOMEM, 0) == E

@@ -90,3 +90,51 @@ def test_generators_are_deterministic():
     b = W.mixed_clustered(n=10_000, nq=8)
     assert all(np.array_equal(x, y) for x, y in zip(a.columns, b.columns))
     assert a.queries == b.queries
+
+
+def _deinterleave(key: np.ndarray, j: int) -> np.ndarray:
+    """Cell of dimension j read back out of a Morton key: bit 4b + j of the key is bit
+    b of the cell (the inverse of the interleave, computed bit by bit per row)."""
+    out = np.zeros(key.shape[0], dtype=np.uint32)
+    for b in range(8):
+        out |= ((key >> np.uint32(4 * b + j)) & np.uint32(1)) << np.uint32(b)
+    return out
+
+
+def test_zorder_key_interleaves_cells():
+    rng = np.random.default_rng(3)
+    cols = [rng.random(5000, dtype=np.float32) for _ in range(4)]
+    cols[0][:3] = [0.0, np.float32(W.ONE_BELOW), 0.5]
+    key = W.zorder_key(cols)
+    for j in range(4):
+        want = np.minimum(np.floor(cols[j].astype(np.float64) * 256.0), 255).astype(np.uint32)
+        assert np.array_equal(_deinterleave(key, j), want)
+    assert list(_deinterleave(key[:3], 0)) == [0, 255, 128]
+    # a single row: dimension 0 in the lowest bit of each nibble
+    one = W.zorder_key([np.array([1.0 / 256], np.float32), np.zeros(1, np.float32),
+                        np.zeros(1, np.float32), np.array([3.0 / 256], np.float32)])
+    assert int(one[0]) == (1 << 0) | (1 << 3) | (1 << 7)
+
+
+def test_zorder_table_is_sorted_and_normalised():
+    wl = W.zorder_learned(n=60_000, nq=16)
+    assert wl.d == 4 and all(c.dtype == np.float32 for c in wl.columns)
+    key = W.zorder_key(wl.columns)
+    assert np.all(key[1:] >= key[:-1])  # rows in key order
+    for c in wl.columns:
+        assert c.min() >= 0.0 and c.max() <= W.ONE_BELOW
+    for j in (1, 3):  # lognormal, normalised by its own min and max: starts at exactly 0
+        assert wl.columns[j].min() == 0.0 and np.median(wl.columns[j]) < 0.1
+    for j in (0, 2):
+        assert abs(float(wl.columns[j].mean()) - 0.5) < 0.01
+    for q in wl.queries:
+        assert sorted(p[0] for p in q) == [0, 1, 2, 3]
+
+
+def test_poisson_arrivals_rate_and_determinism():
+    a = W.poisson_arrivals(1000.0, 20_000, seed=5)
+    assert np.all(np.diff(a) > 0)
+    gaps = np.diff(np.concatenate([[0.0], a]))
+    assert abs(gaps.mean() * 1000.0 - 1.0) < 0.03  # mean gap 1 / rate (sd of the mean 0.7%)
+    assert abs(gaps.std() / gaps.mean() - 1.0) < 0.05  # exponential: sd equals the mean
+    assert np.array_equal(a, W.poisson_arrivals(1000.0, 20_000, seed=5))

@@ -619,7 +619,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
                "h2d_bytes_per_step": 16 * npreds + 16 * nq,
                "d2h_bytes_per_step": 8 * (nq + 1) + 4 * total_ids,
                "path": "mdrq_query_batch with host query descriptors and a pinned host answer "
-                       "buffer (each launch's ids copied while the next runs); host wall clock"}
+                       "buffer (each launch's ids copied while the next runs); host wall clock",
+               "bytes": "h2d: the host descriptors passed to the call (16 B per predicate and per "
+                        "query; the library stages them as one copy of 16 B per query and 32 B per "
+                        "kept predicate); d2h: the offsets and every id"}
 
     # ---- roofline of the scan kernel (algorithmic bytes / event-timed duration)
     peaks = measured_peaks()

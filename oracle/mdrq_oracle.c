@@ -12,11 +12,18 @@
  * qualifying objects' identifiers, where the identifier of an object is its array
  * index i (Sec. 2.2.4). This file returns that set as an ascending uint32 list.
  *
- * How: the row-at-a-time loop of the sequential scan (Sec. 2.2.4, Listing 1): an
- * outer loop over objects, an inner loop over the constrained dimensions that stops
- * at the first dimension the object fails, and an append of i when none failed.
- * The data is held column-wise (one array per dimension, Sec. 3.2), which changes
- * only where a value is read from, not which objects qualify.
+ * How: two plain evaluations of that rule, which must agree.
+ *  - oracle_mdrq, object at a time: every object in index order is tested against
+ *    the rule of Sec. 2.1 ("for every constrained dimension" is decided false at the
+ *    first dimension the object fails) and its index is appended when it qualifies.
+ *    This is the sequential scan of Sec. 2.2.4.
+ *  - oracle_mdrq_columnwise, dimension at a time: each constrained dimension is
+ *    evaluated over its whole column into one flag per object, the flags of all
+ *    constrained dimensions are ANDed, and the indices whose flag survives are
+ *    listed in index order. This is the vertically partitioned evaluation of
+ *    Sec. 3.2 (one array per dimension, per-dimension results combined by AND).
+ * The data is held column-wise (one array per dimension, Sec. 3.2) for both; the
+ * layout changes only where a value is read from, not which objects qualify.
  *
  * Comparisons are made in double precision: every float32 and every int32 value
  * is exactly representable as a double, so `lo <= x && x <= hi` in double decides
@@ -82,25 +89,71 @@ static void push_back(id_vector_t *v, uint32_t id)
     v->ids[v->len++] = id;
 }
 
-/* Sec. 2.2.4 / Listing 1: scan objects [begin, end) and append every match. */
-static void scan_range(const oracle_query_t *q, uint64_t begin, uint64_t end, id_vector_t *out)
+/* Sec. 2.1: object i qualifies iff lb_j <= t_i[j] <= ub_j holds for every
+ * constrained dimension j; "for every" is false as soon as one predicate fails. */
+static int qualifies(const oracle_query_t *q, uint64_t i)
 {
-    for (uint64_t i = begin; i < end; ++i) {
-        int match = 1;
-        for (uint32_t p = 0; p < q->k; ++p) {
-            double x = value_at(q, q->dims[p], i);
-            if (!(q->lo[p] <= x && x <= q->hi[p])) {
-                match = 0;
-                break;
-            }
-        }
-        if (match)
-            push_back(out, (uint32_t)i);
+    for (uint32_t p = 0; p < q->k; ++p) {
+        double x = value_at(q, q->dims[p], i);
+        if (!(q->lo[p] <= x && x <= q->hi[p]))
+            return 0;
     }
+    return 1;
 }
+
+/* Object at a time (Sec. 2.2.4): objects [begin, end) in index order, each
+ * appended when it qualifies. */
+static void scan_objects(const oracle_query_t *q, uint64_t begin, uint64_t end, id_vector_t *out)
+{
+    for (uint64_t i = begin; i < end; ++i)
+        if (qualifies(q, i))
+            push_back(out, (uint32_t)i);
+}
+
+/* 1 iff lb <= v <= ub (closed interval, Sec. 2.1), without a branch */
+static unsigned char in_interval(double lb, double v, double ub)
+{
+    return (unsigned char)((lb <= v) & (v <= ub));
+}
+
+/* Dimension at a time (Sec. 3.2): one flag per object of [begin, end), ANDed with
+ * each constrained dimension's result over its column; the objects whose flag
+ * survives, in index order. Its flag loops are independent per object, so the
+ * compiler may vectorise them (asked for here only; the object-at-a-time scan above
+ * is compiled as the rest of the file). */
+__attribute__((optimize("O3"))) static void scan_dimensions(const oracle_query_t *q, uint64_t begin, uint64_t end, id_vector_t *out)
+{
+    const uint64_t m = end - begin;
+    unsigned char *flag = (unsigned char *)malloc(m > 0 ? m : 1);
+    if (!flag) {
+        out->failed = 1;
+        return;
+    }
+    memset(flag, 1, m);
+    for (uint32_t c = 0; c < q->k; ++c) {
+        const uint32_t dim = q->dims[c];
+        const double lb = q->lo[c], ub = q->hi[c];
+        if (q->types[dim] == ORACLE_F32) {
+            const float *fcol = (const float *)q->cols[dim] + begin;
+            for (uint64_t r = 0; r < m; ++r)
+                flag[r] &= in_interval(lb, (double)fcol[r], ub);
+        } else {
+            const int32_t *icol = (const int32_t *)q->cols[dim] + begin;
+            for (uint64_t r = 0; r < m; ++r)
+                flag[r] &= in_interval(lb, (double)icol[r], ub);
+        }
+    }
+    for (uint64_t r = 0; r < m; ++r)
+        if (flag[r])
+            push_back(out, (uint32_t)(begin + r));
+    free(flag);
+}
+
+typedef void (*scan_fn)(const oracle_query_t *, uint64_t, uint64_t, id_vector_t *);
 
 typedef struct {
     const oracle_query_t *q;
+    scan_fn scan;
     uint64_t begin, end;
     id_vector_t part;
 } worker_t;
@@ -108,21 +161,21 @@ typedef struct {
 static void *worker_main(void *arg)
 {
     worker_t *w = (worker_t *)arg;
-    scan_range(w->q, w->begin, w->end, &w->part);
+    w->scan(w->q, w->begin, w->end, &w->part);
     return NULL;
 }
 
 /*
- * Answer one MDRQ. On success returns the number of qualifying objects and stores a
- * malloc'd ascending id list in *ids_out (NULL when the answer is empty); release it
- * with oracle_free. nthreads <= 1 runs Listing 1 on the calling thread; otherwise
- * the rows are split into nthreads contiguous partitions (Sec. 3.1).
- * Returns ORACLE_E_INVAL for a bad argument (n >= 2^32, a dimension >= d, a type
- * other than the two above) and ORACLE_E_NOMEM if memory runs out.
+ * Answer one MDRQ with the given evaluation. On success returns the number of
+ * qualifying objects and stores a malloc'd ascending id list in *ids_out (NULL when
+ * the answer is empty); release it with oracle_free. nthreads <= 1 scans on the
+ * calling thread; otherwise the rows are split into nthreads contiguous partitions
+ * (Sec. 3.1). Returns ORACLE_E_INVAL for a bad argument (n >= 2^32, a dimension >= d,
+ * a type other than the two above) and ORACLE_E_NOMEM if memory runs out.
  */
-int64_t oracle_mdrq(const void *const *cols, const int32_t *types, uint32_t d, uint64_t n,
-                    const uint32_t *dims, const double *lo, const double *hi, uint32_t k,
-                    int nthreads, uint32_t **ids_out)
+static int64_t answer(const void *const *cols, const int32_t *types, uint32_t d, uint64_t n,
+                      const uint32_t *dims, const double *lo, const double *hi, uint32_t k,
+                      int nthreads, uint32_t **ids_out, scan_fn scan)
 {
     *ids_out = NULL;
     if (n > 0xFFFFFFFFull || (k > 0 && (!dims || !lo || !hi)))
@@ -149,6 +202,7 @@ int64_t oracle_mdrq(const void *const *cols, const int32_t *types, uint32_t d, u
     }
     for (int t = 0; t < nthreads; ++t) {
         w[t].q = &q;
+        w[t].scan = scan;
         w[t].begin = n * (uint64_t)t / (uint64_t)nthreads;
         w[t].end = n * (uint64_t)(t + 1) / (uint64_t)nthreads;
     }
@@ -195,6 +249,23 @@ int64_t oracle_mdrq(const void *const *cols, const int32_t *types, uint32_t d, u
         return ORACLE_E_NOMEM;
     *ids_out = ids;
     return (int64_t)total;
+}
+
+/* Object at a time (Sec. 2.1 rule per object, Sec. 2.2.4 scan). Arguments as above. */
+int64_t oracle_mdrq(const void *const *cols, const int32_t *types, uint32_t d, uint64_t n,
+                    const uint32_t *dims, const double *lo, const double *hi, uint32_t k,
+                    int nthreads, uint32_t **ids_out)
+{
+    return answer(cols, types, d, n, dims, lo, hi, k, nthreads, ids_out, scan_objects);
+}
+
+/* Dimension at a time (Sec. 3.2 flags ANDed over the constrained columns). Same
+ * arguments and result as oracle_mdrq. */
+int64_t oracle_mdrq_columnwise(const void *const *cols, const int32_t *types, uint32_t d, uint64_t n,
+                               const uint32_t *dims, const double *lo, const double *hi, uint32_t k,
+                               int nthreads, uint32_t **ids_out)
+{
+    return answer(cols, types, d, n, dims, lo, hi, k, nthreads, ids_out, scan_dimensions);
 }
 
 void oracle_free(uint32_t *ids) { free(ids); }

@@ -9,7 +9,14 @@ import pins
 
 @pytest.mark.parametrize("pin", pins.ALL_PINS, ids=lambda p: p.__name__)
 def test_oracle_pin(pin):
+    """Object at a time (Sec. 2.2.4)."""
     pin(oracle.mdrq)
+
+
+@pytest.mark.parametrize("pin", pins.ALL_PINS, ids=lambda p: p.__name__)
+def test_oracle_columnwise_pin(pin):
+    """Dimension at a time (Sec. 3.2): held to the same pins on its own."""
+    pin(oracle.mdrq_columnwise)
 
 
 def test_closed_form_matches_paper_numbers():

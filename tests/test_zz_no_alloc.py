@@ -4,8 +4,9 @@ Some callers cannot allocate device memory at query time (a serving loop whose d
 memory belongs to another allocator's budget, a latency-critical path where
 cudaMalloc's implicit synchronisation would stall other streams). For them the library
 keeps the scan's scratch in a fixed device array. These tests call that entry point
-through the C ABI and check it against the table-based entry point (mdrq_query), id
-for id, on two calls in a row, since every call reuses the same scratch array.
+through the C ABI and check it id for id against the CPU oracle and against the
+table-based entry point (mdrq_query), on two calls in a row, since every call reuses
+the same scratch array.
 
 This file is named to be collected last, so that a run stopping at the first failure
 has already run every other test; it also passes on its own in a fresh process.
@@ -13,6 +14,7 @@ has already run every other test; it also passes on its own in a fresh process.
 import numpy as np
 import pytest
 
+import oracle
 from paper_1801_03644_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -37,6 +39,7 @@ def test_static_matches_table_entry_point_on_consecutive_calls(M):
     with M.Table(cols) as t:
         for q in wl.queries:
             want = M.as_uint32_numpy(t.query(q))
+            assert np.array_equal(want, oracle.mdrq(wl.columns, q, nthreads=8))
             for _ in range(2):  # the second call finds the first call's scratch contents
                 st, cnt = M.query_static(cols, q, out)
                 torch.cuda.synchronize()
@@ -56,6 +59,7 @@ def test_static_small_and_ragged_sizes(M):
         with M.Table(cols) as t:
             for q in ([(0, 0.2, 0.7)], [(0, 0.1, 0.9), (1, -3, 4)], [], [(1, 5, 2)]):
                 want = M.as_uint32_numpy(t.query(q))
+                assert np.array_equal(want, oracle.mdrq([x, y], q))
                 for _ in range(2):
                     st, cnt = M.query_static(cols, q, out)
                     assert st == M.OK and cnt == want.size
@@ -97,6 +101,7 @@ def test_static_reports_capacity(M):
     cols = [torch.from_numpy(c).cuda() for c in wl.columns]
     with M.Table(cols) as t:
         want = M.as_uint32_numpy(t.query(wl.queries[0]))
+    assert np.array_equal(want, oracle.mdrq(wl.columns, wl.queries[0]))
     cap = want.size // 2
     out = torch.full((cap + 8,), -1, dtype=torch.int32, device="cuda")
     for _ in range(2):

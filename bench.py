@@ -145,16 +145,18 @@ def scan_kernel_digest() -> str:
 
 
 def dram_traffic_per_launch(workload: str, alg_bytes_per_launch: float):
-    """DRAM bytes per scan launch from the committed ncu summary of this workload, scaled
-    to this run's average launch by the captured launches' traffic / algorithmic ratio;
-    None when the summary is missing or the kernel source changed since it was taken."""
+    """DRAM bytes per scan launch from the committed ncu summary of a smaller case of this
+    workload (same recipe, fewer rows and queries), scaled to this run's launch by the
+    captured launch's DRAM bytes / early-break algorithmic bytes (``early_break_bytes``);
+    None when the summary is missing, counts other bytes, or the kernel source changed
+    since it was taken."""
     p = os.path.join(ROOT, "profiles", "mdrq_scan_kernel_%s.traffic.json" % workload)
     if not os.path.exists(p):
         return None, None
     d = json.load(open(p))
-    if d.get("scan_kernel_digest") != scan_kernel_digest():
+    if d.get("scan_kernel_digest") != scan_kernel_digest() or "early_break_bytes" not in d:
         return None, None
-    ratio = float(d["dram_bytes"]) / float(d["algorithmic_bytes"])
+    ratio = float(d["dram_bytes"]) / float(d["early_break_bytes"])
     return ratio * alg_bytes_per_launch, ratio
 
 
@@ -170,6 +172,86 @@ def selectivity_summary(offsets, n: int) -> dict:
     out.update({"mean": float(sel.mean()), "median": float(np.median(sel)), "min": float(sel.min()),
                 "max": float(sel.max()), "empty_queries": int((counts == 0).sum())})
     return out
+
+
+# ----------------------------------------------------------------------------- answers
+
+def same_answers(off_a, ids_a, off_b, ids_b) -> bool:
+    """Identical CSR answers: the same per-query offsets and the same ids (device
+    tensors compared in full)."""
+    import torch
+    off_a, off_b = np.asarray(off_a), np.asarray(off_b)
+    if not np.array_equal(off_a, off_b):
+        return False
+    total = int(off_a[-1])
+    return bool(torch.equal(ids_a[:total], ids_b[:total]))
+
+
+def verify_with_oracle(columns, queries, ids, off, which, nthreads: int) -> dict:
+    """Count and ids of the queries ``which`` against the CPU oracle (evaluated one
+    dimension at a time, Sec. 3.2; pinned on its own in the test suite). ``ids`` is
+    the batch's device answer (CSR by ``off``)."""
+    import oracle
+    oracle.build()
+    off = np.asarray(off, dtype=np.int64)
+    t0 = time.perf_counter()
+    bad = []
+    for q in which:
+        a, b = int(off[q]), int(off[q + 1])
+        want = oracle.mdrq_columnwise(columns, queries[q], nthreads=nthreads)
+        have = ids[a:b].cpu().numpy().view(np.uint32) if b > a else np.zeros(0, np.uint32)
+        if have.size != want.size or not np.array_equal(have, want):
+            bad.append(int(q))
+    return {"queries": len(which), "of": len(queries), "mismatches": len(bad), "first_mismatches": bad[:8],
+            "oracle": "CPU oracle, dimension at a time, %d threads" % nthreads,
+            "seconds": time.perf_counter() - t0}
+
+
+def early_break_bytes(table, cols_dev, queries, n: int) -> float:
+    """Algorithmic bytes of the plain scan of ``queries`` with its early break (Sec.
+    2.2.4) at DRAM-sector granularity: for each query, in the order the scan evaluates
+    its predicates (``mdrq_explain_query``), 32 B for every 32-byte sector (8 rows) of
+    the column that still holds a row satisfying all earlier predicates, plus 4 B per
+    answer id. Counted on the GPU with plain tensor operations, outside any timed
+    region; it does not depend on the kernel (two lanes of 4 rows share a sector, and
+    a lane whose rows have all failed issues no load)."""
+    import torch
+    pad = (-n) % 8
+    total = 0.0
+    for q in queries:
+        empty, plan = table.explain(q)
+        if empty:
+            continue
+        alive = None
+        for (j, lo, hi) in plan:
+            x = cols_dev[j]
+            if alive is None:
+                sectors = (n + 7) // 8
+            else:
+                a = torch.cat([alive, alive.new_zeros(pad)]) if pad else alive
+                sectors = int(a.view(-1, 8).any(dim=1).sum())
+            total += 32.0 * sectors
+            lo_t = torch.tensor(lo, dtype=x.dtype, device=x.device)
+            hi_t = torch.tensor(hi, dtype=x.dtype, device=x.device)
+            m = (x >= lo_t) & (x <= hi_t)
+            alive = m if alive is None else alive & m
+        total += 4.0 * (n if alive is None else int(alive.sum()))
+    return total
+
+
+def d2h_gbs(torch, nbytes: int = 1 << 30) -> float:
+    """Device-to-pinned-host copy rate of one large copy (CUDA events), for context."""
+    src = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    dst = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    dst.copy_(src, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        dst.copy_(src, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    return 3 * nbytes / (e0.elapsed_time(e1) / 1e3) / 1e9
 
 
 # ----------------------------------------------------------------------------- oracle timing
@@ -250,10 +332,13 @@ def timed_steps(torch, stream, step, steps, barrier):
     return e0.elapsed_time(e1), last
 
 
-def learned_leg(args, table, enc, step, nq, total_ids, world, barrier, stream):
-    """Learned range narrower (PLA and MLP) and zone-map tile pruning on a Z-sorted table:
-    queries/s and speedup over the plain scan of the same batch with zone maps off
-    (every tile read), model error and window coverage."""
+def learned_leg(args, table, enc, step, nq, total_ids, world, barrier, stream, ids, ids_ref, off_ref):
+    """Learned range narrower (PLA, the MLP-rooted two-stage model, and no model: the
+    whole key column searched) and zone-map tile pruning on a Z-sorted table: queries/s
+    and speedup over the plain scan of the same batch with zone maps off (every tile
+    read), model error, window coverage and the keys the window searches read. ``step`` answers the batch into
+    ``ids``; every leg's answer must equal the reference answer (``off_ref``,
+    ``ids_ref``) id for id."""
     import torch
     from paper_1801_03644_gb300 import mdrq, shards
 
@@ -262,37 +347,41 @@ def learned_leg(args, table, enc, step, nq, total_ids, world, barrier, stream):
         table.set_zone_maps(zones)
         for _ in range(args.warmup):
             step()
+        ids.fill_(-1)
         ms, off = timed_steps(torch, stream, step, args.steps, barrier)
         ms = shards.max_over_ranks(ms)
-        return world * nq * args.steps / (ms / 1e3), ms / args.steps, off
+        return world * nq * args.steps / (ms / 1e3), ms / args.steps, same_answers(off_ref, ids_ref, off, ids)
 
-    base, base_ms, off_b = timed(mdrq.BATCH_PLAIN, mdrq.ZONES_OFF)
-    zval, zms, off_z = timed(mdrq.BATCH_PLAIN, mdrq.ZONES_AUTO)
+    base, base_ms, same_b = timed(mdrq.BATCH_PLAIN, mdrq.ZONES_OFF)
+    zval, zms, same_z = timed(mdrq.BATCH_PLAIN, mdrq.ZONES_AUTO)
     zrows, ztiles = table.zone_scan_info()
     out = {"plain_no_zone_maps": {"value": base, "unit": UNIT, "ms_per_step": base_ms,
-                                  "answers_identical_to_plain": bool(int(off_b[-1]) == total_ids)},
+                                  "answers_identical_to_plain": same_b},
            "zone_pruned_plain": {"value": zval, "unit": UNIT, "ms_per_step": zms,
                                  "speedup_vs_plain": zval / base, "rows_visited_per_query": zrows / nq,
-                                 "tiles_visited": ztiles,
-                                 "answers_identical_to_plain": bool(int(off_z[-1]) == total_ids)}}
-    for name, model in (("pla", mdrq.MODEL_PLA), ("mlp", mdrq.MODEL_MLP)):
+                                 "tiles_visited": ztiles, "answers_identical_to_plain": same_z}}
+    for name, model in (("pla", mdrq.MODEL_PLA), ("mlp", mdrq.MODEL_MLP), ("none", mdrq.MODEL_NONE)):
         info = table.learn([0, 1, 2, 3], model)
-        lvalue, lms, off_l = timed(mdrq.BATCH_LEARNED, mdrq.ZONES_AUTO)
+        lvalue, lms, same_l = timed(mdrq.BATCH_LEARNED, mdrq.ZONES_AUTO)
         rows, widen = table.learn_window_rows()
-        # bytes as the learned narrower's roofline counts them: 16 per window row (the
-        # four key columns) plus the ids
+        ranges, probes = table.learn_search_info()
+        # dense-equivalent bytes: 16 per window row (the four key columns) plus the ids;
+        # the scan's early break reads fewer, so this is not a DRAM figure
         lbytes = 16.0 * rows + 4.0 * total_ids
         out[name] = {"value": lvalue, "unit": UNIT, "ms_per_step": lms,
-                     "window_gbs": lbytes / (lms / 1e3) / 1e9,
-                     "window_frac": lbytes / (lms / 1e3) / 1e9 / measured_peaks()["hbm_gbs"],
+                     "window_effective_gbs": lbytes / (lms / 1e3) / 1e9,
+                     "window_effective_frac": lbytes / (lms / 1e3) / 1e9 / measured_peaks()["hbm_gbs"],
+                     "effective_rule": "dense equivalent, not bytes moved: 16 B per window row plus 4 B per id",
                      "speedup_vs_plain": lvalue / base, "speedup_vs_zone_pruned": lvalue / zval,
                      "max_error_rows": info["max_error"],
                      "segments": info["segments"], "train_ms": info["train_ms"],
                      "window_rows_per_query": rows / nq, "window_widenings": widen,
-                     "answers_identical_to_plain": bool(int(off_l[-1]) == total_ids)}
+                     "key_ranges": ranges, "search_keys_read_per_range": probes / max(1, ranges),
+                     "answers_identical_to_plain": same_l}
         if name == "pla":
-            v0, ms0, _ = timed(mdrq.BATCH_LEARNED, mdrq.ZONES_OFF)
-            out[name]["without_zone_maps"] = {"value": v0, "ms_per_step": ms0}
+            v0, ms0, same0 = timed(mdrq.BATCH_LEARNED, mdrq.ZONES_OFF)
+            out[name]["without_zone_maps"] = {"value": v0, "ms_per_step": ms0,
+                                              "answers_identical_to_plain": same0}
     table.set_batch_mode(mdrq.BATCH_PLAIN)
     table.set_zone_maps(mdrq.ZONES_AUTO)
     return out
@@ -300,9 +389,10 @@ def learned_leg(args, table, enc, step, nq, total_ids, world, barrier, stream):
 
 def learned_workload_leg(args, world, barrier):
     """The learned narrower on the 2e8 x 4 Z-sorted table with 4096 queries, against
-    the plain scan of the same batch."""
+    the plain scan of the same batch; a seeded sample of the answers against the CPU
+    oracle (the test suite compares all 4096)."""
     import torch
-    from paper_1801_03644_gb300 import mdrq, shards
+    from paper_1801_03644_gb300 import mdrq
     wl = make_workload("zorder_learned", args.learned_rows)
     stream = torch.cuda.current_stream()
     table = mdrq.Table(wl.columns)
@@ -319,10 +409,115 @@ def learned_workload_leg(args, world, barrier):
             raise mdrq.MDRQError(st, "mdrq_query_batch")
         return o
 
+    off_ref = step()
+    torch.cuda.synchronize()
+    ids_ref = ids[:total].clone()
     nq = len(wl.queries)
     res = {"workload": wl.name, "recipe": wl.recipe, "unit": UNIT, "answer_ids_per_step": total}
-    res.update(learned_leg(args, table, enc, step, nq, total, world, barrier, stream))
+    res.update(learned_leg(args, table, enc, step, nq, total, world, barrier, stream, ids, ids_ref, off_ref))
     table.close()
+    del ids
+    if not args.no_verify:
+        pick = np.sort(np.random.default_rng(4).choice(nq, size=min(args.verify_sample, nq), replace=False))
+        res["verified"] = verify_with_oracle(wl.columns, wl.queries, ids_ref, off_ref, pick.tolist(),
+                                             os.cpu_count() or 1)
+        res["verified"]["sample"] = "seeded sample of the batch; the test suite compares every query"
+    del ids_ref
+    torch.cuda.empty_cache()
+    return res
+
+
+def small_table_leg(args, world, barrier):
+    """The 1,000,000 x 3 uniform table (12 MB of columns, 100 queries of about 1%
+    selectivity), kernel time only (the scan's own CUDA events, bracketing each launch
+    on its stream):
+
+    * warm: the batch of 100 queries in one persistent launch, repeated; the table stays
+      in the 126 MB L2 between launches (the hot-cache convention of Sec. 7.1.2), so
+      this measures the scan out of L2, not HBM;
+    * cold: each query in a launch of its own, after a 512 MB read-and-write of a
+      scratch buffer that evicts the table from L2 (outside the events), so that the
+      launch reads its columns from HBM.
+
+    Byte rates use the early-break algorithmic bytes (``early_break_bytes``) and the
+    dense bytes (every row of every constrained column); fractions are of the measured
+    HBM copy peak and of the nominal 7.9 TB/s."""
+    import torch
+    from paper_1801_03644_gb300 import mdrq, shards
+    wl = W.uniform_small()
+    cols = [torch.from_numpy(c).cuda() for c in wl.columns]
+    t = mdrq.Table(cols)
+    t.set_batch_mode(mdrq.BATCH_PLAIN)
+    enc = t.encode_batch(wl.queries)
+    probe = torch.empty(1, dtype=torch.int32, device="cuda")
+    st, off = t.query_batch_raw(enc, probe.data_ptr(), 0, True)
+    ids = torch.empty(max(1, int(off[-1])), dtype=torch.int32, device="cuda")
+    nq = len(wl.queries)
+    peak = measured_peaks()["hbm_gbs"]
+
+    def step():
+        st, o = t.query_batch_raw(enc, ids.data_ptr(), ids.numel(), True)
+        if st != mdrq.OK:
+            raise mdrq.MDRQError(st, "mdrq_query_batch")
+        return o
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    t.scan_timing(True)
+    t.scan_timing_read(reset=True)
+    for _ in range(args.steps):
+        off = step()
+    warm = t.scan_timing_read(reset=True)
+    ids_batch = ids[: int(off[-1])].clone()
+    least = early_break_bytes(t, cols, wl.queries, wl.n)
+    dense = warm["bytes"] / max(1, warm["scan_launches"])
+    warm_s = shards.max_over_ranks(warm["ms"]) / 1e3 / max(1, warm["scan_launches"])
+
+    # cold: one launch per query, L2 evicted before each
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    out = torch.empty(wl.n, dtype=torch.int32, device="cuda")
+    match = True
+    cold_ms = 0.0
+    launches = 0
+    for _ in range(args.steps):
+        for q, query in enumerate(wl.queries):
+            flush.add_(1)
+            torch.cuda.synchronize()
+            t.scan_timing_read(reset=True)
+            one = t.query(query, out=out)
+            tm = t.scan_timing_read(reset=True)
+            cold_ms += tm["ms"]
+            launches += tm["scan_launches"]
+            match = match and bool(torch.equal(one, ids_batch[int(off[q]):int(off[q + 1])]))
+    t.scan_timing(False)
+    del flush
+    cold_s = shards.max_over_ranks(cold_ms) / 1e3 / max(1, launches)
+    least_q, dense_q = least / nq, dense / nq
+    res = {
+        "workload": wl.name, "recipe": wl.recipe, "unit": UNIT,
+        "early_break_bytes_per_query": least_q, "dense_bytes_per_query": dense_q,
+        "warm": {"value": world * nq / warm_s, "unit": UNIT, "kernel_ms_per_batch": warm_s * 1e3,
+                 "launches": warm["scan_launches"],
+                 "early_break_gbs": least / warm_s / 1e9, "dense_gbs": dense / warm_s / 1e9,
+                 "early_break_frac": least / warm_s / 1e9 / peak,
+                 "dense_frac": dense / warm_s / 1e9 / peak,
+                 "dense_frac_of_nominal": dense / warm_s / 1e9 / NOMINAL_HBM_GBS,
+                 "served_from": "L2 (12 MB table; the batch's 100 queries re-read it)"},
+        "cold": {"value": world / cold_s, "unit": UNIT, "kernel_us_per_query": cold_s * 1e6,
+                 "launches": launches,
+                 "early_break_gbs": least_q / cold_s / 1e9, "dense_gbs": dense_q / cold_s / 1e9,
+                 "early_break_frac": least_q / cold_s / 1e9 / peak,
+                 "dense_frac": dense_q / cold_s / 1e9 / peak,
+                 "dense_frac_of_nominal": dense_q / cold_s / 1e9 / NOMINAL_HBM_GBS,
+                 "cache": "L2 evicted by a 512 MB read-and-write before every launch (outside the events)",
+                 "answers_identical_to_batch": match},
+        "peak_gbs": peak, "nominal_peak_gbs": NOMINAL_HBM_GBS,
+    }
+    res["verified"] = verify_with_oracle(wl.columns, wl.queries, ids_batch, off, list(range(nq)),
+                                         os.cpu_count() or 1)
+    t.close()
     return res
 
 
@@ -342,6 +537,8 @@ def serving_leg(args):
     switch = sys.getswitchinterval()
     sys.setswitchinterval(1e-4)
     import gc
+    verify_every = 64
+    served = []
     for rate in args.serving_rates:
         count = int(min(len(wl.queries), max(500, rate * args.serving_seconds)))
         arrivals = np.asarray(W.poisson_arrivals(rate, count, seed=int(rate)))
@@ -353,13 +550,23 @@ def serving_leg(args):
         lat_us = np.zeros(count)
         state = {"n": 0, "last": None}
 
+        kept = {}  # a sample of the served answers (1 in verify_every), checked afterwards
+
         def consumer():
             done = 0
             while done < count:
                 while state["n"] <= done:
                     time.sleep(1e-4)
                 upto = min(state["n"], done + 256)
-                _, _, lat = srv.wait_many(tickets[done:upto], release=True)
+                sample = [i for i in range(done, upto) if i % verify_every == 0]
+                _, _, lat = srv.wait_many(tickets[done:upto], release=not sample)
+                if sample:
+                    for i in sample:
+                        st, d_ids, cnt, _ = srv.wait(int(tickets[i]))
+                        kept[i] = (st, d_ids.cpu().numpy().view(np.uint32) if d_ids is not None
+                                   else np.zeros(0, np.uint32))
+                    for i in range(done, upto):
+                        srv.release(int(tickets[i]))
                 lat_us[done:upto] = lat
                 done = upto
             state["last"] = time.perf_counter()
@@ -396,10 +603,26 @@ def serving_leg(args):
                      "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99),
                      "p50_from_arrival_ms": pct(lat_arr, 0.5), "p99_from_arrival_ms": pct(lat_arr, 0.99),
                      "batches": stats["batches"], "deferred": stats["deferred"]})
+        served.extend((i, st_, a) for i, (st_, a) in kept.items())
     sys.setswitchinterval(switch)
     table.close()
-    return {"workload": wl.name, "recipe": wl.recipe, "result_memory_cap_bytes": 2 << 30,
-            "arrivals": "open-loop Poisson", "rates": rows}
+    res = {"workload": wl.name, "recipe": wl.recipe, "result_memory_cap_bytes": 2 << 30,
+           "arrivals": "open-loop Poisson", "rates": rows}
+    if not args.no_verify:
+        # the kept answers of the timed runs against the CPU oracle
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        bad = []
+        for i, st_, a in served:
+            want = oracle.mdrq_columnwise(wl.columns, wl.queries[i], nthreads=os.cpu_count() or 1)
+            if st_ != mdrq.OK or a.size != want.size or not np.array_equal(a, want):
+                bad.append(i)
+        res["verified"] = {"queries": len(served), "mismatches": len(bad), "first_mismatches": bad[:8],
+                           "sample": "every %d-th served answer of each timed rate, copied out before its "
+                                     "release; the test suite compares all 20,000 queries" % verify_every,
+                           "oracle": "CPU oracle, dimension at a time", "seconds": time.perf_counter() - t0}
+    return res
 
 
 def ctypes_array_slice(arr, i: int, j: int):
@@ -429,9 +652,16 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
             qs.append(W.target_selectivity_query(samples, dtypes, dims, s, qrng))
         wl = W.Workload(wl.name, wl.columns, qs, wl.recipe)
     nq = len(wl.queries)
+    nthreads = os.cpu_count() or 1
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
 
     stream = torch.cuda.current_stream()
-    table = mdrq.Table(wl.columns)  # copied to the device once (not timed)
+    # the columns are made resident once (not timed); the table refers to them in place
+    cols_dev = [torch.from_numpy(c).cuda() for c in wl.columns]
+    table = mdrq.Table(cols_dev)
     table.set_batch_mode(mdrq.BATCH_PLAIN)  # the headline: every query scanned on its own
     enc = table.encode_batch(wl.queries)
 
@@ -454,10 +684,6 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
         step()
     torch.cuda.synchronize()
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
     # ---- timed region: answers stay on the device
     sampler = ClockSampler(gpu_smi_id(torch, dev))
     time.sleep(0.3)
@@ -469,7 +695,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        step()
+        off_ref = step()
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -482,33 +708,13 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     zone_rows = table.zone_scan_info()[0] if args.workload == "zorder_learned" else None
     ms = shards.max_over_ranks(ms)  # the slowest rank's time counts
     value = world * nq * args.steps / (ms / 1e3)
-
-    # ---- a table that fits in L2: the same steps from a cold L2 (a 512 MB write before
-    # every step, outside the timed span; each step timed on its own)
-    cold = None
-    if 4 * wl.n * wl.d <= 126e6:
-        flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-        cold_ms = 0.0
-        for _ in range(args.steps):
-            flush.zero_()
-            c0 = torch.cuda.Event(enable_timing=True)
-            c1 = torch.cuda.Event(enable_timing=True)
-            c0.record(stream)
-            step()
-            c1.record(stream)
-            torch.cuda.synchronize()
-            cold_ms += c0.elapsed_time(c1)
-        cold_ms = shards.max_over_ranks(cold_ms)
-        alg_step = timing["bytes"] / max(1, timing["scan_launches"])
-        cold = {"value": world * nq * args.steps / (cold_ms / 1e3), "unit": UNIT,
-                "ms_per_step": cold_ms / args.steps,
-                "algorithmic_gbs": alg_step / (cold_ms / args.steps / 1e3) / 1e9,
-                "cache": "L2 flushed by a 512 MB write before every step; per-step CUDA events summed"}
-        del flush
+    # the timed batch's answer: every other leg must reproduce it id for id
+    ids_ref = ids[:total_ids].clone()
 
     # ---- the same plain batch replayed as a prepared CUDA graph (no per-call host work)
     def graph_steps(mode):
         table.set_batch_mode(mode)
+        ids.fill_(-1)
         with table.prepare(wl.queries, out=ids) as p:
             for _ in range(args.warmup):
                 p.launch()
@@ -526,7 +732,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
             kernels = p.kernels()
         return {"value": world * nq * args.steps / (gms / 1e3), "unit": UNIT, "ms_per_step": gms / args.steps,
                 "kernels_per_replay": kernels,
-                "answers_identical_to_plain": bool(int(off_g[-1]) == total_ids)}
+                "answers_identical_to_plain": same_answers(off_ref, ids_ref, off_g, ids)}
 
     plain_graph = graph_steps(mdrq.BATCH_PLAIN)
     table.set_batch_mode(mdrq.BATCH_PLAIN)
@@ -538,6 +744,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
+        ids.fill_(-1)
         barrier()
         b0 = torch.cuda.Event(enable_timing=True)
         b1 = torch.cuda.Event(enable_timing=True)
@@ -551,10 +758,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
         bvalue = world * nq * args.steps / (bms / 1e3)
         batched = {"value": bvalue, "unit": UNIT, "ms_per_step": bms / args.steps,
                    "speedup_vs_plain": bvalue / value,
-                   "mode": "shared scan: each constrained column read once per chunk of up to "
-                           "128 queries, per-row query sets from elementary-interval tables, "
-                           "two passes (count, write)",
-                   "answers_identical_to_plain": bool(int(off_b[-1]) == total_ids)}
+                   "mode": "shared scan: each constrained column read once per chunk of queries, "
+                           "per-row query sets from elementary-interval tables, two passes (count, write)",
+                   "answers_identical_to_plain": same_answers(off_ref, ids_ref, off_b, ids)}
         # autotuned shape (untimed search), then the tuned batch as a prepared graph
         t_tune = time.perf_counter()
         tune = table.autotune(wl.queries)
@@ -568,29 +774,21 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
                       "mode": "shared scan, autotuned shape (0 = built-in rule), replayed as a "
                               "prepared CUDA graph"})
         batched["tuned_graph"] = tuned
-        # the shared scan's two bounds: ALU issue for the per-predicate work (two compares
-        # and an AND per constrained value, rows x predicates x 3 simple operations at
-        # SMs x 128 lanes x the SM clock), and HBM for the least bytes a batch needs
-        # (every constrained column once, plus the ids)
-        ops = 3.0 * wl.n * sum(len({p[0] for p in q}) for q in wl.queries)
-        sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
-        alu_peak = torch.cuda.get_device_properties(dev).multi_processor_count * 128 * sm_mhz * 1e6
+        # the shared scan's bound: HBM for the least bytes a batch needs (every
+        # constrained column once per chunk of queries, plus the ids)
         cols = len({p[0] for q in wl.queries for p in q})
         least_bytes = 4.0 * wl.n * cols + 4.0 * total_ids
         for leg in (batched, tuned):
             t_s = leg["ms_per_step"] / 1e3
-            leg["alu_frac"] = ops / t_s / alu_peak
             leg["hbm_frac_least_bytes"] = least_bytes / t_s / 1e9 / measured_peaks()["hbm_gbs"]
-        batched["bounds"] = {"ops_per_batch": ops, "alu_peak_ops_per_s": alu_peak,
-                             "least_bytes_per_batch": least_bytes,
-                             "note": "per-predicate operation count; the shared scan's own "
-                                     "operations are interval lookups per column and chunk"}
+        batched["bounds"] = {"least_bytes_per_batch": least_bytes,
+                             "least_bytes_rule": "every column some query constrains, read once, plus 4 B per id"}
         table.set_batch_mode(mdrq.BATCH_PLAIN)
 
     # ---- learned range narrower: on this table when it is Z-sorted, else on its own
     learned = None
     if args.workload == "zorder_learned":
-        learned = learned_leg(args, table, enc, step, nq, total_ids, world, barrier, stream)
+        learned = learned_leg(args, table, enc, step, nq, total_ids, world, barrier, stream, ids, ids_ref, off_ref)
 
     # ---- end to end: host query descriptors in, host answers out (pinned)
     e2e = None
@@ -607,36 +805,55 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
         step_host()
         barrier()
         torch.cuda.synchronize()
+        table.scan_timing(True)
+        table.scan_timing_read(reset=True)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            step_host()
+            off_h = step_host()
         torch.cuda.synchronize()
         barrier()
         e2e_s = time.perf_counter() - t0
+        e2e_kernel = table.scan_timing_read(reset=True)
+        table.scan_timing(False)
         e2e_s = shards.max_over_ranks(e2e_s)
+        back = host_ids[:total_ids].to("cuda")
         npreds = sum(len(q) for q in wl.queries)
         e2e = {"value": world * nq * args.steps / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": 16 * npreds + 16 * nq,
                "d2h_bytes_per_step": 8 * (nq + 1) + 4 * total_ids,
+               "wall_ms_per_step": 1e3 * e2e_s / args.steps,
+               "scan_kernel_ms_per_step": e2e_kernel["ms"] / args.steps,
+               "launches_per_step": e2e_kernel["scan_launches"] / args.steps,
+               "d2h_gbs_one_copy": d2h_gbs(torch),
+               "answers_identical_to_plain": same_answers(off_ref, ids_ref, off_h, back),
                "path": "mdrq_query_batch with host query descriptors and a pinned host answer "
                        "buffer (each launch's ids copied while the next runs); host wall clock",
                "bytes": "h2d: the host descriptors passed to the call (16 B per predicate and per "
                         "query; the library stages them as one copy of 16 B per query and 32 B per "
                         "kept predicate); d2h: the offsets and every id"}
+        del back, host_ids
 
-    # ---- roofline of the scan kernel (algorithmic bytes / event-timed duration)
+    # ---- roofline of the scan kernel: bytes / event-timed launch duration
     peaks = measured_peaks()
     launches = max(1, timing["scan_launches"])
-    alg_per_launch = timing["bytes"] / launches
-    bytes_rule = "4 B per row per constrained column (every row of the table) plus 4 B per id"
+    dense_per_launch = timing["bytes"] / launches
+    dense_rule = "4 B per row per constrained column (every row of the table) plus 4 B per id"
     if zone_rows is not None:
         # every constrained column of every row of the tiles left, plus the ids
         cols = max(len({p[0] for p in q}) for q in wl.queries)
-        alg_per_launch = 4.0 * cols * zone_rows + 4.0 * total_ids
-        bytes_rule = ("4 B per row per constrained column over the rows of the tiles the zone "
+        dense_per_launch = 4.0 * cols * zone_rows + 4.0 * total_ids
+        dense_rule = ("4 B per row per constrained column over the rows of the tiles the zone "
                       "maps leave (%d rows per query) plus 4 B per id" % (zone_rows // max(1, nq)))
     avg_launch_s = timing["ms"] / 1e3 / launches
+    if zone_rows is None:
+        alg_per_launch = early_break_bytes(table, cols_dev, wl.queries, wl.n)
+        alg_rule = ("early-break bytes: per query, in the scan's predicate order, 32 B per 32-byte "
+                    "sector (8 rows) of each evaluated column that still holds a row satisfying "
+                    "the earlier predicates, plus 4 B per id")
+    else:
+        alg_per_launch, alg_rule = dense_per_launch, dense_rule
     achieved = alg_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
+    effective = dense_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
     traffic, ratio = dram_traffic_per_launch(args.workload, alg_per_launch)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"],
@@ -644,31 +861,43 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
                 "peak_source": peaks["source"] + " (HBM copy bandwidth)",
                 "kernel": ("mdrq_scan_window_kernel (plain batch over the tiles the zone maps leave)"
                            if args.workload == "zorder_learned" else "mdrq_scan_kernel"),
-                "alg_bytes_per_launch": alg_per_launch, "alg_bytes_rule": bytes_rule,
+                "alg_bytes_per_launch": alg_per_launch, "alg_bytes_rule": alg_rule,
                 "avg_launch_ms": avg_launch_s * 1e3,
                 "scan_launches": timing["scan_launches"],
-                "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
-                "dram_gbs_moved": traffic / avg_launch_s / 1e9 if traffic and avg_launch_s > 0 else None}
+                "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
+                "traffic_over_alg_bytes": ratio,
+                "dram_gbs_moved": traffic / avg_launch_s / 1e9 if traffic and avg_launch_s > 0 else None,
+                "dram_frac_moved": (traffic / avg_launch_s / 1e9 / peaks["hbm_gbs"]
+                                    if traffic and avg_launch_s > 0 else None),
+                "effective_gbs": effective, "effective_frac": effective / peaks["hbm_gbs"],
+                "effective_rule": "dense equivalent, not bytes moved: " + dense_rule}
+
+    # ---- every answer of the timed batch against the CPU oracle (rank 0)
+    verified = None
+    if rank == 0 and not args.no_verify:
+        verified = verify_with_oracle(wl.columns, wl.queries, ids_ref, off_ref, list(range(nq)), nthreads)
 
     # ---- CPU baseline: the oracle as it stands, on the host cores (rank 0, N = 1)
     cpu = None
     if world == 1 and rank == 0 and not args.no_cpu_baseline:
-        nthreads = os.cpu_count() or 1
         m, secs = time_oracle(wl, args.cpu_seconds, nthreads)
         cpu = {"value": m / secs, "unit": UNIT, "cores": nthreads, "kind": "oracle",
                "sample": "first %d of the %d queries, whole table (%d rows), %d threads over "
-                         "contiguous horizontal partitions" % (m, nq, wl.n, nthreads),
+                         "contiguous horizontal partitions, object at a time" % (m, nq, wl.n, nthreads),
                "host_cpu": host_cpu_model()}
-        # Listing 1 as written: one thread, the same queries from the first (a shorter sample)
+        # the same scan on one thread, the same queries from the first (a shorter sample)
         m1, secs1 = time_oracle(wl, args.cpu_seconds / 3.0, 1, min_queries=1)
         cpu["single_thread"] = {"value": m1 / secs1, "unit": UNIT, "cores": 1,
                                 "sample": "first %d of the %d queries, whole table, 1 thread" % (m1, nq)}
 
-    # ---- the learned narrower and the server, each on its own table
+    # ---- the small table, the learned narrower and the server, each on its own table
+    table.close()
+    del ids, ids_ref, cols_dev
+    torch.cuda.empty_cache()
+    small = None
+    if args.workload != "uniform_1M" and not args.no_small:
+        small = small_table_leg(args, world, barrier)
     if args.workload != "zorder_learned" and not args.no_learned:
-        table.close()
-        del ids
-        torch.cuda.empty_cache()
         learned = learned_workload_leg(args, world, barrier)
     serving = None
     if not args.no_serving and world == 1:
@@ -683,12 +912,11 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": cfg, "clocks": clocks, "e2e": e2e,
             "gpu_launches": timing["kernel_launches"], "roofline": roofline,
-            "cpu_baseline": cpu, "answer_ids_per_step": total_ids, "achieved_selectivity": selectivity,
-            "cold_l2": cold, "plain_graph": plain_graph,
-            "batched": batched,
+            "cpu_baseline": cpu, "verified": verified,
+            "answer_ids_per_step": total_ids, "achieved_selectivity": selectivity,
+            "plain_graph": plain_graph, "batched": batched, "small_table": small,
             "learned": learned, "serving": serving,
         }), flush=True)
-    table.close()
 
 
 def main():
@@ -712,6 +940,12 @@ def main():
     ap.add_argument("--serving-rates", type=float, nargs="*", default=[1000.0, 10000.0, 100000.0])
     ap.add_argument("--serving-seconds", type=float, default=1.5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-verify", action="store_true", help="skip the oracle check of the timed batch")
+    ap.add_argument("--no-small", action="store_true", help="skip the 1M x 3 warm / cold leg")
+    ap.add_argument("--only-small", action="store_true",
+                    help="run the 1M x 3 warm / cold leg alone (a profiling case)")
+    ap.add_argument("--verify-sample", type=int, default=256,
+                    help="queries of the Z-sorted batch checked against the oracle")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
@@ -721,6 +955,12 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.only_small:
+        # profiling case: the 1M x 3 table's warm and cold launches alone
+        import torch
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"small_table": small_table_leg(args, 1, lambda: None)}), flush=True)
         return
     if world > 1:
         import torch

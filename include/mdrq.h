@@ -165,6 +165,25 @@ uint32_t mdrq_table_dims(const mdrq_table *t);
 void mdrq_last_scan_stats(const mdrq_table *t, uint64_t *launches, uint64_t *bytes);
 
 /*
+ * mdrq_explain_query — the plan the scan follows for one query (query encoding, Sec.
+ * 2.1 with Sec. 2.2.4's most-selective-first order): the predicates it evaluates, in
+ * evaluation order, after predicates on one dimension are intersected (ANDed) and
+ * predicates that every value of their column satisfies are dropped. *empty = 1 when
+ * the query is answered as empty without a scan (an empty interval, or one that no
+ * value of its column meets); the plan is then empty. Nothing runs on the GPU.
+ *
+ *  preds, npreds   host predicates, as mdrq_query.
+ *  plan, max_plan  host output: plan[i].dim and its intersected bounds (column type).
+ *  nplan, empty    host outputs.
+ *
+ * Errors: MDRQ_E_INVAL (t, nplan or empty NULL, plan NULL with max_plan > 0, a bad
+ * predicate as for mdrq_query); MDRQ_E_CAPACITY (*nplan > max_plan: the first max_plan
+ * entries are written).
+ */
+int mdrq_explain_query(const mdrq_table *t, const mdrq_pred *preds, uint32_t npreds, mdrq_pred *plan,
+                       uint32_t max_plan, uint32_t *nplan, int *empty);
+
+/*
  * mdrq_scan_timing — measurement aid: turn per-launch timing of the scan kernel on
  * (enable = 1) or off (0) for this table. While on, every scan launch is bracketed
  * by two CUDA events recorded on the stream it is launched on.
@@ -229,8 +248,13 @@ int mdrq_set_batch_mode(mdrq_table *t, int mode);
  * each range's run from its end keys:
  *  MDRQ_MODEL_PLA  piecewise-linear, 4096 segments through evenly spaced (key, row)
  *                  pairs of the sorted keys, FP32;
- *  MDRQ_MODEL_MLP  1-32-32-1 ReLU network, FP32, trained on the GPU (Adam, 3000 steps
- *                  of 8192 pairs from a 2^20-pair sample).
+ *  MDRQ_MODEL_MLP  two stages: a 1-32-32-1 ReLU network, FP32, trained on the GPU
+ *                  (Adam, 3000 steps of 8192 pairs from a 2^20-pair sample) on the key
+ *                  normalised over the column's key range, sends a key to one of 2^18
+ *                  leaves (floor of its output times 2^18); the leaf's line through the
+ *                  first and last (key, row) pair sent to it predicts the row;
+ *  MDRQ_MODEL_NONE no model: every range's run is searched in the whole key column
+ *                  (the ablation that measures what a model saves).
  * Its largest error over all n keys is measured exhaustively (mdrq_learn_info). Each
  * predicted window is proven against the key column (widened until the keys just
  * outside it lie outside the range) and narrowed to the range's exact run before it is
@@ -242,11 +266,12 @@ int mdrq_set_batch_mode(mdrq_table *t, int mode);
  */
 #define MDRQ_MODEL_PLA 1
 #define MDRQ_MODEL_MLP 2
+#define MDRQ_MODEL_NONE 3
 int mdrq_learn(mdrq_table *t, const uint32_t *dims, uint32_t ndims, int model, void *stream);
 
-/* mdrq_learn_info — the model's largest position error over all keys, its PLA segment
- * count (0 for the MLP) and the training time in ms. Any pointer may be NULL.
- * Errors: MDRQ_E_INVAL (t NULL or no model). */
+/* mdrq_learn_info — the model's largest position error over all keys (n for
+ * MDRQ_MODEL_NONE), its segments (PLA) or leaves (MLP; 0 for none) and the training time
+ * in ms. Any pointer may be NULL. Errors: MDRQ_E_INVAL (t NULL or no model). */
 int mdrq_learn_info(const mdrq_table *t, uint64_t *max_error, uint32_t *segments, double *train_ms);
 
 /* mdrq_learn_window_rows — measurement aid: rows the last MDRQ_BATCH_LEARNED call's
@@ -254,6 +279,42 @@ int mdrq_learn_info(const mdrq_table *t, uint64_t *max_error, uint32_t *segments
  * several) and how many widening steps the window checks took (0 when every model
  * window already held its key run). Synchronous. Errors: MDRQ_E_INVAL (no model). */
 int mdrq_learn_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *widenings);
+
+/* mdrq_learn_search_info — measurement aid: key ranges the last MDRQ_BATCH_LEARNED call
+ * searched (of its last launch) and the keys its searches read in all (the two window
+ * checks, the widening steps and both binary searches of every range). Synchronous.
+ * Errors: MDRQ_E_INVAL (t NULL or no model); MDRQ_E_CUDA. */
+int mdrq_learn_search_info(mdrq_table *t, uint64_t *ranges, uint64_t *probes);
+
+/*
+ * mdrq_learn_export — the trained model, for checking it away from the GPU (the paper
+ * has no learned component; this serves tests and inspection).
+ *  desc        kind, segments (PLA segments, MLP leaves, 0 for none), mlp_params, the
+ *              MLP's input normalisation (u = (float)(key - key_min) * key_inv) and the
+ *              largest error mdrq_learn_info reports.
+ *  knot_key, knot_pos, slope   PLA: segments + 1 knots (the last is (max key + 1, n))
+ *              and segments slopes; segment i predicts knot_pos[i] + (float)(key -
+ *              knot_key[i]) * slope[i] (the product in float32) for the last i with
+ *              knot_key[i] <= key (i = 0 below the first knot). MLP: the same per leaf
+ *              (segments entries), for the leaf the network sends the key to.
+ *  mlp         MLP: mlp_params float32 weights W1[32], b1[32], W2[32][32] (row = output
+ *              unit), b2[32], W3[32], b3; output y, leaf = clamp(floor(y * segments)).
+ *  capacity    entries knot_key / knot_pos / slope can hold.
+ * Any array may be NULL. Synchronous. Errors: MDRQ_E_INVAL (t or desc NULL, no model);
+ * MDRQ_E_CAPACITY (capacity below the entries of a non-NULL array); MDRQ_E_CUDA.
+ */
+typedef struct {
+    int32_t kind;
+    uint32_t segments;
+    uint32_t mlp_params;
+    uint32_t reserved;
+    uint64_t key_min;
+    float key_inv;
+    float reserved2;
+    uint64_t max_error;
+} mdrq_model_desc;
+int mdrq_learn_export(const mdrq_table *t, mdrq_model_desc *desc, uint64_t *knot_key, uint64_t *knot_pos,
+                      float *slope, float *mlp, uint32_t capacity);
 
 /*
  * Serving: continuous batching of queries that arrive over time; the paper has no
@@ -319,7 +380,7 @@ int mdrq_server_stats(mdrq_server *s, uint64_t *completed, uint64_t *batches, ui
 
 /* mdrq_server_stop — stop accepting queries, answer the queued ones, free the server and
  * its arena (unreleased answers die with it). NULL is a no-op. Returns MDRQ_OK or the
- * CUDA error that stopped the server. */
+ * error that stopped the server (a CUDA or allocation failure of a batch). */
 int mdrq_server_stop(mdrq_server *s);
 
 /*
@@ -331,8 +392,12 @@ int mdrq_server_stop(mdrq_server *s);
  *                         bounded wait runs out (about a second), the kernel records an
  *                         error bit and finishes, and the call returns MDRQ_E_TIMEOUT;
  *                         the table's scratch is then reset and stays usable.
- *  MDRQ_FAULT_NOMEM       the next query call fails as if its scratch allocation had
- *                         failed: MDRQ_E_NOMEM, nothing launched.
+ *  MDRQ_FAULT_NOMEM       the next query call, or the next batch of a server running
+ *                         on this table, fails as if its scratch allocation had failed:
+ *                         MDRQ_E_NOMEM, nothing launched. In a server that batch's
+ *                         queries and every query queued behind it end with
+ *                         MDRQ_E_NOMEM, mdrq_server_submit refuses new queries with it,
+ *                         and mdrq_server_stop returns it.
  * Errors: MDRQ_E_INVAL (t NULL, unknown kind, SKIP_TILES with arg = 0).
  */
 #define MDRQ_FAULT_SKIP_TILES 1

@@ -12,8 +12,16 @@
 // A model predicts those two positions from the keys:
 //  * PLA: a piecewise-linear function through every (n / S)-th (key, position) pair of
 //    the sorted key column, S = 4096 segments, evaluated in FP32 (segment base exact).
-//  * MLP: position / n ~ f(key / 2^32), f a 1-32-32-1 ReLU network in FP32, trained on
-//    the device with Adam on an evenly spaced sample of (key, position) pairs.
+//  * MLP: a two-stage model whose first stage is a 1-32-32-1 ReLU network in FP32,
+//    f(u) ~ position / n with u = (key - min key) / (max key - min key), trained on the
+//    device with Adam on an evenly spaced sample of (key, position) pairs; it routes a
+//    key to one of L = 2^18 leaves, leaf floor(f(u) * L), and the leaf's linear model
+//    (through the first and the last (key, position) pair routed to it) predicts the
+//    position. On its own the network cannot follow the staircase-shaped CDF of Z-order
+//    keys over skewed columns (its error stays near a fifth of n); the leaves correct it
+//    locally.
+//  * NONE: no model; the window is the whole key column (the ablation that shows what
+//    a model saves: only search probes, since the scanned runs are exact either way).
 // Its largest error over all n keys, eps, is measured exhaustively on the device. The
 // window [pred(Z(lo)) - eps - 1, pred(Z(hi)) + eps + 2) is then checked against the key
 // column and widened (doubling steps) until the key before it is < Z(lo) and the key
@@ -37,6 +45,7 @@
 namespace mdrq {
 
 constexpr uint32_t kPlaSegments = 4096;
+constexpr uint32_t kMlpLeaves = 1u << 18;  // second stage of the MLP-rooted model
 constexpr int kMlpHidden = 32;
 constexpr int kMlpParams = kMlpHidden + kMlpHidden + kMlpHidden * kMlpHidden + kMlpHidden + kMlpHidden + 1;
 constexpr uint32_t kMlpSample = 1u << 20;   // training pairs
@@ -48,12 +57,15 @@ constexpr int kW1 = 0, kB1 = kW1 + kMlpHidden, kW2 = kB1 + kMlpHidden, kB2 = kW2
               kW3 = kB2 + kMlpHidden, kB3 = kW3 + kMlpHidden;
 
 struct LearnedModel {
-    int kind = 0;                   // MDRQ_MODEL_PLA / MDRQ_MODEL_MLP
+    int kind = 0;                   // MDRQ_MODEL_PLA / MDRQ_MODEL_MLP / MDRQ_MODEL_NONE
     uint32_t ndims = 0;
     uint32_t dims[4] = {0, 0, 0, 0};
     uint32_t *keys = nullptr;       // sorted key column (device)
-    // PLA: segment i covers keys [knot_key[i], knot_key[i+1]) from position knot_pos[i]
+    // PLA: segment i covers keys [knot_key[i], knot_key[i+1]) from position knot_pos[i];
+    // MLP: leaf i predicts knot_pos[i] + (key - knot_key[i]) * slope[i]
     uint32_t segments = 0;
+    unsigned long long key_min = 0;          // MLP input: (key - key_min) * key_inv
+    float key_inv = 0.0f;
     unsigned long long *knot_key = nullptr;  // segments + 1 (last = max key + 1)
     unsigned long long *knot_pos = nullptr;  // segments + 1
     float *slope = nullptr;                  // segments
@@ -209,7 +221,9 @@ constexpr int kMlpGradBlocks = kMlpBatch / kMlpBlockPairs;
 constexpr int kPad = kMlpHidden + 1;
 
 __global__ void __launch_bounds__(kMlpBlockPairs) mdrq_mlp_grad_kernel(const float *w, const uint32_t *keys,
-                                                                        uint64_t n, uint32_t step, float *partial)
+                                                                        uint64_t n, uint32_t step,
+                                                                        unsigned long long key_min, float key_inv,
+                                                                        float *partial)
 {
     __shared__ float s_w[kMlpParams];
     __shared__ float s_h1[kMlpBlockPairs][kPad], s_h2[kMlpBlockPairs][kPad];
@@ -222,7 +236,7 @@ __global__ void __launch_bounds__(kMlpBlockPairs) mdrq_mlp_grad_kernel(const flo
     const uint32_t j = blockIdx.x * kMlpBlockPairs + threadIdx.x;
     const uint32_t sidx = (uint32_t)(((unsigned long long)step * kMlpBatch + j) * 2654435761ull % kMlpSample);
     const unsigned long long pos = (unsigned long long)sidx * n / kMlpSample;
-    const float u = (float)keys[pos] * (1.0f / 4294967296.0f);
+    const float u = (float)((unsigned long long)keys[pos] - key_min) * key_inv;
     const float target = (float)((double)pos / (double)n);
     float h1[kMlpHidden], h2[kMlpHidden];
     const float y = mlp_forward(s_w, u, h1, h2);
@@ -291,36 +305,94 @@ __global__ void mdrq_mlp_adam_kernel(float *w, const float *partial, float *adam
     w[i] -= lr * mh / (sqrtf(vh) + 1e-8f);
 }
 
-__device__ __forceinline__ double mlp_predict(const float *w, uint64_t n, unsigned long long k)
-{
-    float h1[kMlpHidden], h2[kMlpHidden];
-    const float u = (float)k * (1.0f / 4294967296.0f);
-    return (double)mlp_forward(w, u, h1, h2) * (double)n;
-}
-
 // ---------------------------------------------------------------- error and windows
 
 struct ModelView {
     int kind;
-    uint32_t segments;
-    const unsigned long long *knot_key;
+    uint32_t segments;                   // PLA segments or MLP leaves
+    const unsigned long long *knot_key;  // PLA knots or leaf first keys
     const unsigned long long *knot_pos;
     const float *slope;
     const float *mlp;
+    unsigned long long key_min;
+    float key_inv;
     uint64_t n;
 };
+
+// the leaf the MLP-rooted model sends key k to (first stage, weights in shared memory)
+__device__ __forceinline__ uint32_t mlp_leaf(const ModelView &mv, const float *w, unsigned long long k)
+{
+    float h1[kMlpHidden], h2[kMlpHidden];
+    const float d = k >= mv.key_min ? (float)(k - mv.key_min) : -(float)(mv.key_min - k);
+    const float y = mlp_forward(w, d * mv.key_inv, h1, h2) * (float)mv.segments;
+    if (!(y > 0.0f))  // also NaN
+        return 0;
+    return y >= (float)(mv.segments - 1) ? mv.segments - 1 : (uint32_t)y;
+}
 
 __device__ __forceinline__ double model_predict(const ModelView &mv, const float *w_shared, unsigned long long k)
 {
     if (mv.kind == MDRQ_MODEL_PLA)
         return pla_predict(mv.knot_key, mv.knot_pos, mv.slope, mv.segments, k);
-    return mlp_predict(w_shared, mv.n, k);
+    const uint32_t l = mlp_leaf(mv, w_shared, k);
+    const unsigned long long k0 = mv.knot_key[l];
+    const float dk = k >= k0 ? (float)(k - k0) : -(float)(k0 - k);
+    return (double)mv.knot_pos[l] + (double)(dk * mv.slope[l]);
+}
+
+// MLP-rooted model, second stage: the first and the last row each leaf receives. One
+// row per thread, a warp's rows consecutive: the lanes sent to one leaf form groups
+// whose lowest lane holds the group's first row and highest lane its last.
+__global__ void __launch_bounds__(256) mdrq_leaf_span_kernel(ModelView mv, const uint32_t *keys, uint32_t *first,
+                                                             uint32_t *last)
+{
+    __shared__ float s_w[kMlpParams];
+    for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x)
+        s_w[i] = mv.mlp[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < mv.n; base += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i = base + threadIdx.x;
+        const bool live = i < mv.n;
+        const uint32_t leaf = live ? mlp_leaf(mv, s_w, keys[i]) : 0xffffffffu;
+        const uint32_t group = __match_any_sync(0xffffffffu, leaf);
+        if (live && lane == __ffs(group) - 1)
+            atomicMin(&first[leaf], (uint32_t)i);
+        if (live && lane == 31 - __clz(group))
+            atomicMax(&last[leaf], (uint32_t)i);
+    }
+}
+
+// a leaf's line through its first and last (key, row) pair; an empty leaf is marked
+// with first = 0xffffffff and filled in on the host
+__global__ void mdrq_leaf_fit_kernel(const uint32_t *keys, const uint32_t *first, const uint32_t *last, uint32_t L,
+                                     unsigned long long *leaf_key, unsigned long long *leaf_pos, float *slope)
+{
+    const uint32_t l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= L)
+        return;
+    const uint32_t p0 = first[l], p1 = last[l];
+    if (p0 == 0xffffffffu) {
+        leaf_key[l] = ~0ull;
+        leaf_pos[l] = 0;
+        slope[l] = 0.0f;
+        return;
+    }
+    const unsigned long long k0 = keys[p0], k1 = keys[p1];
+    leaf_key[l] = k0;
+    leaf_pos[l] = p0;
+    slope[l] = k1 > k0 ? (float)(p1 - p0) / (float)(k1 - k0) : 0.0f;
 }
 
 // out[0] = max over rows i of ceil(|pred(keys[i]) - i|)
 __global__ void __launch_bounds__(256) mdrq_model_error_kernel(ModelView mv, const uint32_t *keys,
                                                                unsigned long long *out)
 {
+    if (mv.kind == MDRQ_MODEL_NONE) {
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            *out = mv.n;  // the window is the whole column
+        return;
+    }
     __shared__ float s_w[kMlpParams];
     if (mv.kind == MDRQ_MODEL_MLP)
         for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x)
@@ -341,11 +413,14 @@ __global__ void __launch_bounds__(256) mdrq_model_error_kernel(ModelView mv, con
         atomicMax(out, worst);
 }
 
-// first position in [lo, hi) whose key is > k (keys[lo..hi) sorted); keys[hi] unread
+// first position in [lo, hi) whose key is > k (keys[lo..hi) sorted); keys[hi] unread;
+// *probes counts the keys read
 __device__ __forceinline__ unsigned long long upper_in(const uint32_t *keys, unsigned long long lo,
-                                                       unsigned long long hi, unsigned long long k)
+                                                       unsigned long long hi, unsigned long long k,
+                                                       unsigned long long *probes)
 {
     while (lo < hi) {
+        ++*probes;
         const unsigned long long mid = lo + ((hi - lo) >> 1);
         if ((unsigned long long)keys[mid] <= k)
             lo = mid + 1;
@@ -357,9 +432,11 @@ __device__ __forceinline__ unsigned long long upper_in(const uint32_t *keys, uns
 
 // first position in [lo, hi) whose key is >= k
 __device__ __forceinline__ unsigned long long lower_in(const uint32_t *keys, unsigned long long lo,
-                                                       unsigned long long hi, unsigned long long k)
+                                                       unsigned long long hi, unsigned long long k,
+                                                       unsigned long long *probes)
 {
     while (lo < hi) {
+        ++*probes;
         const unsigned long long mid = lo + ((hi - lo) >> 1);
         if ((unsigned long long)keys[mid] < k)
             lo = mid + 1;
@@ -372,29 +449,33 @@ __device__ __forceinline__ unsigned long long lower_in(const uint32_t *keys, uns
 // The exact row run [lower_bound(Z(lo)), upper_bound(Z(hi))) of one key range, found
 // from the model's window after the window has been proven to contain it: every row
 // before its start must have a key below Z(lo) and every row from its end on a key
-// above Z(hi), else the window is widened by doubling steps (counted in *probes).
+// above Z(hi), else the window is widened by doubling steps (counted in *widenings).
+// *probes counts every key read: the two checks, the widening steps and the searches.
 __device__ __forceinline__ void prove_run(const ModelView &mv, const float *s_w, const uint32_t *keys,
                                           unsigned long long eps, unsigned long long zlo, unsigned long long zhi,
                                           unsigned long long *lb_out, unsigned long long *ub_out,
-                                          unsigned long long *probes)
+                                          unsigned long long *widenings, unsigned long long *probes)
 {
     const long long n = (long long)mv.n;
-    const double plo = model_predict(mv, s_w, zlo), phi = model_predict(mv, s_w, zhi);
-    long long w0 = (long long)floor(fmin(fmax(plo, -1.0), (double)n)) - (long long)eps - 1;
-    long long w1 = (long long)ceil(fmin(fmax(phi, -1.0), (double)n)) + (long long)eps + 2;
-    w0 = w0 < 0 ? 0 : (w0 > n ? n : w0);
-    w1 = w1 < w0 ? w0 : (w1 > n ? n : w1);
-    for (long long step = 1; w0 > 0 && (unsigned long long)keys[w0 - 1] >= zlo; step *= 2) {
+    long long w0 = 0, w1 = n;
+    if (mv.kind != MDRQ_MODEL_NONE) {
+        const double plo = model_predict(mv, s_w, zlo), phi = model_predict(mv, s_w, zhi);
+        w0 = (long long)floor(fmin(fmax(plo, -1.0), (double)n)) - (long long)eps - 1;
+        w1 = (long long)ceil(fmin(fmax(phi, -1.0), (double)n)) + (long long)eps + 2;
+        w0 = w0 < 0 ? 0 : (w0 > n ? n : w0);
+        w1 = w1 < w0 ? w0 : (w1 > n ? n : w1);
+    }
+    for (long long step = 1; w0 > 0 && (++*probes, (unsigned long long)keys[w0 - 1] >= zlo); step *= 2) {
         w0 = w0 > step ? w0 - step : 0;
-        ++*probes;
+        ++*widenings;
     }
-    for (long long step = 1; w1 < n && (unsigned long long)keys[w1] <= zhi; step *= 2) {
+    for (long long step = 1; w1 < n && (++*probes, (unsigned long long)keys[w1] <= zhi); step *= 2) {
         w1 = w1 + step < n ? w1 + step : n;
-        ++*probes;
+        ++*widenings;
     }
-    const unsigned long long lb = lower_in(keys, (unsigned long long)w0, (unsigned long long)w1, zlo);
+    const unsigned long long lb = lower_in(keys, (unsigned long long)w0, (unsigned long long)w1, zlo, probes);
     *lb_out = lb;
-    *ub_out = upper_in(keys, lb, (unsigned long long)w1, zhi);
+    *ub_out = upper_in(keys, lb, (unsigned long long)w1, zhi, probes);
 }
 
 // ---------------------------------------------------------------- box decomposition
@@ -502,7 +583,7 @@ __device__ __forceinline__ ulonglong2 run_of_node(const BoxNode &x, uint32_t nd)
 // the query, the range count to counts[q] and the tile total to qtiles[q].
 __global__ void __launch_bounds__(kBoxThreads) mdrq_box_windows_kernel(
     ModelView mv, const uint32_t *keys, unsigned long long eps, const uint32_t *qcells, uint32_t nd,
-    uint32_t tile_rows, DevWindow *slots, uint32_t *counts, uint32_t *qtiles, unsigned long long *probe_count)
+    uint32_t tile_rows, DevWindow *slots, uint32_t *counts, uint32_t *qtiles, unsigned long long *counters)
 {
     extern __shared__ __align__(16) unsigned char s_raw[];
     BoxNode *cur = reinterpret_cast<BoxNode *>(s_raw);
@@ -681,15 +762,17 @@ __global__ void __launch_bounds__(kBoxThreads) mdrq_box_windows_kernel(
     // (2) row runs and tiles of the ranges, thread t taking ranges t*kBoxPer.. in key order
     unsigned long long lbs[kBoxPer], ubs[kBoxPer];
     uint32_t tl[kBoxPer], mytiles = 0;
-    unsigned long long probes = 0;
+    unsigned long long widenings = 0, probes = 0, ranges = 0;
 #pragma unroll
     for (int k = 0; k < kBoxPer; ++k) {
         const uint32_t i = threadIdx.x * kBoxPer + k;
         lbs[k] = ubs[k] = 0;
         tl[k] = 0;
         if (i < nr) {
-            if (!none)
-                prove_run(mv, s_w, keys, eps, rng[i].x, rng[i].y, &lbs[k], &ubs[k], &probes);
+            if (!none) {
+                prove_run(mv, s_w, keys, eps, rng[i].x, rng[i].y, &lbs[k], &ubs[k], &widenings, &probes);
+                ++ranges;
+            }
             const unsigned long long rows = ubs[k] > lbs[k] ? ubs[k] - (lbs[k] & ~127ull) : 0;
             tl[k] = rows ? (uint32_t)((rows + tile_rows - 1) / tile_rows) : (i + 1 == nr ? 1u : 0u);
         }
@@ -718,10 +801,19 @@ __global__ void __launch_bounds__(kBoxThreads) mdrq_box_windows_kernel(
         counts[q] = nr;
         qtiles[q] = tincl;
     }
-    for (int o = 16; o > 0; o >>= 1)
+    for (int o = 16; o > 0; o >>= 1) {
+        widenings += __shfl_xor_sync(0xffffffffu, widenings, o);
         probes += __shfl_xor_sync(0xffffffffu, probes, o);
-    if ((threadIdx.x & 31) == 0 && probes)
-        atomicAdd(probe_count, probes);
+        ranges += __shfl_xor_sync(0xffffffffu, ranges, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (widenings)
+            atomicAdd(&counters[0], widenings);
+        if (probes)
+            atomicAdd(&counters[1], probes);
+        if (ranges)
+            atomicAdd(&counters[2], ranges);
+    }
 }
 
 // Exclusive scans of the per-query window counts and tile totals (one block):
@@ -822,6 +914,8 @@ ModelView view_of(const LearnedModel &m, uint64_t n)
     v.knot_pos = m.knot_pos;
     v.slope = m.slope;
     v.mlp = m.mlp;
+    v.key_min = m.key_min;
+    v.key_inv = m.key_inv;
     v.n = n;
     return v;
 }
@@ -856,7 +950,8 @@ void learned_free(mdrq_table *t)
 
 int learn(mdrq_table *t, const uint32_t *dims, uint32_t ndims, int kind, cudaStream_t s)
 {
-    if (!t || !dims || ndims == 0 || ndims > 4 || (kind != MDRQ_MODEL_PLA && kind != MDRQ_MODEL_MLP) || t->n == 0)
+    if (!t || !dims || ndims == 0 || ndims > 4 ||
+        (kind != MDRQ_MODEL_PLA && kind != MDRQ_MODEL_MLP && kind != MDRQ_MODEL_NONE) || t->n == 0)
         return MDRQ_E_INVAL;
     for (uint32_t j = 0; j < ndims; ++j)
         if (dims[j] >= t->d || t->cols[dims[j]].type != MDRQ_F32)
@@ -903,7 +998,20 @@ int learn(mdrq_table *t, const uint32_t *dims, uint32_t ndims, int kind, cudaStr
                 break;
             mdrq_pla_fit_kernel<<<(m->segments + 256) / 256, 256, 0, s>>>(m->keys, n, m->segments, m->knot_key,
                                                                          m->knot_pos, m->slope);
-        } else {
+        } else if (kind == MDRQ_MODEL_MLP) {
+            // the network's input: the key normalised over the column's key range
+            unsigned long long ends[2] = {0, 0};
+            {
+                uint32_t k0 = 0, k1 = 0;
+                if ((st = cuda_status(cudaMemcpyAsync(&k0, m->keys, 4, cudaMemcpyDeviceToHost, s))) ||
+                    (st = cuda_status(cudaMemcpyAsync(&k1, m->keys + n - 1, 4, cudaMemcpyDeviceToHost, s))) ||
+                    (st = cuda_status(cudaStreamSynchronize(s))))
+                    break;
+                ends[0] = k0;
+                ends[1] = k1;
+            }
+            m->key_min = ends[0];
+            m->key_inv = ends[1] > ends[0] ? (float)(1.0 / (double)(ends[1] - ends[0])) : 0.0f;
             float *grad = nullptr, *adam = nullptr;
             if ((st = cuda_status(cudaMalloc(&m->mlp, kMlpParams * 4))) ||
                 (st = cuda_status(cudaMalloc(&grad, (size_t)kMlpGradBlocks * kMlpParams * 4))) ||
@@ -915,13 +1023,63 @@ int learn(mdrq_table *t, const uint32_t *dims, uint32_t ndims, int kind, cudaStr
             const uint32_t pb = (kMlpParams + 255) / 256;
             mdrq_mlp_init_kernel<<<pb, 256, 0, s>>>(m->mlp, adam);
             for (uint32_t step = 0; step < kMlpSteps; ++step) {
-                mdrq_mlp_grad_kernel<<<kMlpGradBlocks, kMlpBlockPairs, 0, s>>>(m->mlp, m->keys, n, step, grad);
+                mdrq_mlp_grad_kernel<<<kMlpGradBlocks, kMlpBlockPairs, 0, s>>>(m->mlp, m->keys, n, step, m->key_min,
+                                                                               m->key_inv, grad);
                 mdrq_mlp_adam_kernel<<<pb, 256, 0, s>>>(m->mlp, grad, adam, step);
             }
             st = cuda_status(cudaStreamSynchronize(s));
             cudaFree(grad);
             cudaFree(adam);
             if (st)
+                break;
+            // second stage: each leaf's line through its first and last row
+            const uint32_t L = kMlpLeaves;
+            m->segments = L;
+            uint32_t *span = nullptr;
+            if ((st = cuda_status(cudaMalloc(&m->knot_key, L * 8ull))) ||
+                (st = cuda_status(cudaMalloc(&m->knot_pos, L * 8ull))) ||
+                (st = cuda_status(cudaMalloc(&m->slope, L * 4ull))) ||
+                (st = cuda_status(cudaMalloc(&span, L * 8ull))))
+                break;
+            uint32_t *first = span, *last = span + L;
+            if ((st = cuda_status(cudaMemsetAsync(first, 0xff, L * 4ull, s))) ||
+                (st = cuda_status(cudaMemsetAsync(last, 0, L * 4ull, s)))) {
+                cudaFree(span);
+                break;
+            }
+            const ModelView mv0 = view_of(*m, n);
+            mdrq_leaf_span_kernel<<<(uint32_t)t->sm_count * 8, 256, 0, s>>>(mv0, m->keys, first, last);
+            mdrq_leaf_fit_kernel<<<(L + 255) / 256, 256, 0, s>>>(m->keys, first, last, L, m->knot_key, m->knot_pos,
+                                                                  m->slope);
+            // an empty leaf (reached by no key of the table, only by query keys) predicts
+            // the row after the last row of the nearest non-empty leaf before it
+            std::vector<uint32_t> hlast(L), hfirst(L);
+            std::vector<unsigned long long> hkey(L), hpos(L);
+            std::vector<float> hslope(L);
+            if ((st = cuda_status(cudaMemcpyAsync(hfirst.data(), first, L * 4ull, cudaMemcpyDeviceToHost, s))) ||
+                (st = cuda_status(cudaMemcpyAsync(hlast.data(), last, L * 4ull, cudaMemcpyDeviceToHost, s))) ||
+                (st = cuda_status(cudaMemcpyAsync(hkey.data(), m->knot_key, L * 8ull, cudaMemcpyDeviceToHost, s))) ||
+                (st = cuda_status(cudaMemcpyAsync(hpos.data(), m->knot_pos, L * 8ull, cudaMemcpyDeviceToHost, s))) ||
+                (st = cuda_status(cudaMemcpyAsync(hslope.data(), m->slope, L * 4ull, cudaMemcpyDeviceToHost, s))) ||
+                (st = cuda_status(cudaStreamSynchronize(s)))) {
+                cudaFree(span);
+                break;
+            }
+            cudaFree(span);
+            unsigned long long after = 0;  // the row after the last non-empty leaf so far
+            for (uint32_t l = 0; l < L; ++l) {
+                if (hfirst[l] == 0xffffffffu) {
+                    hkey[l] = 0;
+                    hpos[l] = after;
+                    hslope[l] = 0.0f;
+                } else {
+                    after = std::min<unsigned long long>((unsigned long long)hlast[l] + 1, n);
+                }
+            }
+            if ((st = cuda_status(cudaMemcpyAsync(m->knot_key, hkey.data(), L * 8ull, cudaMemcpyHostToDevice, s))) ||
+                (st = cuda_status(cudaMemcpyAsync(m->knot_pos, hpos.data(), L * 8ull, cudaMemcpyHostToDevice, s))) ||
+                (st = cuda_status(cudaMemcpyAsync(m->slope, hslope.data(), L * 4ull, cudaMemcpyHostToDevice, s))) ||
+                (st = cuda_status(cudaStreamSynchronize(s))))
                 break;
         }
         if ((st = cuda_status(cudaGetLastError())))
@@ -990,7 +1148,7 @@ int learned_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std
     unsigned long long *wbase = reinterpret_cast<unsigned long long *>(qtiles + nlive);
     unsigned long long *tbase = wbase + nlive;
     MDRQ_TRY_STATUS(cudaMemcpyAsync(qcells, m->qcells.data(), (size_t)nlive * 8, cudaMemcpyHostToDevice, s));
-    MDRQ_TRY_STATUS(cudaMemsetAsync(m->scratch + 1, 0, 8, s));
+    MDRQ_TRY_STATUS(cudaMemsetAsync(m->scratch + 1, 0, 3 * 8, s));
     MDRQ_TRY_STATUS(cudaFuncSetAttribute(mdrq_box_windows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kBoxSmem));
     const ModelView mv = view_of(*m, t->n);
@@ -1005,7 +1163,7 @@ int learned_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std
                               m->totals, s);
 }
 
-int learned_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *probes)
+int learned_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *widenings)
 {
     if (!t || !t->learned)
         return MDRQ_E_INVAL;
@@ -1022,8 +1180,51 @@ int learned_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *probes)
         sum += x.row_end > x.row_first ? x.row_end - x.row_first : 0;
     if (rows)
         *rows = sum;
+    if (widenings)
+        *widenings = pr;
+    return MDRQ_OK;
+}
+
+int learned_search_info(mdrq_table *t, uint64_t *ranges, uint64_t *probes)
+{
+    if (!t || !t->learned)
+        return MDRQ_E_INVAL;
+    unsigned long long c[2] = {0, 0};  // probes, ranges
+    MDRQ_TRY_STATUS(cudaMemcpy(c, t->learned->scratch + 2, 16, cudaMemcpyDeviceToHost));
     if (probes)
-        *probes = pr;
+        *probes = c[0];
+    if (ranges)
+        *ranges = c[1];
+    return MDRQ_OK;
+}
+
+int learned_export(const mdrq_table *t, mdrq_model_desc *desc, uint64_t *knot_key, uint64_t *knot_pos, float *slope,
+                   float *mlp, uint32_t capacity)
+{
+    if (!t || !t->learned || !desc)
+        return MDRQ_E_INVAL;
+    const LearnedModel &m = *t->learned;
+    std::memset(desc, 0, sizeof(*desc));
+    desc->kind = m.kind;
+    desc->segments = m.kind == MDRQ_MODEL_NONE ? 0 : m.segments;
+    desc->mlp_params = m.kind == MDRQ_MODEL_MLP ? (uint32_t)kMlpParams : 0;
+    desc->key_min = m.key_min;
+    desc->key_inv = m.key_inv;
+    desc->max_error = m.max_error;
+    // PLA knots: segments + 1 (the end knot); MLP leaves: segments
+    const uint32_t entries = m.kind == MDRQ_MODEL_PLA ? m.segments + 1 : (m.kind == MDRQ_MODEL_MLP ? m.segments : 0);
+    if (entries && (knot_key || knot_pos || slope)) {
+        if (capacity < entries)
+            return MDRQ_E_CAPACITY;
+        if (knot_key)
+            MDRQ_TRY_STATUS(cudaMemcpy(knot_key, m.knot_key, entries * 8ull, cudaMemcpyDeviceToHost));
+        if (knot_pos)
+            MDRQ_TRY_STATUS(cudaMemcpy(knot_pos, m.knot_pos, entries * 8ull, cudaMemcpyDeviceToHost));
+        if (slope)
+            MDRQ_TRY_STATUS(cudaMemcpy(slope, m.slope, m.segments * 4ull, cudaMemcpyDeviceToHost));
+    }
+    if (mlp && m.kind == MDRQ_MODEL_MLP)
+        MDRQ_TRY_STATUS(cudaMemcpy(mlp, m.mlp, kMlpParams * 4ull, cudaMemcpyDeviceToHost));
     return MDRQ_OK;
 }
 
@@ -1034,7 +1235,7 @@ int learned_info(const mdrq_table *t, uint64_t *max_error, uint32_t *segments, d
     if (max_error)
         *max_error = t->learned->max_error;
     if (segments)
-        *segments = t->learned->kind == MDRQ_MODEL_PLA ? t->learned->segments : 0;
+        *segments = t->learned->segments;
     if (train_ms)
         *train_ms = t->learned->train_ms;
     return MDRQ_OK;

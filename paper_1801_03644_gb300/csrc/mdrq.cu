@@ -699,10 +699,8 @@ int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, u
     t->last_launches = 0;
     t->last_bytes = 0;
     MDRQ_TRY(cudaSetDevice(t->device));
-    if (t->inject_nomem) {
-        t->inject_nomem = 0;
+    if (__atomic_exchange_n(&t->inject_nomem, 0, __ATOMIC_ACQ_REL))
         return MDRQ_E_NOMEM;
-    }
     // host answers: the scan writes a device staging buffer, and the ids of each finished
     // launch are copied to the host on a second stream while the next launch runs
     uint32_t *out = ids;
@@ -1107,6 +1105,17 @@ int mdrq_learn_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *widenings)
     return learned_window_rows(t, rows, widenings);
 }
 
+int mdrq_learn_search_info(mdrq_table *t, uint64_t *ranges, uint64_t *probes)
+{
+    return learned_search_info(t, ranges, probes);
+}
+
+int mdrq_learn_export(const mdrq_table *t, mdrq_model_desc *desc, uint64_t *knot_key, uint64_t *knot_pos,
+                      float *slope, float *mlp, uint32_t capacity)
+{
+    return learned_export(t, desc, knot_key, knot_pos, slope, mlp, capacity);
+}
+
 int mdrq_set_zone_maps(mdrq_table *t, int mode)
 {
     if (!t || (mode != MDRQ_ZONES_OFF && mode != MDRQ_ZONES_AUTO && mode != MDRQ_ZONES_ALL))
@@ -1138,11 +1147,31 @@ int mdrq_inject_fault(mdrq_table *t, int kind, uint64_t arg)
         t->inject_skip_tiles = arg;
         return MDRQ_OK;
     case MDRQ_FAULT_NOMEM:
-        t->inject_nomem = 1;
+        __atomic_store_n(&t->inject_nomem, 1, __ATOMIC_RELEASE);
         return MDRQ_OK;
     default:
         return MDRQ_E_INVAL;
     }
+}
+
+int mdrq_explain_query(const mdrq_table *t, const mdrq_pred *preds, uint32_t npreds, mdrq_pred *plan,
+                       uint32_t max_plan, uint32_t *nplan, int *empty)
+{
+    if (!t || !nplan || !empty || (max_plan > 0 && !plan))
+        return MDRQ_E_INVAL;
+    EncodedQuery q;
+    const int st = encode_query(t, preds, npreds, q);
+    if (st != MDRQ_OK)
+        return st;
+    *empty = q.empty ? 1 : 0;
+    *nplan = (uint32_t)q.preds.size();
+    for (size_t i = 0; i < q.preds.size() && i < max_plan; ++i) {
+        plan[i].dim = q.dims[i];
+        plan[i].reserved = 0;
+        std::memcpy(&plan[i].lo, &q.preds[i].lo, 4);
+        std::memcpy(&plan[i].hi, &q.preds[i].hi, 4);
+    }
+    return q.preds.size() > max_plan ? MDRQ_E_CAPACITY : MDRQ_OK;
 }
 
 void mdrq_last_scan_stats(const mdrq_table *t, uint64_t *launches, uint64_t *bytes)

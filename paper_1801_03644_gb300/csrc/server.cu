@@ -212,6 +212,10 @@ void scheduler_main(mdrq_server *S)
         // exact answer sizes of the batch: the shared scan's count phase, or for a small
         // batch the whole plain scan into the scratch buffer
         int rc = grow_pinned((void **)&S->host_buf[k], &S->host_cap[k], nb * 8 * 3 + 8);
+        // host-side failure injection (mdrq_inject_fault): this batch's scratch
+        // allocation fails before any of its GPU work is enqueued
+        if (rc == MDRQ_OK && __atomic_exchange_n(&S->t->inject_nomem, 0, __ATOMIC_ACQ_REL))
+            rc = MDRQ_E_NOMEM;
         unsigned long long *totals = S->host_buf[k], *bases = S->host_buf[k] + nb;
         uint64_t *offs = reinterpret_cast<uint64_t *>(S->host_buf[k] + 2 * nb);
         if (plain) {
@@ -290,8 +294,10 @@ void scheduler_main(mdrq_server *S)
                         S->pending.pop_front();
                     }
                 }
-                // nothing fitted: wait until answers are released (or a batch ends)
-                wait_for_release = i < nb && S->inflight.empty();
+                // nothing fitted: wait until answers are released. Counting the same
+                // queries again before then would only repeat the count phase (its
+                // sizes cannot change) and take HBM from the batch in flight.
+                wait_for_release = i < nb;
             }
             S->cv_done.notify_all();
         }
@@ -299,8 +305,9 @@ void scheduler_main(mdrq_server *S)
             if (wait_for_release) {
                 std::unique_lock<std::mutex> lock(S->mu);
                 const uint64_t used = S->arena.used();
-                S->cv_sched.wait_for(lock, std::chrono::milliseconds(50),
-                                     [&] { return S->stopping || S->arena.used() < used; });
+                S->cv_sched.wait_for(lock, std::chrono::milliseconds(50), [&] {
+                    return S->stopping || S->fatal != MDRQ_OK || S->arena.used() < used;
+                });
             }
             continue;
         }

@@ -198,6 +198,9 @@ int learned_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std
                   cudaStream_t s);
 int learned_info(const mdrq_table *t, uint64_t *max_error, uint32_t *segments, double *train_ms);
 void learned_free(mdrq_table *t);
-int learned_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *probes);
+int learned_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *widenings);
+int learned_search_info(mdrq_table *t, uint64_t *ranges, uint64_t *probes);
+int learned_export(const mdrq_table *t, mdrq_model_desc *desc, uint64_t *knot_key, uint64_t *knot_pos, float *slope,
+                   float *mlp, uint32_t capacity);
 
 }  // namespace mdrq

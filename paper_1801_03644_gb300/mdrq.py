@@ -39,6 +39,12 @@ class Tuning(ctypes.Structure):
                 ("shared_default_ms", ctypes.c_double), ("shared_ms", ctypes.c_double)]
 
 
+class ModelDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("segments", ctypes.c_uint32), ("mlp_params", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("key_min", ctypes.c_uint64), ("key_inv", ctypes.c_float),
+                ("reserved2", ctypes.c_float), ("max_error", ctypes.c_uint64)]
+
+
 class QDesc(ctypes.Structure):
     _fields_ = [("preds", ctypes.POINTER(Pred)), ("npreds", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32)]
@@ -55,11 +61,12 @@ EXPORTS = ["mdrq_load_columns", "mdrq_query", "mdrq_query_batch", "mdrq_free",
            "mdrq_prepared_launch", "mdrq_prepared_wait", "mdrq_prepared_kernels", "mdrq_prepared_free",
            "mdrq_set_shared_config", "mdrq_set_shared_bits_budget", "mdrq_autotune",
            "mdrq_set_zone_maps", "mdrq_zone_map_info", "mdrq_zone_scan_info",
-           "mdrq_server_submit_batch", "mdrq_server_wait_many"]
+           "mdrq_server_submit_batch", "mdrq_server_wait_many", "mdrq_explain_query",
+           "mdrq_learn_search_info", "mdrq_learn_export"]
 
 FAULT_SKIP_TILES, FAULT_NOMEM = 1, 2
 BATCH_AUTO, BATCH_PLAIN, BATCH_SHARED, BATCH_LEARNED = 0, 1, 2, 3
-MODEL_PLA, MODEL_MLP = 1, 2
+MODEL_PLA, MODEL_MLP, MODEL_NONE = 1, 2, 3
 ZONES_OFF, ZONES_AUTO, ZONES_ALL = 0, 1, 2
 
 STATIC_MAX_ROWS = 1 << 28  # MDRQ_STATIC_MAX_ROWS
@@ -103,6 +110,11 @@ def lib():
         L.mdrq_learn_info.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u32), ctypes.POINTER(ctypes.c_double)]
         L.mdrq_learn_window_rows.restype = ctypes.c_int
         L.mdrq_learn_window_rows.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]
+        L.mdrq_learn_export.restype = ctypes.c_int
+        L.mdrq_learn_export.argtypes = [vp, ctypes.POINTER(ModelDesc), ctypes.POINTER(u64), ctypes.POINTER(u64),
+                                        ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), u32]
+        L.mdrq_learn_search_info.restype = ctypes.c_int
+        L.mdrq_learn_search_info.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]
         L.mdrq_set_batch_mode.restype = ctypes.c_int
         L.mdrq_set_batch_mode.argtypes = [vp, ctypes.c_int]
         L.mdrq_server_start.restype = ctypes.c_int
@@ -152,6 +164,9 @@ def lib():
         L.mdrq_prepared_kernels.argtypes = [vp, ctypes.POINTER(u64)]
         L.mdrq_prepared_free.restype = None
         L.mdrq_prepared_free.argtypes = [vp]
+        L.mdrq_explain_query.restype = ctypes.c_int
+        L.mdrq_explain_query.argtypes = [vp, ctypes.POINTER(Pred), u32, ctypes.POINTER(Pred), u32,
+                                         ctypes.POINTER(u32), ctypes.POINTER(ctypes.c_int)]
         _lib = L
     return _lib
 
@@ -170,6 +185,13 @@ def _bits(v, dtype: int) -> int:
     if not -2**31 <= iv < 2**31:
         raise ValueError("int32 bound out of range: %r" % v)
     return iv & 0xFFFFFFFF
+
+
+def _unbits(b: int, dtype: int):
+    """Inverse of ``_bits``: a bound's bit pattern as a Python float or int."""
+    if dtype == F32:
+        return float(np.array([b], dtype=np.uint32).view(np.float32)[0])
+    return int(np.array([b], dtype=np.uint32).view(np.int32)[0])
 
 
 def encode_query(query, dtypes) -> ctypes.Array:
@@ -319,6 +341,24 @@ class Table:
             raise MDRQError(st, "mdrq_query")
         return out[: int(cnt.value)]
 
+    def explain(self, query):
+        """``mdrq_explain_query``: (empty, [(dim, lo, hi), ...]) — whether the query is
+        answered empty without a scan, and the predicates the scan evaluates in order,
+        with bounds as Python numbers of the columns' types."""
+        preds = encode_query(query, self.dtypes)
+        cap = max(1, len(query))
+        plan = (Pred * cap)()
+        k, empty = ctypes.c_uint32(0), ctypes.c_int(0)
+        st = lib().mdrq_explain_query(self._h, preds, len(query), plan, cap, ctypes.byref(k), ctypes.byref(empty))
+        if st != OK:
+            raise MDRQError(st, "mdrq_explain_query")
+        out = []
+        for i in range(int(k.value)):
+            j = int(plan[i].dim)
+            lo, hi = _unbits(plan[i].lo, self.dtypes[j]), _unbits(plan[i].hi, self.dtypes[j])
+            out.append((j, lo, hi))
+        return bool(empty.value), out
+
     def query_host(self, query, capacity=None, stream=None) -> np.ndarray:
         """Answer one query into host memory (``ids_on_device = 0``); uint32 numpy array."""
         preds = encode_query(query, self.dtypes)
@@ -461,6 +501,36 @@ class Table:
         if st != OK:
             raise MDRQError(st, "mdrq_learn_window_rows")
         return int(r.value), int(w.value)
+
+    def learn_search_info(self) -> tuple:
+        """(key ranges searched, keys read by the searches) of the last learned batch."""
+        r, k = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        st = lib().mdrq_learn_search_info(self._h, ctypes.byref(r), ctypes.byref(k))
+        if st != OK:
+            raise MDRQError(st, "mdrq_learn_search_info")
+        return int(r.value), int(k.value)
+
+    def learn_export(self) -> dict:
+        """``mdrq_learn_export``: the model's description and parameters as numpy arrays."""
+        d = ModelDesc()
+        st = lib().mdrq_learn_export(self._h, ctypes.byref(d), None, None, None, None, 0)
+        if st != OK:
+            raise MDRQError(st, "mdrq_learn_export")
+        cap = d.segments + 1
+        kk = np.zeros(cap, dtype=np.uint64)
+        kp = np.zeros(cap, dtype=np.uint64)
+        sl = np.zeros(max(1, d.segments), dtype=np.float32)
+        w = np.zeros(max(1, d.mlp_params), dtype=np.float32)
+        P = ctypes.POINTER
+        st = lib().mdrq_learn_export(self._h, ctypes.byref(d), kk.ctypes.data_as(P(ctypes.c_uint64)),
+                                     kp.ctypes.data_as(P(ctypes.c_uint64)), sl.ctypes.data_as(P(ctypes.c_float)),
+                                     w.ctypes.data_as(P(ctypes.c_float)), cap)
+        if st != OK:
+            raise MDRQError(st, "mdrq_learn_export")
+        entries = d.segments + 1 if d.kind == MODEL_PLA else d.segments
+        return {"kind": d.kind, "segments": d.segments, "key_min": int(d.key_min), "key_inv": np.float32(d.key_inv),
+                "max_error": int(d.max_error), "knot_key": kk[:entries], "knot_pos": kp[:entries],
+                "slope": sl[:d.segments], "mlp": w[:d.mlp_params]}
 
     def set_batch_mode(self, mode: int):
         """``mdrq_set_batch_mode``: BATCH_AUTO, BATCH_PLAIN or BATCH_SHARED."""

@@ -287,3 +287,26 @@ def test_host_answers_pinned_and_pageable(M, mode):
         page = np.zeros(total, dtype=np.uint32)
         st, off = t.query_batch_raw(enc, page.ctypes.data, total, False)
         assert st == M.OK and np.array_equal(page, cat)
+
+
+def test_explain_query_plan(M):
+    """mdrq_explain_query: repeated dimensions are intersected, predicates every value
+    satisfies are dropped, queries no value can meet are answered empty, and the rest
+    are evaluated most selective first; the answer follows the plan."""
+    rng = np.random.default_rng(5)
+    n = 100_000
+    x = rng.random(n, dtype=np.float32)
+    y = rng.integers(-5, 6, size=n, dtype=np.int32)
+    with M.Table(_device([x, y])) as t:
+        assert t.explain([(0, 0.2, 0.5), (1, -100, 100)]) == (False, [(0, float(np.float32(0.2)),
+                                                                          float(np.float32(0.5)))])
+        assert t.explain([(0, 0.2, 0.5), (0, 0.3, 0.9)]) == (False, [(0, float(np.float32(0.3)),
+                                                                         float(np.float32(0.5)))])
+        assert t.explain([(0, 0.5, 0.2)]) == (True, [])
+        assert t.explain([(1, 10, 20)]) == (True, [])
+        assert t.explain([]) == (False, [])
+        empty, plan = t.explain([(0, 0.0, 0.9), (1, 0, 0)])
+        assert not empty and [p[0] for p in plan] == [1, 0]  # y = 0 holds for 1 in 11 rows
+        for q in ([(0, 0.2, 0.5), (1, -100, 100)], [(0, 0.0, 0.9), (1, 0, 0)]):
+            _, plan = t.explain(q)
+            assert np.array_equal(M.as_uint32_numpy(t.query(q)), oracle.mdrq([x, y], plan))

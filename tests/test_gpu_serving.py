@@ -154,3 +154,27 @@ def test_bulk_submit_and_wait_many(M):
         with pytest.raises(M.MDRQError):
             srv.wait_many(tk[:1])  # already released
         assert srv.stop() == M.OK
+
+
+def test_allocation_failure_ends_the_batch_and_the_queue(M):
+    """A batch whose scratch allocation fails (injected on the host, before any of its
+    GPU work) ends with MDRQ_E_NOMEM, and so does every query queued behind it; submit
+    then refuses with that status, and stop returns it. No GPU fault is involved."""
+    wl = W.serving_table(n=200_000, nq=600)
+    with M.Table(_device(wl.columns)) as t:
+        srv = M.Server(t, result_bytes=1 << 26, max_batch=64)
+        t.inject_fault(M.FAULT_NOMEM)
+        tickets = srv.submit_batch(t.encode_batch(wl.queries))
+        status, counts, _ = srv.wait_many(tickets, release=False, timeout_us=30_000_000)
+        failed = status == M.E_NOMEM
+        # queries proven empty on the host are answered at submit, before any batch
+        answered_at_submit = (status == M.OK) & (counts == 0)
+        assert np.all(failed | answered_at_submit), np.unique(status)
+        assert failed.sum() >= 64 and failed.sum() > 64  # the failed batch and the queue behind it
+        with pytest.raises(M.MDRQError) as e:
+            srv.submit(wl.queries[0])
+        assert e.value.status == M.E_NOMEM
+        assert srv.stop() == M.E_NOMEM
+    # the table itself stays usable
+    with M.Table(_device(wl.columns)) as t:
+        assert np.array_equal(M.as_uint32_numpy(t.query(wl.queries[0])), oracle.mdrq(wl.columns, wl.queries[0]))

@@ -207,16 +207,18 @@ def verify_with_oracle(columns, queries, ids, off, which, nthreads: int) -> dict
             "seconds": time.perf_counter() - t0}
 
 
-def early_break_bytes(table, cols_dev, queries, n: int) -> float:
+def early_break_bytes(table, cols_dev, queries, n: int, granule: int = 32):
     """Algorithmic bytes of the plain scan of ``queries`` with its early break (Sec.
     2.2.4) at DRAM-sector granularity: for each query, in the order the scan evaluates
     its predicates (``mdrq_explain_query``), 32 B for every 32-byte sector (8 rows) of
     the column that still holds a row satisfying all earlier predicates, plus 4 B per
-    answer id. Counted on the GPU with plain tensor operations, outside any timed
+    answer id (``granule``: the same count at a coarser fetch size, for comparison with
+    the DRAM traffic). Counted on the GPU with plain tensor operations, outside any timed
     region; it does not depend on the kernel (two lanes of 4 rows share a sector, and
     a lane whose rows have all failed issues no load)."""
     import torch
-    pad = (-n) % 8
+    rows = granule // 4
+    pad = (-n) % rows
     total = 0.0
     for q in queries:
         empty, plan = table.explain(q)
@@ -226,11 +228,11 @@ def early_break_bytes(table, cols_dev, queries, n: int) -> float:
         for (j, lo, hi) in plan:
             x = cols_dev[j]
             if alive is None:
-                sectors = (n + 7) // 8
+                sectors = (n + rows - 1) // rows
             else:
                 a = torch.cat([alive, alive.new_zeros(pad)]) if pad else alive
-                sectors = int(a.view(-1, 8).any(dim=1).sum())
-            total += 32.0 * sectors
+                sectors = int(a.view(-1, rows).any(dim=1).sum())
+            total += float(granule) * sectors
             lo_t = torch.tensor(lo, dtype=x.dtype, device=x.device)
             hi_t = torch.tensor(hi, dtype=x.dtype, device=x.device)
             m = (x >= lo_t) & (x <= hi_t)
@@ -758,9 +760,21 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
         bvalue = world * nq * args.steps / (bms / 1e3)
         batched = {"value": bvalue, "unit": UNIT, "ms_per_step": bms / args.steps,
                    "speedup_vs_plain": bvalue / value,
-                   "mode": "shared scan: each constrained column read once per chunk of queries, "
-                           "per-row query sets from elementary-interval tables, two passes (count, write)",
+                   "mode": "shared scan: each constrained column encoded once per batch into 16-bit "
+                           "codes, per-row query sets of each chunk of up to 128 queries from "
+                           "elementary-interval tables looked up by code, two passes (count, write)",
                    "answers_identical_to_plain": same_answers(off_ref, ids_ref, off_b, ids)}
+        # the same batch with the values searched per chunk instead of encoded once
+        table.set_shared_codes(False)
+        for _ in range(args.warmup):
+            step()
+        ids.fill_(-1)
+        vms, off_v = timed_steps(torch, stream, step, args.steps, barrier)
+        vms = shards.max_over_ranks(vms)
+        batched["values_searched"] = {"value": world * nq * args.steps / (vms / 1e3), "unit": UNIT,
+                                      "ms_per_step": vms / args.steps,
+                                      "answers_identical_to_plain": same_answers(off_ref, ids_ref, off_v, ids)}
+        table.set_shared_codes(True)
         # autotuned shape (untimed search), then the tuned batch as a prepared graph
         t_tune = time.perf_counter()
         tune = table.autotune(wl.queries)
@@ -802,21 +816,29 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
                 raise mdrq.MDRQError(st, "mdrq_query_batch")
             return o
 
-        step_host()
-        barrier()
-        torch.cuda.synchronize()
-        table.scan_timing(True)
-        table.scan_timing_read(reset=True)
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            off_h = step_host()
-        torch.cuda.synchronize()
-        barrier()
-        e2e_s = time.perf_counter() - t0
-        e2e_kernel = table.scan_timing_read(reset=True)
-        table.scan_timing(False)
-        e2e_s = shards.max_over_ranks(e2e_s)
-        back = host_ids[:total_ids].to("cuda")
+        def e2e_run(host_mode):
+            table.set_host_answers(host_mode)
+            step_host()
+            barrier()
+            torch.cuda.synchronize()
+            table.scan_timing(True)
+            table.scan_timing_read(reset=True)
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                off_h = step_host()
+            torch.cuda.synchronize()
+            barrier()
+            secs = shards.max_over_ranks(time.perf_counter() - t0)
+            kern = table.scan_timing_read(reset=True)
+            table.scan_timing(False)
+            back = host_ids[:total_ids].to("cuda")
+            same = same_answers(off_ref, ids_ref, off_h, back)
+            del back
+            return secs, kern, same
+
+        e2e_s, e2e_kernel, same_d = e2e_run(mdrq.HOST_AUTO)
+        st_s, st_kernel, same_s = e2e_run(mdrq.HOST_STAGED)
+        table.set_host_answers(mdrq.HOST_AUTO)
         npreds = sum(len(q) for q in wl.queries)
         e2e = {"value": world * nq * args.steps / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": 16 * npreds + 16 * nq,
@@ -824,14 +846,21 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
                "wall_ms_per_step": 1e3 * e2e_s / args.steps,
                "scan_kernel_ms_per_step": e2e_kernel["ms"] / args.steps,
                "launches_per_step": e2e_kernel["scan_launches"] / args.steps,
-               "d2h_gbs_one_copy": d2h_gbs(torch),
-               "answers_identical_to_plain": same_answers(off_ref, ids_ref, off_h, back),
+               "answers_identical_to_plain": same_d,
                "path": "mdrq_query_batch with host query descriptors and a pinned host answer "
-                       "buffer (each launch's ids copied while the next runs); host wall clock",
+                       "buffer, which the scan writes itself over the CPU-GPU link; host wall clock",
                "bytes": "h2d: the host descriptors passed to the call (16 B per predicate and per "
                         "query; the library stages them as one copy of 16 B per query and 32 B per "
-                        "kept predicate); d2h: the offsets and every id"}
-        del back, host_ids
+                        "kept predicate); d2h: the offsets and every id",
+               "staged": {"value": world * nq * args.steps / st_s, "unit": UNIT,
+                          "wall_ms_per_step": 1e3 * st_s / args.steps,
+                          "scan_kernel_ms_per_step": st_kernel["ms"] / args.steps,
+                          "launches_per_step": st_kernel["scan_launches"] / args.steps,
+                          "d2h_gbs_one_copy_alone": d2h_gbs(torch),
+                          "answers_identical_to_plain": same_s,
+                          "path": "the same call with the ids staged in device memory and copied "
+                                  "out per launch on a second stream (mdrq_set_host_answers STAGED)"}}
+        del host_ids
 
     # ---- roofline of the scan kernel: bytes / event-timed launch duration
     peaks = measured_peaks()
@@ -847,11 +876,13 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     avg_launch_s = timing["ms"] / 1e3 / launches
     if zone_rows is None:
         alg_per_launch = early_break_bytes(table, cols_dev, wl.queries, wl.n)
+        alg64_per_launch = early_break_bytes(table, cols_dev, wl.queries, wl.n, granule=64)
         alg_rule = ("early-break bytes: per query, in the scan's predicate order, 32 B per 32-byte "
                     "sector (8 rows) of each evaluated column that still holds a row satisfying "
                     "the earlier predicates, plus 4 B per id")
     else:
         alg_per_launch, alg_rule = dense_per_launch, dense_rule
+        alg64_per_launch = None
     achieved = alg_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
     effective = dense_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
     traffic, ratio = dram_traffic_per_launch(args.workload, alg_per_launch)
@@ -869,6 +900,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
                 "dram_gbs_moved": traffic / avg_launch_s / 1e9 if traffic and avg_launch_s > 0 else None,
                 "dram_frac_moved": (traffic / avg_launch_s / 1e9 / peaks["hbm_gbs"]
                                     if traffic and avg_launch_s > 0 else None),
+                "early_break_bytes_64B_fetches": alg64_per_launch,
                 "effective_gbs": effective, "effective_frac": effective / peaks["hbm_gbs"],
                 "effective_rule": "dense equivalent, not bytes moved: " + dense_rule}
 

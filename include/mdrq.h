@@ -110,15 +110,16 @@ int mdrq_load_columns(const void *const *cols, const int32_t *types, uint32_t d,
  *  preds, npreds  host array of predicates; npreds = 0 is the full-domain query
  *                 (all n ids). At most 128 distinct dimensions may be constrained.
  *  ids            output, `capacity` uint32 slots; device memory when
- *                 ids_on_device = 1, host memory when 0. Host answers go through a
- *                 device staging buffer of `capacity` ids that the table keeps; a plain
- *                 batch that scans at least 2 GiB of columns runs as several launches
+ *                 ids_on_device = 1, host memory when 0. Host answers in page-locked
+ *                 memory (cudaHostAlloc / cudaHostRegister, a pinned torch tensor) are
+ *                 written by the scan kernels themselves over the CPU-GPU link (see
+ *                 mdrq_set_host_answers). Other host memory goes through a device
+ *                 staging buffer of `capacity` ids that the table keeps; a plain batch
+ *                 that scans at least 2 GiB of columns then runs as several launches
  *                 (up to 16, of equal query counts, on average at least 1 GiB of
- *                 columns each) and the ids of each are copied
- *                 out (on a second stream) while the next one runs; a smaller batch is
- *                 one launch followed by one copy. Page-locked host memory
- *                 (cudaHostAlloc / cudaHostRegister, a pinned torch tensor) copies
- *                 fastest.
+ *                 columns each) and the ids of each are copied out (on a second
+ *                 stream) while the next one runs; a smaller batch is one launch
+ *                 followed by one copy.
  *  count          host; receives the length of the answer (also when it exceeds
  *                 capacity).
  *
@@ -144,6 +145,23 @@ int mdrq_query(mdrq_table *t, const mdrq_pred *preds, uint32_t npreds, uint32_t 
  */
 int mdrq_query_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids,
                      uint64_t capacity, uint64_t *offsets, int ids_on_device, void *stream);
+
+/*
+ * mdrq_set_host_answers — how answers bound for host memory (ids_on_device = 0) get
+ * there; the paper's answers stay in the memory of the machine that scans (Sec. 7.1).
+ *  MDRQ_HOST_AUTO    (default) written by the scan itself when the buffer is page-locked
+ *                    and mapped into the device's address space (on a GPU that shares a
+ *                    coherent link with the CPU, as on GB300, the stores cross that link
+ *                    at the scan's pace), staged otherwise;
+ *  MDRQ_HOST_STAGED  always through the device staging buffer and copies;
+ *  MDRQ_HOST_DIRECT  always written by the scan; calls with a buffer that is not
+ *                    page-locked fail with MDRQ_E_INVAL.
+ * Answers are identical in every mode. Errors: MDRQ_E_INVAL (t NULL, unknown mode).
+ */
+#define MDRQ_HOST_AUTO 0
+#define MDRQ_HOST_STAGED 1
+#define MDRQ_HOST_DIRECT 2
+int mdrq_set_host_answers(mdrq_table *t, int mode);
 
 /* mdrq_free — release a table and its device memory (not caller-owned columns). NULL is
  * a no-op. Synchronises the device work the table still has in flight. */
@@ -509,6 +527,17 @@ int mdrq_set_shared_config(mdrq_table *t, uint32_t unit_rows, uint32_t image_kib
  * the write pass. UINT64_MAX restores the default (32 GiB, and at most a quarter of the
  * free device memory). Memory already held is kept. Errors: MDRQ_E_INVAL (t NULL). */
 int mdrq_set_shared_bits_budget(mdrq_table *t, uint64_t max_bytes);
+
+/* mdrq_set_shared_codes — whether the shared scan may encode its columns (enable = 1,
+ * the default): per batch, each column some query constrains is encoded once into
+ * 16-bit codes, code(x) = the number of the batch's interval end points (over all
+ * chunks) at or below x, and each chunk finds a row's elementary interval by a lookup
+ * of its code instead of a search of the value. Used when every column has at most
+ * 16,383 end points, each chunk's lookup tables fit its shared memory, and the codes
+ * (2 bytes per row and encoded column, kept with the table) fit 32 GB and a quarter of
+ * the free device memory; otherwise the values are searched. enable = 0 always
+ * searches. Answers are identical either way. Errors: MDRQ_E_INVAL (t NULL). */
+int mdrq_set_shared_codes(mdrq_table *t, int enable);
 int mdrq_autotune(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, void *stream, mdrq_tuning *out);
 
 /*

@@ -186,6 +186,14 @@ int mdrq_set_shared_bits_budget(mdrq_table *t, uint64_t max_bytes)
     return MDRQ_OK;
 }
 
+int mdrq_set_shared_codes(mdrq_table *t, int enable)
+{
+    if (!t)
+        return MDRQ_E_INVAL;
+    t->shared_coded = enable != 0;
+    return MDRQ_OK;
+}
+
 int mdrq_autotune(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, void *stream, mdrq_tuning *out)
 {
     if (!t || !out || (nq > 0 && !qs))

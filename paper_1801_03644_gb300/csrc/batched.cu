@@ -21,6 +21,13 @@
 //    word loads from shared memory per row and column, independent of how many
 //    predicates the chunk has.
 //
+// Coded columns: when the batch fits, each constrained column is first encoded once for
+// the whole batch into 16-bit codes, code(x) = #{cut points of the batch <= x} over the
+// union of all chunks' cut points of that column (one binary search per row and
+// column instead of one per row, column and chunk). A chunk's elementary interval is
+// then a function of the code, held as a lookup table in its image: e = L[code]. The
+// passes read 2-byte codes instead of 4-byte values and look up instead of searching.
+//
 // Output is CSR over the batch, ascending per query, in two passes over the table:
 // pass 1 counts each query's matches per warp unit of consecutive rows, an exclusive
 // scan per query (and over the queries) turns the counts into write offsets, and
@@ -63,6 +70,7 @@ constexpr uint32_t kBlockStride = kBlockSteps + 1;  // words per query in the bl
 constexpr uint32_t kLanesPerWord = 32 / kBlockSteps;  // lanes sharing one step's word in a flush
 constexpr uint32_t kLaneBits = kBlockSteps == 32 ? 0xffffffffu : (1u << kBlockSteps) - 1u;
 constexpr size_t kBlockBufferBytes = (size_t)kSharedWarps * kSharedG * 32 * kBlockStride * 4;
+constexpr uint32_t kCodedMaxCuts = 16383;        // coded columns: most cut points of one column
 constexpr int kBallotQueries = 2;                // write pass: up to this many matching queries
                                                  // per step are ranked by ballots, more by a
                                                  // bit-matrix transpose
@@ -70,9 +78,12 @@ constexpr int kBallotQueries = 2;                // write pass: up to this many 
 // One column of a chunk's shared-memory image (kColWords words). The first 16 bytes are
 // what the passes read for every row (one 128-bit shared-memory load):
 //   w0: image word of the cut points (bits 0-15), their number m (bits 16-24), the
-//       search hint's walk length (bits 25-28), type (bit 31: 1 = int32);
+//       search hint's walk length (bits 25-28), type (bit 31: 1 = int32); for a coded
+//       column, bits 0-15 locate the code lookup table L, of bytes when bit 30 is set
+//       (the chunk has at most 255 cut points on the column) or else of 16-bit entries;
 //   w1: image word of the tables (bits 0-15) and of the hint (bits 16-31);
 //   w2, w3: the hint's bucket base and scale (float; scale 0: no hint).
+// col: the device column, or for a coded column its 16-bit codes.
 struct ChunkCol {
     uint32_t w0, w1;
     float base;           // search hint: bucket trunc((x - base) * scale), clamped
@@ -163,6 +174,48 @@ __device__ __forceinline__ uint32_t interval_of(const uint32_t *img, uint4 hot, 
     return pos;
 }
 
+// A coded column's elementary interval: the chunk's lookup table entry of the code
+__device__ __forceinline__ uint32_t coded_interval(const uint32_t *img, uint4 hot, uint32_t code)
+{
+    const uint32_t *lut = img + (hot.x & 0xffffu);
+    if (hot.x & (1u << 30))
+        return reinterpret_cast<const unsigned char *>(lut)[code];
+    return reinterpret_cast<const unsigned short *>(lut)[code];
+}
+
+// Row r's value of a chunk column (its 16-bit code when CODED), read through the
+// read-only path
+template <bool CODED>
+__device__ __forceinline__ uint32_t column_value(const uint32_t *desc, uint64_t r)
+{
+    const uint32_t *col = reinterpret_cast<const ChunkCol *>(desc)->col;
+    if (CODED)
+        return __ldg(reinterpret_cast<const unsigned short *>(col) + r);
+    return __ldg(col + r);
+}
+
+// The batch's codes of one column: code(x) = #{cut points <= x} over the sorted cut
+// points cut[0 .. m) of every chunk (m <= kCodedMaxCuts), by the fixed-step search.
+struct EncodeCol {
+    const uint32_t *col;      // device column
+    unsigned short *codes;    // n codes
+    uint64_t cut_off;         // plan word of its cut points
+    uint32_t m;
+    uint32_t type;
+};
+
+__global__ void __launch_bounds__(256) mdrq_shared_encode_kernel(const EncodeCol *ec, const uint32_t *plan,
+                                                                 uint64_t n)
+{
+    extern __shared__ uint32_t s_cut[];
+    const EncodeCol c = ec[blockIdx.y];
+    for (uint32_t i = threadIdx.x; i < c.m; i += blockDim.x)
+        s_cut[i] = plan[c.cut_off + i];
+    __syncthreads();
+    for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x)
+        c.codes[r] = (unsigned short)elementary_interval(s_cut, c.m, __ldg(c.col + r), c.type);
+}
+
 // T[e][g] for every elementary interval of every (chunk, column): bit i of word g is
 // set when query 32g + i of the chunk accepts that interval. Block (chunk, column).
 __global__ void __launch_bounds__(256) mdrq_shared_tables_kernel(SharedParams p, uint32_t max_cols)
@@ -226,7 +279,9 @@ __device__ __forceinline__ void flush_counts(uint32_t (&plane)[kSharedG][kCountP
 // Pass 2 (WRITE = true): the ids, at qbase[q] + counts[q][unit] (exclusive prefix).
 // CACHED: pass 1 also stores every row's 128 query bits of the chunk (16 bytes per row
 // and chunk) and pass 2 reads them instead of evaluating the columns again.
-template <bool WRITE, bool CACHED>
+// CODED: the chunk columns are the batch's 16-bit codes (mdrq_shared_encode_kernel),
+// each chunk's elementary interval a table lookup.
+template <bool WRITE, bool CACHED, bool CODED>
 // (64 registers, so that four blocks fit an SM: measured faster than 80 and three)
 __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(SharedParams p)
 {
@@ -297,7 +352,7 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
             const uint64_t r = r_begin + lane;
             xn[i] = 0u;
             if (i < (int)npre && r < r_end)
-                xn[i] = __ldg(reinterpret_cast<const ChunkCol *>(s_img + i * kColWords)->col + r);
+                xn[i] = column_value<CODED>(s_img + i * kColWords, r);
         }
         // cached write pass: this warp's block buffer of transposed step matrices
         uint32_t *tb = s_img + (size_t)warp * kSharedG * 32 * kBlockStride;
@@ -322,7 +377,7 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
                     const uint64_t rn = r + 32;
                     xn[i] = 0u;
                     if (i < (int)npre && rn < r_end)
-                        xn[i] = __ldg(reinterpret_cast<const ChunkCol *>(s_img + i * kColWords)->col + rn);
+                        xn[i] = column_value<CODED>(s_img + i * kColWords, rn);
                 }
 #pragma unroll
                 for (int g = 0; g < kSharedG; ++g)
@@ -331,7 +386,7 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
                 for (int i = 0; i < kPrefetchCols; ++i) {
                     if (i < (int)npre) {
                         const uint4 hot = *reinterpret_cast<const uint4 *>(s_img + i * kColWords);
-                        const uint32_t e = interval_of(s_img, hot, x[i]);
+                        const uint32_t e = CODED ? coded_interval(s_img, hot, x[i]) : interval_of(s_img, hot, x[i]);
                         const uint4 t = *reinterpret_cast<const uint4 *>(s_img + (hot.y & 0xffffu) + e * kSharedG);
                         mask[0] &= t.x;
                         mask[1] &= t.y;
@@ -346,13 +401,14 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
                     for (int i = 0; i < kPrefetchCols; ++i) {
                         y[i] = 0u;
                         if (a0 + i < h.ncols && valid)
-                            y[i] = __ldg(reinterpret_cast<const ChunkCol *>(s_img + (a0 + i) * kColWords)->col + r);
+                            y[i] = column_value<CODED>(s_img + (a0 + i) * kColWords, r);
                     }
 #pragma unroll
                     for (int i = 0; i < kPrefetchCols; ++i) {
                         if (a0 + i < h.ncols) {
                             const uint4 hot = *reinterpret_cast<const uint4 *>(s_img + (a0 + i) * kColWords);
-                            const uint32_t e = interval_of(s_img, hot, y[i]);
+                            const uint32_t e = CODED ? coded_interval(s_img, hot, y[i])
+                                                     : interval_of(s_img, hot, y[i]);
                             const uint4 t = *reinterpret_cast<const uint4 *>(s_img + (hot.y & 0xffffu) + e * kSharedG);
                             mask[0] &= t.x;
                             mask[1] &= t.y;
@@ -604,6 +660,11 @@ struct SharedScanState {
     bool smem_attr = false;            // pass kernels opted in to kMaxImageWords
     uint4 *masks = nullptr;            // row masks between the passes
     size_t masks_cap = 0;
+    unsigned short *codes = nullptr;   // coded columns: 16-bit codes, one column after another
+    size_t codes_cap = 0;
+    EncodeCol *ecols = nullptr;        // coded columns to encode
+    size_t ecols_cap = 0;
+    bool coded = false;                // the prepared batch uses coded columns
     // (image words | cached << 31, (count-pass grid, write-pass grid))
     std::vector<std::pair<uint32_t, std::pair<int, int>>> grid_for_words;
     // the batch prepared by shared_scan_count, for shared_scan_write
@@ -641,6 +702,28 @@ uint32_t to_bits(double v, int32_t type)
 
 }  // namespace
 
+namespace {
+
+using PassKernel = void (*)(SharedParams);
+
+// pass 1 of a batch (stores row masks when cached; reads codes when coded)
+PassKernel count_kernel(bool cached, bool coded)
+{
+    if (coded)
+        return cached ? mdrq_shared_pass_kernel<false, true, true> : mdrq_shared_pass_kernel<false, false, true>;
+    return cached ? mdrq_shared_pass_kernel<false, true, false> : mdrq_shared_pass_kernel<false, false, false>;
+}
+
+// pass 2: from the stored row masks when cached, else evaluating the columns again
+PassKernel write_kernel(bool cached, bool coded)
+{
+    if (cached)
+        return mdrq_shared_pass_kernel<true, true, false>;
+    return coded ? mdrq_shared_pass_kernel<true, false, true> : mdrq_shared_pass_kernel<true, false, false>;
+}
+
+}  // namespace
+
 SharedScanState *shared_state_new() { return new (std::nothrow) SharedScanState(); }
 
 void shared_state_free(SharedScanState *S)
@@ -654,6 +737,8 @@ void shared_state_free(SharedScanState *S)
     cudaFree(S->totals);
     cudaFree(S->qbase);
     cudaFree(S->masks);
+    cudaFree(S->codes);
+    cudaFree(S->ecols);
     cudaFreeHost(S->stage);
     delete S;
 }
@@ -705,17 +790,15 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
         }
     }
 
-    // ---- per chunk: columns, cut points, intervals; laid out as plan words
-    std::vector<ChunkHdr> hdrs(chunks.size());
-    std::vector<uint32_t> plan;
-    plan.reserve(1 << 16);
-    uint32_t max_cols = 1;
-    uint32_t max_img = 4;  // words of the largest chunk image: the launches' shared memory
+    // ---- per chunk: columns and cut points
+    std::vector<std::vector<ColPlan>> chunk_cols(chunks.size());
+    std::vector<std::vector<int>> chunk_slot(chunks.size());
     for (size_t ci = 0; ci < chunks.size(); ++ci) {
         const Chunk &ch = chunks[ci];
         // columns in first-use order, with their cut points
-        std::vector<int> slot(t->d, -1);
-        std::vector<ColPlan> cols;
+        std::vector<int> &slot = chunk_slot[ci];
+        slot.assign(t->d, -1);
+        std::vector<ColPlan> &cols = chunk_cols[ci];
         for (uint32_t k = 0; k < ch.nq; ++k) {
             const EncodedQuery &e = enc[live[ch.q0 + k]];
             for (size_t i = 0; i < e.dims.size(); ++i) {
@@ -737,109 +820,219 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
             std::sort(cp.cuts.begin(), cp.cuts.end());
             cp.cuts.erase(std::unique(cp.cuts.begin(), cp.cuts.end()), cp.cuts.end());
         }
+    }
+
+    // ---- coded columns: the union of every chunk's cut points per column; used when
+    // each union stays within kCodedMaxCuts, every chunk's coded image fits the largest
+    // image budget and the codes (2 bytes per row and column) fit the device
+    std::vector<std::vector<double>> gcuts(t->d);
+    std::vector<int> gslot(t->d, -1);
+    std::vector<uint32_t> gdims;
+    for (const auto &cols : chunk_cols)
+        for (const ColPlan &cp : cols) {
+            if (gslot[cp.dim] < 0) {
+                gslot[cp.dim] = (int)gdims.size();
+                gdims.push_back(cp.dim);
+            }
+            gcuts[cp.dim].insert(gcuts[cp.dim].end(), cp.cuts.begin(), cp.cuts.end());
+        }
+    bool coded = t->shared_coded && !gdims.empty();
+    for (uint32_t j : gdims) {
+        std::vector<double> &g = gcuts[j];
+        std::sort(g.begin(), g.end());
+        g.erase(std::unique(g.begin(), g.end()), g.end());
+        coded = coded && g.size() <= kCodedMaxCuts;
+    }
+    // a column's lookup table: bytes when the chunk has at most 255 cut points on it
+    auto lut_words = [&](const ColPlan &cp) -> uint64_t {
+        const uint64_t entries = gcuts[cp.dim].size() + 1;
+        return cp.cuts.size() <= 255 ? (entries + 3) / 4 : (entries + 1) / 2;
+    };
+    auto coded_image_words = [&](const std::vector<ColPlan> &cols) {
+        uint64_t w = (uint64_t)cols.size() * kColWords;
+        for (const ColPlan &cp : cols)
+            w += lut_words(cp);
+        w = (w + 3) & ~3ull;
+        for (const ColPlan &cp : cols)
+            w += (uint64_t)(cp.cuts.size() + 1) * kSharedG;
+        return (w + 3) & ~3ull;
+    };
+    for (const auto &cols : chunk_cols)
+        coded = coded && coded_image_words(cols) <= std::min<uint64_t>(kMaxImageWords, 0xffff);
+    if (coded) {
+        const uint64_t code_bytes = (uint64_t)gdims.size() * t->n * 2;
+        size_t free_b = 0, total_b = 0;
+        coded = code_bytes <= kMaskBudgetBytes &&
+                (S.codes_cap >= code_bytes ||
+                 (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && code_bytes <= free_b / 4 &&
+                  grow_device((void **)&S.codes, &S.codes_cap, (size_t)code_bytes) == MDRQ_OK));
+        (void)cudaGetLastError();
+    }
+
+    // ---- per chunk: images and intervals, laid out as plan words
+    std::vector<ChunkHdr> hdrs(chunks.size());
+    std::vector<uint32_t> plan;
+    plan.reserve(1 << 16);
+    uint32_t max_cols = 1;
+    uint32_t max_img = 4;  // words of the largest chunk image: the launches' shared memory
+    for (size_t ci = 0; ci < chunks.size(); ++ci) {
+        const Chunk &ch = chunks[ci];
+        const std::vector<int> &slot = chunk_slot[ci];
+        const std::vector<ColPlan> &cols = chunk_cols[ci];
         const uint32_t ncols = (uint32_t)cols.size();
         max_cols = std::max(max_cols, ncols);
-        // image: ChunkCol[ncols], hints, cut points, (pad to 4), tables ((m + 1) * G words each)
-        while (plan.size() % 4)
-            plan.push_back(0);
-        const uint64_t img_off = plan.size();
-        uint32_t w = ncols * kColWords;
-        struct ColLayout {
-            uint32_t type = 0, m = 0, cut_off = 0, tab_off = 0, hint_off = 0, steps = 0;
-            float base = 0.0f, scale = 0.0f;
-            const uint32_t *col = nullptr;
-        };
-        std::vector<ColLayout> cl(ncols);
-        std::vector<std::vector<uint32_t>> hint(ncols);
-        for (uint32_t a = 0; a < ncols; ++a) {
-            const ColumnInfo &ci_ = t->cols[cols[a].dim];
-            cl[a].col = static_cast<const uint32_t *>(ci_.ptr);
-            cl[a].type = (uint32_t)ci_.type;
-            cl[a].m = (uint32_t)cols[a].cuts.size();
-            // search hint over [min, max] in kHintBuckets equal value buckets, with the
-            // bucket function the device evaluates (float: trunc((x - base) * scale),
-            // clamped): bucket b starts at the number of cuts in lower buckets, and the
-            // walk covers the most cuts one bucket holds; used when that stays short
-            const std::vector<double> &cut = cols[a].cuts;
-            const double mn = bound_value(ci_.min_bits, ci_.type), mx = bound_value(ci_.max_bits, ci_.type);
-            const double range = mx - mn;
-            const float base = (float)mn, scale = (float)(kHintBuckets / range);
-            if (std::isfinite(range) && range > 0 && cl[a].m > 8 && std::isfinite(base) && std::isfinite(scale) &&
-                scale > 0.0f) {
-                auto bucket = [&](double v) {
-                    const float xf = cl[a].type == MDRQ_F32 ? (float)v : (float)(int32_t)v;
-                    const float tq = (xf - base) * scale;
-                    if (!(tq >= 1.0f))
-                        return 0u;  // negative, below one, or NaN
-                    if (tq >= (float)(kHintBuckets - 1))
-                        return kHintBuckets - 1;
-                    return (uint32_t)tq;  // truncation, as __float2int_rz
-                };
-                std::vector<uint32_t> in_bucket(kHintBuckets, 0);
-                for (double c : cut)
-                    ++in_bucket[bucket(c)];
-                uint32_t steps = 0;
-                for (uint32_t b = 0; b < kHintBuckets; ++b)
-                    steps = std::max(steps, in_bucket[b]);
-                if (steps <= kMaxHintSteps) {
-                    cl[a].base = base;
-                    cl[a].scale = scale;
-                    cl[a].steps = steps;
-                    hint[a].assign(kHintBuckets / 2, 0);
-                    uint32_t below = 0;
-                    for (uint32_t b = 0; b < kHintBuckets; ++b) {
-                        hint[a][b >> 1] |= below << ((b & 1) * 16);
-                        below += in_bucket[b];
+        uint64_t img_off;
+        uint32_t img_words;
+        if (coded) {
+            // image: ChunkCol[ncols], lookup tables (code -> this chunk's elementary
+            // interval, bytes or 16-bit entries), (pad to 4), tables
+            while (plan.size() % 4)
+                plan.push_back(0);
+            img_off = plan.size();
+            img_words = (uint32_t)coded_image_words(cols);
+            plan.resize(img_off + img_words, 0);
+            uint32_t w = ncols * kColWords;
+            std::vector<uint32_t> lut_off(ncols), tab_off(ncols);
+            for (uint32_t a = 0; a < ncols; ++a) {
+                lut_off[a] = w;
+                w += (uint32_t)lut_words(cols[a]);
+            }
+            w = (w + 3) & ~3u;
+            for (uint32_t a = 0; a < ncols; ++a) {
+                tab_off[a] = w;
+                w += (uint32_t)(cols[a].cuts.size() + 1) * kSharedG;
+            }
+            for (uint32_t a = 0; a < ncols; ++a) {
+                const uint32_t j = cols[a].dim;
+                const std::vector<double> &g = gcuts[j], &cut = cols[a].cuts;
+                ChunkCol cc;
+                std::memset(&cc, 0, sizeof(cc));
+                const bool bytes = cut.size() <= 255;
+                cc.w0 = lut_off[a] | ((uint32_t)cut.size() << 16) | ((bytes ? 1u : 0u) << 30) |
+                        ((t->cols[j].type == MDRQ_I32 ? 1u : 0u) << 31);
+                cc.w1 = tab_off[a];
+                cc.col = reinterpret_cast<const uint32_t *>(S.codes + (size_t)gslot[j] * t->n);
+                std::memcpy(&plan[img_off + a * kColWords], &cc, sizeof(ChunkCol));
+                // code k: the values in [g[k-1], g[k]); the chunk's cut points at or
+                // below them are its cut points among g[0 .. k)
+                uint32_t e = 0;
+                size_t ci2 = 0;
+                for (size_t k = 0; k <= g.size(); ++k) {
+                    if (k > 0) {
+                        while (ci2 < cut.size() && cut[ci2] <= g[k - 1])
+                            ++ci2;
+                        e = (uint32_t)ci2;
+                    }
+                    if (bytes)
+                        plan[img_off + lut_off[a] + k / 4] |= e << (8 * (k & 3));
+                    else
+                        plan[img_off + lut_off[a] + k / 2] |= e << (16 * (k & 1));
+                }
+            }
+            max_img = std::max(max_img, img_words);
+        } else {
+            // image: ChunkCol[ncols], hints, cut points, (pad to 4), tables ((m + 1) * G words each)
+            while (plan.size() % 4)
+                plan.push_back(0);
+            img_off = plan.size();
+            uint32_t w = ncols * kColWords;
+            struct ColLayout {
+                uint32_t type = 0, m = 0, cut_off = 0, tab_off = 0, hint_off = 0, steps = 0;
+                float base = 0.0f, scale = 0.0f;
+                const uint32_t *col = nullptr;
+            };
+            std::vector<ColLayout> cl(ncols);
+            std::vector<std::vector<uint32_t>> hint(ncols);
+            for (uint32_t a = 0; a < ncols; ++a) {
+                const ColumnInfo &ci_ = t->cols[cols[a].dim];
+                cl[a].col = static_cast<const uint32_t *>(ci_.ptr);
+                cl[a].type = (uint32_t)ci_.type;
+                cl[a].m = (uint32_t)cols[a].cuts.size();
+                // search hint over [min, max] in kHintBuckets equal value buckets, with the
+                // bucket function the device evaluates (float: trunc((x - base) * scale),
+                // clamped): bucket b starts at the number of cuts in lower buckets, and the
+                // walk covers the most cuts one bucket holds; used when that stays short
+                const std::vector<double> &cut = cols[a].cuts;
+                const double mn = bound_value(ci_.min_bits, ci_.type), mx = bound_value(ci_.max_bits, ci_.type);
+                const double range = mx - mn;
+                const float base = (float)mn, scale = (float)(kHintBuckets / range);
+                if (std::isfinite(range) && range > 0 && cl[a].m > 8 && std::isfinite(base) && std::isfinite(scale) &&
+                    scale > 0.0f) {
+                    auto bucket = [&](double v) {
+                        const float xf = cl[a].type == MDRQ_F32 ? (float)v : (float)(int32_t)v;
+                        const float tq = (xf - base) * scale;
+                        if (!(tq >= 1.0f))
+                            return 0u;  // negative, below one, or NaN
+                        if (tq >= (float)(kHintBuckets - 1))
+                            return kHintBuckets - 1;
+                        return (uint32_t)tq;  // truncation, as __float2int_rz
+                    };
+                    std::vector<uint32_t> in_bucket(kHintBuckets, 0);
+                    for (double c : cut)
+                        ++in_bucket[bucket(c)];
+                    uint32_t steps = 0;
+                    for (uint32_t b = 0; b < kHintBuckets; ++b)
+                        steps = std::max(steps, in_bucket[b]);
+                    if (steps <= kMaxHintSteps) {
+                        cl[a].base = base;
+                        cl[a].scale = scale;
+                        cl[a].steps = steps;
+                        hint[a].assign(kHintBuckets / 2, 0);
+                        uint32_t below = 0;
+                        for (uint32_t b = 0; b < kHintBuckets; ++b) {
+                            hint[a][b >> 1] |= below << ((b & 1) * 16);
+                            below += in_bucket[b];
+                        }
                     }
                 }
             }
-        }
-        // hints where the image budget leaves room for them (the rest search by bisection)
-        {
-            uint64_t base_words = (uint64_t)ncols * kColWords + 8;
-            for (uint32_t a = 0; a < ncols; ++a)
-                base_words += cl[a].m + (uint64_t)(cl[a].m + 1) * kSharedG;
-            for (uint32_t a = 0; a < ncols; ++a) {
-                if (hint[a].empty())
-                    continue;
-                if (base_words + kHintBuckets / 2 > budget) {
-                    hint[a].clear();
-                    cl[a].base = cl[a].scale = 0.0f;
-                    cl[a].steps = 0;
-                    continue;
+            // hints where the image budget leaves room for them (the rest search by bisection)
+            {
+                uint64_t base_words = (uint64_t)ncols * kColWords + 8;
+                for (uint32_t a = 0; a < ncols; ++a)
+                    base_words += cl[a].m + (uint64_t)(cl[a].m + 1) * kSharedG;
+                for (uint32_t a = 0; a < ncols; ++a) {
+                    if (hint[a].empty())
+                        continue;
+                    if (base_words + kHintBuckets / 2 > budget) {
+                        hint[a].clear();
+                        cl[a].base = cl[a].scale = 0.0f;
+                        cl[a].steps = 0;
+                        continue;
+                    }
+                    base_words += kHintBuckets / 2;
+                    cl[a].hint_off = w;
+                    w += kHintBuckets / 2;
                 }
-                base_words += kHintBuckets / 2;
-                cl[a].hint_off = w;
-                w += kHintBuckets / 2;
             }
-        }
-        for (uint32_t a = 0; a < ncols; ++a) {
-            cl[a].cut_off = w;
-            w += cl[a].m;
-        }
-        w = (w + 3) & ~3u;
-        for (uint32_t a = 0; a < ncols; ++a) {
-            cl[a].tab_off = w;
-            w += (cl[a].m + 1) * kSharedG;
-        }
-        const uint32_t img_words = (w + 3) & ~3u;
-        if (img_words > budget || img_words > 0xffffu)
-            return MDRQ_E_INVAL;  // cannot happen: the chunking bounded it
-        max_img = std::max(max_img, img_words);
-        plan.resize(img_off + img_words, 0);
-        for (uint32_t a = 0; a < ncols; ++a) {
-            ChunkCol cc;
-            std::memset(&cc, 0, sizeof(cc));
-            cc.w0 = cl[a].cut_off | (cl[a].m << 16) | (cl[a].steps << 25) | ((cl[a].type == MDRQ_I32 ? 1u : 0u) << 31);
-            cc.w1 = cl[a].tab_off | (cl[a].hint_off << 16);
-            cc.base = cl[a].base;
-            cc.scale = cl[a].scale;
-            cc.col = cl[a].col;
-            std::memcpy(&plan[img_off + a * kColWords], &cc, sizeof(ChunkCol));
-            for (size_t i = 0; i < hint[a].size(); ++i)
-                plan[img_off + cl[a].hint_off + i] = hint[a][i];
-            for (uint32_t i = 0; i < cl[a].m; ++i)
-                plan[img_off + cl[a].cut_off + i] = to_bits(cols[a].cuts[i], (int32_t)cl[a].type);
+            for (uint32_t a = 0; a < ncols; ++a) {
+                cl[a].cut_off = w;
+                w += cl[a].m;
+            }
+            w = (w + 3) & ~3u;
+            for (uint32_t a = 0; a < ncols; ++a) {
+                cl[a].tab_off = w;
+                w += (cl[a].m + 1) * kSharedG;
+            }
+            img_words = (w + 3) & ~3u;
+            if (img_words > budget || img_words > 0xffffu)
+                return MDRQ_E_INVAL;  // cannot happen: the chunking bounded it
+            max_img = std::max(max_img, img_words);
+            plan.resize(img_off + img_words, 0);
+            for (uint32_t a = 0; a < ncols; ++a) {
+                ChunkCol cc;
+                std::memset(&cc, 0, sizeof(cc));
+                cc.w0 = cl[a].cut_off | (cl[a].m << 16) | (cl[a].steps << 25) | ((cl[a].type == MDRQ_I32 ? 1u : 0u) << 31);
+                cc.w1 = cl[a].tab_off | (cl[a].hint_off << 16);
+                cc.base = cl[a].base;
+                cc.scale = cl[a].scale;
+                cc.col = cl[a].col;
+                std::memcpy(&plan[img_off + a * kColWords], &cc, sizeof(ChunkCol));
+                for (size_t i = 0; i < hint[a].size(); ++i)
+                    plan[img_off + cl[a].hint_off + i] = hint[a][i];
+                for (uint32_t i = 0; i < cl[a].m; ++i)
+                    plan[img_off + cl[a].cut_off + i] = to_bits(cols[a].cuts[i], (int32_t)cl[a].type);
+            }
         }
         // intervals: word [a][k] = elo | ehi << 16, the elementary intervals query k accepts on column a
         const uint64_t iv_off = plan.size();
@@ -872,20 +1065,39 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
         h.img_off = img_off;
         h.iv_off = iv_off;
     }
+    // coded columns: each column's sorted cut points, for the encode kernel
+    std::vector<EncodeCol> ecols;
+    uint32_t max_gcuts = 0;
+    if (coded) {
+        for (size_t gi = 0; gi < gdims.size(); ++gi) {
+            const uint32_t j = gdims[gi];
+            EncodeCol ec;
+            ec.col = static_cast<const uint32_t *>(t->cols[j].ptr);
+            ec.codes = S.codes + gi * t->n;
+            ec.cut_off = plan.size();
+            ec.m = (uint32_t)gcuts[j].size();
+            ec.type = (uint32_t)t->cols[j].type;
+            for (double v : gcuts[j])
+                plan.push_back(to_bits(v, t->cols[j].type));
+            max_gcuts = std::max(max_gcuts, ec.m);
+            ecols.push_back(ec);
+        }
+    }
+    S.coded = coded;
 
     // ---- grid shape: the persistent grid at the occupancy of the largest image; enough
     // warp units to fill it (small tables get smaller units), at most kMaxUnitRows rows
     // each, unless the table sets the unit size (mdrq_set_shared_config)
     if (!S.smem_attr) {
         const int most = (int)kMaxImageWords * 4;
-        if (cudaFuncSetAttribute(mdrq_shared_pass_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 most) != cudaSuccess ||
-            cudaFuncSetAttribute(mdrq_shared_pass_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 most) != cudaSuccess ||
-            cudaFuncSetAttribute(mdrq_shared_pass_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 most) != cudaSuccess ||
-            cudaFuncSetAttribute(mdrq_shared_pass_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 most) != cudaSuccess)
+        const PassKernel all[] = {count_kernel(false, false), count_kernel(true, false), count_kernel(false, true),
+                                  count_kernel(true, true),   write_kernel(true, false), write_kernel(false, false),
+                                  write_kernel(false, true)};
+        for (PassKernel k : all)
+            if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, most) != cudaSuccess)
+                return cuda_status(cudaGetLastError());
+        if (cudaFuncSetAttribute(mdrq_shared_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kCodedMaxCuts * 4) != cudaSuccess)
             return cuda_status(cudaGetLastError());
         S.smem_attr = true;
         S.grid_scan = t->sm_count * 2;
@@ -906,7 +1118,7 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
     const size_t smem_write = cached ? kBlockBufferBytes : smem;
     // persistent grids of the two passes (their register budgets differ)
     int grid_pass = 0, grid_write = 0;
-    const uint32_t key = max_img | (cached ? 0x80000000u : 0u);
+    const uint32_t key = max_img | (cached ? 0x80000000u : 0u) | (coded ? 0x40000000u : 0u);
     for (const auto &g : S.grid_for_words)
         if (g.first == key) {
             grid_pass = g.second.first;
@@ -914,12 +1126,10 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
         }
     if (grid_pass == 0) {
         int bps = 0, bpw = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &bps, cached ? mdrq_shared_pass_kernel<false, true> : mdrq_shared_pass_kernel<false, false>,
-                kSharedThreads, smem) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &bpw, cached ? mdrq_shared_pass_kernel<true, true> : mdrq_shared_pass_kernel<true, false>,
-                kSharedThreads, smem_write) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, count_kernel(cached, coded), kSharedThreads, smem) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpw, write_kernel(cached, coded), kSharedThreads,
+                                                          smem_write) != cudaSuccess)
             return cuda_status(cudaGetLastError());
         grid_pass = t->sm_count * std::max(1, bps);
         grid_write = t->sm_count * std::max(1, bpw);
@@ -939,7 +1149,10 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
     const size_t hdr_bytes = hdrs.size() * sizeof(ChunkHdr);
     const size_t plan_bytes = plan.size() * 4;
     const size_t live_bytes = (size_t)nlive * 4;
+    const size_t ecol_bytes = ecols.size() * sizeof(EncodeCol);
     int st = grow_device((void **)&S.plan, &S.plan_cap, std::max<size_t>(16, plan_bytes));
+    if (st == MDRQ_OK && ecol_bytes)
+        st = grow_device((void **)&S.ecols, &S.ecols_cap, ecol_bytes);
     if (st == MDRQ_OK)
         st = grow_device((void **)&S.chunks, &S.chunks_cap, hdr_bytes);
     if (st == MDRQ_OK)
@@ -951,7 +1164,7 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
     if (st == MDRQ_OK)
         st = grow_device((void **)&S.qbase, &S.qbase_cap, (size_t)nlive * 8);
     if (st == MDRQ_OK)
-        st = grow_pinned((void **)&S.stage, &S.stage_cap, hdr_bytes + plan_bytes + live_bytes);
+        st = grow_pinned((void **)&S.stage, &S.stage_cap, hdr_bytes + plan_bytes + live_bytes + 16 + ecol_bytes);
     if (st != MDRQ_OK)
         return st;
     std::memcpy(S.stage, hdrs.data(), hdr_bytes);
@@ -962,6 +1175,11 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
     MDRQ_TRY_STATUS(cudaMemcpyAsync(S.plan, S.stage + hdr_bytes, plan_bytes, cudaMemcpyHostToDevice, s));
     MDRQ_TRY_STATUS(cudaMemcpyAsync(S.live_orig, S.stage + hdr_bytes + plan_bytes, live_bytes,
                                     cudaMemcpyHostToDevice, s));
+    if (ecol_bytes) {
+        unsigned char *es = S.stage + ((hdr_bytes + plan_bytes + live_bytes + 15) & ~(size_t)15);
+        std::memcpy(es, ecols.data(), ecol_bytes);
+        MDRQ_TRY_STATUS(cudaMemcpyAsync(S.ecols, es, ecol_bytes, cudaMemcpyHostToDevice, s));
+    }
 
     SharedParams p;
     std::memset(&p, 0, sizeof(p));
@@ -982,18 +1200,22 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
 
     const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)grid_pass, p.items);
     mdrq_shared_tables_kernel<<<(uint32_t)hdrs.size() * max_cols, 256, 0, s>>>(p, max_cols);
+    if (coded) {
+        const uint32_t bx = std::max<uint32_t>(1, (uint32_t)t->sm_count * 8 / (uint32_t)ecols.size());
+        mdrq_shared_encode_kernel<<<dim3(bx, (uint32_t)ecols.size()), 256, (size_t)max_gcuts * 4, s>>>(S.ecols, S.plan,
+                                                                                                       t->n);
+    }
     p.masks = cached ? S.masks : nullptr;
-    (cached ? mdrq_shared_pass_kernel<false, true> : mdrq_shared_pass_kernel<false, false>)<<<grid, kSharedThreads,
-                                                                                                smem, s>>>(p);
+    count_kernel(cached, coded)<<<grid, kSharedThreads, smem, s>>>(p);
     mdrq_shared_scan_kernel<<<std::min<uint32_t>(nlive, (uint32_t)S.grid_scan), 1024, 0, s>>>(p);
     MDRQ_TRY_STATUS(cudaGetLastError());
     S.params = p;
     S.grid = (uint32_t)std::min<uint64_t>((uint64_t)grid_write, p.items);
     S.smem = smem_write;
     S.ready = true;
-    t->last_launches += 3;
+    t->last_launches += coded ? 4 : 3;
     if (t->timing)
-        t->acc_kernels += 3;
+        t->acc_kernels += coded ? 4 : 3;
     return MDRQ_OK;
 }
 
@@ -1009,8 +1231,7 @@ int shared_scan_write(mdrq_table *t, SharedScanState &S, uint32_t *ids, uint64_t
     p.capacity = capacity;
     if (csr)
         mdrq_shared_qbase_kernel<<<1, 1024, 0, s>>>(p);
-    (p.masks ? mdrq_shared_pass_kernel<true, true> : mdrq_shared_pass_kernel<true, false>)<<<S.grid, kSharedThreads,
-                                                                                              S.smem, s>>>(p);
+    write_kernel(p.masks != nullptr, S.coded)<<<S.grid, kSharedThreads, S.smem, s>>>(p);
     MDRQ_TRY_STATUS(cudaGetLastError());
     t->last_launches += csr ? 2 : 1;
     if (t->timing)

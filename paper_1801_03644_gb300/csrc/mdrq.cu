@@ -705,7 +705,20 @@ int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, u
     // launch are copied to the host on a second stream while the next launch runs
     uint32_t *out = ids;
     HostSink sink;
-    if (!ids_on_device && capacity > 0) {
+    uint32_t *mapped = nullptr;  // the caller's page-locked buffer as the device sees it
+    if (!ids_on_device && capacity > 0 && t->host_answers != MDRQ_HOST_STAGED) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, ids) == cudaSuccess && a.type == cudaMemoryTypeHost && a.devicePointer)
+            mapped = static_cast<uint32_t *>(a.devicePointer);
+        (void)cudaGetLastError();
+        if (!mapped && t->host_answers == MDRQ_HOST_DIRECT)
+            return MDRQ_E_INVAL;
+    }
+    if (mapped) {
+        // the scan writes the ids into host memory itself, over the CPU-GPU link: no
+        // staging buffer, no copy engine competing with the scan for HBM
+        out = mapped;
+    } else if (!ids_on_device && capacity > 0) {
         st = grow_device((void **)&t->ids_stage, &t->ids_stage_cap, (size_t)capacity * 4);
         if (st == MDRQ_OK && !t->sink_copy) {
             st = cuda_status(cudaStreamCreateWithFlags(&t->sink_copy, cudaStreamNonBlocking));
@@ -1114,6 +1127,14 @@ int mdrq_learn_export(const mdrq_table *t, mdrq_model_desc *desc, uint64_t *knot
                       float *slope, float *mlp, uint32_t capacity)
 {
     return learned_export(t, desc, knot_key, knot_pos, slope, mlp, capacity);
+}
+
+int mdrq_set_host_answers(mdrq_table *t, int mode)
+{
+    if (!t || (mode != MDRQ_HOST_AUTO && mode != MDRQ_HOST_STAGED && mode != MDRQ_HOST_DIRECT))
+        return MDRQ_E_INVAL;
+    t->host_answers = mode;
+    return MDRQ_OK;
 }
 
 int mdrq_set_zone_maps(mdrq_table *t, int mode)

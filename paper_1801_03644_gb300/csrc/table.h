@@ -108,9 +108,11 @@ struct mdrq_table {
     uint32_t shared_image_words = 0;  // shared-memory budget per chunk (0: built-in default)
     uint64_t shared_bits_budget = ~0ull;  // row bits kept between the passes, bytes (~0: default)
     int auto_mode = -1;               // mode AUTO takes for 32+ queries, once measured (-1: rule)
+    bool shared_coded = true;         // shared scan may encode its columns (mdrq_set_shared_codes)
     mdrq::LearnedModel *learned = nullptr;
 
     int zone_mode = MDRQ_ZONES_AUTO;  // mdrq_set_zone_maps
+    int host_answers = MDRQ_HOST_AUTO;  // mdrq_set_host_answers
     mdrq::HostSink *sink = nullptr;   // set while a batch answers into host memory (run_batch)
     mdrq::ZoneWindows *zwin = nullptr;
 

@@ -62,12 +62,13 @@ EXPORTS = ["mdrq_load_columns", "mdrq_query", "mdrq_query_batch", "mdrq_free",
            "mdrq_set_shared_config", "mdrq_set_shared_bits_budget", "mdrq_autotune",
            "mdrq_set_zone_maps", "mdrq_zone_map_info", "mdrq_zone_scan_info",
            "mdrq_server_submit_batch", "mdrq_server_wait_many", "mdrq_explain_query",
-           "mdrq_learn_search_info", "mdrq_learn_export"]
+           "mdrq_learn_search_info", "mdrq_learn_export", "mdrq_set_host_answers", "mdrq_set_shared_codes"]
 
 FAULT_SKIP_TILES, FAULT_NOMEM = 1, 2
 BATCH_AUTO, BATCH_PLAIN, BATCH_SHARED, BATCH_LEARNED = 0, 1, 2, 3
 MODEL_PLA, MODEL_MLP, MODEL_NONE = 1, 2, 3
 ZONES_OFF, ZONES_AUTO, ZONES_ALL = 0, 1, 2
+HOST_AUTO, HOST_STAGED, HOST_DIRECT = 0, 1, 2
 
 STATIC_MAX_ROWS = 1 << 28  # MDRQ_STATIC_MAX_ROWS
 
@@ -110,6 +111,10 @@ def lib():
         L.mdrq_learn_info.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u32), ctypes.POINTER(ctypes.c_double)]
         L.mdrq_learn_window_rows.restype = ctypes.c_int
         L.mdrq_learn_window_rows.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]
+        L.mdrq_set_shared_codes.restype = ctypes.c_int
+        L.mdrq_set_shared_codes.argtypes = [vp, ctypes.c_int]
+        L.mdrq_set_host_answers.restype = ctypes.c_int
+        L.mdrq_set_host_answers.argtypes = [vp, ctypes.c_int]
         L.mdrq_learn_export.restype = ctypes.c_int
         L.mdrq_learn_export.argtypes = [vp, ctypes.POINTER(ModelDesc), ctypes.POINTER(u64), ctypes.POINTER(u64),
                                         ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), u32]
@@ -405,6 +410,18 @@ class Table:
         if st != OK:
             raise MDRQError(st, "mdrq_query_batch")
         return out[: int(off[-1])], off
+
+    def set_shared_codes(self, enable: bool):
+        """``mdrq_set_shared_codes``: let the shared scan encode its columns (default on)."""
+        st = lib().mdrq_set_shared_codes(self._h, 1 if enable else 0)
+        if st != OK:
+            raise MDRQError(st, "mdrq_set_shared_codes")
+
+    def set_host_answers(self, mode: int):
+        """``mdrq_set_host_answers``: HOST_AUTO, HOST_STAGED or HOST_DIRECT."""
+        st = lib().mdrq_set_host_answers(self._h, int(mode))
+        if st != OK:
+            raise MDRQError(st, "mdrq_set_host_answers")
 
     def set_zone_maps(self, mode: int):
         """``mdrq_set_zone_maps``: ZONES_OFF, ZONES_AUTO or ZONES_ALL."""

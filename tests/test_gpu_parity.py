@@ -28,13 +28,16 @@ def _device(cols):
     return [torch.from_numpy(np.ascontiguousarray(c)).cuda() for c in cols]
 
 
-def check_batch(M, columns, queries, on_device=True, nthreads=8, mode=None):
-    """Every query's answer equals the oracle's (count and every id)."""
+def check_batch(M, columns, queries, on_device=True, nthreads=8, mode=None, setup=None):
+    """Every query's answer equals the oracle's (count and every id). ``setup(table)``
+    may configure the table first."""
     import torch
     cols = _device(columns) if on_device else columns
     with M.Table(cols) as t:
         if mode is not None:
             t.set_batch_mode(mode)
+        if setup is not None:
+            setup(t)
         ids, off = t.query_batch(queries)
         torch.cuda.synchronize()
         got = M.as_uint32_numpy(ids)
@@ -253,12 +256,14 @@ def test_repeat_calls_reuse_scratch(M):
     check_batch(M, wl.columns, wl.queries, mode=1)
 
 
+@pytest.mark.parametrize("host", [1, 0, 2], ids=["staged", "auto", "direct"])
 @pytest.mark.parametrize("mode", [1, 2], ids=["plain", "shared"])
-def test_host_answers_pinned_and_pageable(M, mode):
-    """Host answers (staged; a plain batch's launches copied out one by one while the next
-    runs): the result and the capacity rule are those of the device path, for a
-    page-locked and a pageable buffer, with the capacity cut inside a middle launch.
-    The batch scans more than 2 GiB of columns, so it is split into several launches."""
+def test_host_answers_pinned_and_pageable(M, mode, host):
+    """Host answers: staged (a plain batch's launches copied out one by one while the
+    next runs; the batch scans more than 2 GiB of columns, so it is split into several
+    launches) or written by the scan itself into page-locked memory (auto, direct). The
+    result and the capacity rule are those of the device path, for a page-locked and a
+    pageable buffer, with the capacity cut inside the batch."""
     import torch
     wl = W.mixed_clustered(n=3_000_017, nq=64)
     want = [oracle.mdrq(wl.columns, q, 8) for q in wl.queries]
@@ -266,13 +271,15 @@ def test_host_answers_pinned_and_pageable(M, mode):
     total = cat.size
     with M.Table(_device(wl.columns)) as t:
         t.set_batch_mode(mode)
+        t.set_host_answers(host)
         enc = t.encode_batch(wl.queries)
         pinned = torch.full((total + 64,), -1, dtype=torch.int32, pin_memory=True)
         st, off = t.query_batch_raw(enc, pinned.data_ptr(), total, False)
         assert st == M.OK and int(off[-1]) == total
         if mode == 1:
             launches, scanned = t.last_scan_stats()
-            assert launches >= 2 and scanned >= 2 << 30, (launches, scanned)
+            assert scanned >= 2 << 30
+            assert (launches >= 2) if host == 1 else (launches == 1), launches
         got = pinned.numpy().view(np.uint32)
         assert np.array_equal(got[:total], cat)
         assert np.all(pinned.numpy()[total:] == -1)
@@ -283,10 +290,24 @@ def test_host_answers_pinned_and_pageable(M, mode):
         assert st == M.E_CAPACITY and int(off[-1]) == total
         assert np.array_equal(pinned.numpy().view(np.uint32)[:cap], cat[:cap])
         assert np.all(pinned.numpy()[cap:] == -1)
-        # pageable host memory (staged copy)
+        # pageable host memory: staged, except in direct mode, which refuses it
         page = np.zeros(total, dtype=np.uint32)
         st, off = t.query_batch_raw(enc, page.ctypes.data, total, False)
-        assert st == M.OK and np.array_equal(page, cat)
+        if host == 2:
+            assert st == M.E_INVAL
+        else:
+            assert st == M.OK and np.array_equal(page, cat)
+        # a single query into page-locked memory
+        one = np.zeros(0, dtype=np.uint32)
+        if want[0].size:
+            pin1 = torch.full((want[0].size,), -1, dtype=torch.int32, pin_memory=True)
+            cnt = M.ctypes.c_uint64(0)
+            preds = M.encode_query(wl.queries[0], t.dtypes)
+            st = M.lib().mdrq_query(t.handle, preds, len(wl.queries[0]), pin1.data_ptr(), pin1.numel(),
+                                    M.ctypes.byref(cnt), 0, None)
+            one = pin1.numpy().view(np.uint32)
+            assert st == M.OK and cnt.value == want[0].size
+        assert np.array_equal(one, want[0])
 
 
 def test_explain_query_plan(M):

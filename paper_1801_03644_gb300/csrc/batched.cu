@@ -195,13 +195,23 @@ __device__ __forceinline__ uint32_t column_value(const uint32_t *desc, uint64_t 
 }
 
 // The batch's codes of one column: code(x) = #{cut points <= x} over the sorted cut
-// points cut[0 .. m) of every chunk (m <= kCodedMaxCuts), by the fixed-step search.
+// points cut[0 .. m) of every chunk (m <= kCodedMaxCuts). With a hint (scale != 0) the
+// value's bucket trunc((x - base) * scale), clamped to [0, kEncodeBuckets), gives the
+// number of cut points in lower buckets (16-bit entries in the plan after the cut
+// points), and at most `steps` compares walk the cut points of its own bucket: the
+// bucket function is monotone in x and the host computed the entries with the same
+// float arithmetic, so this is exact. Without a hint, the fixed-step search.
+constexpr uint32_t kEncodeBuckets = 4096;
+
 struct EncodeCol {
     const uint32_t *col;      // device column
     unsigned short *codes;    // n codes
-    uint64_t cut_off;         // plan word of its cut points
+    uint64_t cut_off;         // plan word of its cut points (then the hint, if any)
     uint32_t m;
     uint32_t type;
+    uint32_t steps;           // most cut points in one bucket (hint only)
+    float base, scale;        // bucket function (scale 0: no hint)
+    uint32_t pad;
 };
 
 __global__ void __launch_bounds__(256) mdrq_shared_encode_kernel(const EncodeCol *ec, const uint32_t *plan,
@@ -209,11 +219,35 @@ __global__ void __launch_bounds__(256) mdrq_shared_encode_kernel(const EncodeCol
 {
     extern __shared__ uint32_t s_cut[];
     const EncodeCol c = ec[blockIdx.y];
-    for (uint32_t i = threadIdx.x; i < c.m; i += blockDim.x)
+    const bool hinted = c.scale != 0.0f;
+    const uint32_t words = c.m + (hinted ? kEncodeBuckets / 2 : 0u);
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x)
         s_cut[i] = plan[c.cut_off + i];
     __syncthreads();
-    for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x)
-        c.codes[r] = (unsigned short)elementary_interval(s_cut, c.m, __ldg(c.col + r), c.type);
+    const unsigned short *hint = reinterpret_cast<const unsigned short *>(s_cut + c.m);
+    const bool f32 = c.type == kTypeF32;
+    for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t x = __ldg(c.col + r);
+        uint32_t pos;
+        if (hinted) {
+            const float xf = f32 ? __uint_as_float(x) : (float)(int)x;
+            int b = __float2int_rz((xf - c.base) * c.scale);
+            b = b < 0 ? 0 : (b >= (int)kEncodeBuckets ? (int)kEncodeBuckets - 1 : b);
+            pos = hint[b];
+            const uint32_t end = pos + c.steps < c.m ? pos + c.steps : c.m;
+            if (f32) {
+                const float xv = __uint_as_float(x);
+                while (pos < end && __uint_as_float(s_cut[pos]) <= xv)
+                    ++pos;
+            } else {
+                while (pos < end && (int)s_cut[pos] <= (int)x)
+                    ++pos;
+            }
+        } else {
+            pos = elementary_interval(s_cut, c.m, x, c.type);
+        }
+        c.codes[r] = (unsigned short)pos;
+    }
 }
 
 // T[e][g] for every elementary interval of every (chunk, column): bit i of word g is
@@ -1077,9 +1111,49 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
             ec.cut_off = plan.size();
             ec.m = (uint32_t)gcuts[j].size();
             ec.type = (uint32_t)t->cols[j].type;
+            ec.steps = 0;
+            ec.base = ec.scale = 0.0f;
+            ec.pad = 0;
             for (double v : gcuts[j])
                 plan.push_back(to_bits(v, t->cols[j].type));
-            max_gcuts = std::max(max_gcuts, ec.m);
+            // the bucket hint: cut points below each of kEncodeBuckets value buckets over
+            // [min, max], with the kernel's float bucket function; kept when no bucket
+            // holds more than kMaxHintSteps cut points
+            const ColumnInfo &ci_ = t->cols[j];
+            const double mn = bound_value(ci_.min_bits, ci_.type), mx = bound_value(ci_.max_bits, ci_.type);
+            const double range = mx - mn;
+            const float base = (float)mn, scale = (float)(kEncodeBuckets / range);
+            if (std::isfinite(range) && range > 0 && ec.m > 8 && std::isfinite(base) && std::isfinite(scale) &&
+                scale > 0.0f) {
+                auto bucket = [&](double v) {
+                    const float xf = ec.type == MDRQ_F32 ? (float)v : (float)(int32_t)v;
+                    const float tq = (xf - base) * scale;
+                    if (!(tq >= 1.0f))
+                        return 0u;  // negative, below one, or NaN
+                    if (tq >= (float)(kEncodeBuckets - 1))
+                        return kEncodeBuckets - 1;
+                    return (uint32_t)tq;  // truncation, as __float2int_rz
+                };
+                std::vector<uint32_t> in_bucket(kEncodeBuckets, 0);
+                for (double c : gcuts[j])
+                    ++in_bucket[bucket(c)];
+                uint32_t steps = 0;
+                for (uint32_t b = 0; b < kEncodeBuckets; ++b)
+                    steps = std::max(steps, in_bucket[b]);
+                if (steps <= kMaxHintSteps) {
+                    ec.steps = steps;
+                    ec.base = base;
+                    ec.scale = scale;
+                    const size_t h0 = plan.size();
+                    plan.resize(h0 + kEncodeBuckets / 2, 0);
+                    uint32_t below = 0;
+                    for (uint32_t b = 0; b < kEncodeBuckets; ++b) {
+                        plan[h0 + (b >> 1)] |= below << ((b & 1) * 16);
+                        below += in_bucket[b];
+                    }
+                }
+            }
+            max_gcuts = std::max(max_gcuts, ec.m + (ec.scale != 0.0f ? kEncodeBuckets / 2 : 0u));
             ecols.push_back(ec);
         }
     }
@@ -1097,7 +1171,7 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
             if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, most) != cudaSuccess)
                 return cuda_status(cudaGetLastError());
         if (cudaFuncSetAttribute(mdrq_shared_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kCodedMaxCuts * 4) != cudaSuccess)
+                                 (int)(kCodedMaxCuts + kEncodeBuckets / 2) * 4) != cudaSuccess)
             return cuda_status(cudaGetLastError());
         S.smem_attr = true;
         S.grid_scan = t->sm_count * 2;

@@ -226,8 +226,7 @@ __global__ void __launch_bounds__(256) mdrq_shared_encode_kernel(const EncodeCol
     __syncthreads();
     const unsigned short *hint = reinterpret_cast<const unsigned short *>(s_cut + c.m);
     const bool f32 = c.type == kTypeF32;
-    for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t x = __ldg(c.col + r);
+    auto code_of = [&](uint32_t x) -> uint32_t {
         uint32_t pos;
         if (hinted) {
             const float xf = f32 ? __uint_as_float(x) : (float)(int)x;
@@ -246,8 +245,20 @@ __global__ void __launch_bounds__(256) mdrq_shared_encode_kernel(const EncodeCol
         } else {
             pos = elementary_interval(s_cut, c.m, x, c.type);
         }
-        c.codes[r] = (unsigned short)pos;
+        return pos;
+    };
+    // four rows per thread: one 16-byte load (the column is 16-byte aligned) and one
+    // 8-byte store (each code column starts on a multiple of 8 codes); the last n % 4
+    // rows one by one
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t n4 = n / 4;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(c.col) + i);
+        const uint32_t a = code_of(v.x), b = code_of(v.y), d = code_of(v.z), e = code_of(v.w);
+        reinterpret_cast<uint2 *>(c.codes)[i] = make_uint2(a | (b << 16), d | (e << 16));
     }
+    for (uint64_t r = 4 * n4 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride)
+        c.codes[r] = (unsigned short)code_of(__ldg(c.col + r));
 }
 
 // T[e][g] for every elementary interval of every (chunk, column): bit i of word g is
@@ -320,6 +331,9 @@ template <bool WRITE, bool CACHED, bool CODED>
 __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(SharedParams p)
 {
     constexpr bool kLoadMasks = WRITE && CACHED;
+    // columns whose next-step values are loaded ahead: fewer for 2-byte codes, whose
+    // lookups are short, than for values, whose searches are long (measured)
+    constexpr int kPre = CODED ? 4 : kPrefetchCols;
     extern __shared__ __align__(16) uint32_t s_img[];
     __shared__ uint32_t s_chunk;
     const int lane = threadIdx.x & 31;
@@ -377,12 +391,12 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
             valid_words[g] = left >= 32 ? 0xffffffffu : left > 0 ? (1u << left) - 1u : 0u;
         }
 
-        // values of the first kPrefetchCols columns for the next 32-row step are loaded
+        // values of the first kPre columns for the next 32-row step are loaded
         // while the current step is evaluated (software pipelining of the column reads)
-        const uint32_t npre = kLoadMasks ? 0u : (h.ncols < kPrefetchCols ? h.ncols : kPrefetchCols);
-        uint32_t xn[kPrefetchCols];
+        const uint32_t npre = kLoadMasks ? 0u : (h.ncols < kPre ? h.ncols : kPre);
+        uint32_t xn[kPre];
 #pragma unroll
-        for (int i = 0; i < kPrefetchCols; ++i) {
+        for (int i = 0; i < kPre; ++i) {
             const uint64_t r = r_begin + lane;
             xn[i] = 0u;
             if (i < (int)npre && r < r_end)
@@ -404,9 +418,9 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
                 mask[2] = m4.z;
                 mask[3] = m4.w;
             } else {
-                uint32_t x[kPrefetchCols];
+                uint32_t x[kPre];
 #pragma unroll
-                for (int i = 0; i < kPrefetchCols; ++i) {
+                for (int i = 0; i < kPre; ++i) {
                     x[i] = xn[i];
                     const uint64_t rn = r + 32;
                     xn[i] = 0u;
@@ -417,7 +431,7 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
                 for (int g = 0; g < kSharedG; ++g)
                     mask[g] = valid ? valid_words[g] : 0u;
 #pragma unroll
-                for (int i = 0; i < kPrefetchCols; ++i) {
+                for (int i = 0; i < kPre; ++i) {
                     if (i < (int)npre) {
                         const uint4 hot = *reinterpret_cast<const uint4 *>(s_img + i * kColWords);
                         const uint32_t e = CODED ? coded_interval(s_img, hot, x[i]) : interval_of(s_img, hot, x[i]);
@@ -429,16 +443,16 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
                     }
                 }
                 // columns beyond the prefetched ones: loaded together, then evaluated
-                for (uint32_t a0 = npre; a0 < h.ncols; a0 += kPrefetchCols) {
-                    uint32_t y[kPrefetchCols];
+                for (uint32_t a0 = npre; a0 < h.ncols; a0 += kPre) {
+                    uint32_t y[kPre];
 #pragma unroll
-                    for (int i = 0; i < kPrefetchCols; ++i) {
+                    for (int i = 0; i < kPre; ++i) {
                         y[i] = 0u;
                         if (a0 + i < h.ncols && valid)
                             y[i] = column_value<CODED>(s_img + (a0 + i) * kColWords, r);
                     }
 #pragma unroll
-                    for (int i = 0; i < kPrefetchCols; ++i) {
+                    for (int i = 0; i < kPre; ++i) {
                         if (a0 + i < h.ncols) {
                             const uint4 hot = *reinterpret_cast<const uint4 *>(s_img + (a0 + i) * kColWords);
                             const uint32_t e = CODED ? coded_interval(s_img, hot, y[i])
@@ -893,8 +907,9 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
     };
     for (const auto &cols : chunk_cols)
         coded = coded && coded_image_words(cols) <= std::min<uint64_t>(kMaxImageWords, 0xffff);
+    const uint64_t code_stride = (t->n + 7) & ~7ull;  // codes per column, a multiple of 8
     if (coded) {
-        const uint64_t code_bytes = (uint64_t)gdims.size() * t->n * 2;
+        const uint64_t code_bytes = (uint64_t)gdims.size() * code_stride * 2;
         size_t free_b = 0, total_b = 0;
         coded = code_bytes <= kMaskBudgetBytes &&
                 (S.codes_cap >= code_bytes ||
@@ -945,7 +960,7 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
                 cc.w0 = lut_off[a] | ((uint32_t)cut.size() << 16) | ((bytes ? 1u : 0u) << 30) |
                         ((t->cols[j].type == MDRQ_I32 ? 1u : 0u) << 31);
                 cc.w1 = tab_off[a];
-                cc.col = reinterpret_cast<const uint32_t *>(S.codes + (size_t)gslot[j] * t->n);
+                cc.col = reinterpret_cast<const uint32_t *>(S.codes + (size_t)gslot[j] * code_stride);
                 std::memcpy(&plan[img_off + a * kColWords], &cc, sizeof(ChunkCol));
                 // code k: the values in [g[k-1], g[k]); the chunk's cut points at or
                 // below them are its cut points among g[0 .. k)
@@ -1107,7 +1122,7 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
             const uint32_t j = gdims[gi];
             EncodeCol ec;
             ec.col = static_cast<const uint32_t *>(t->cols[j].ptr);
-            ec.codes = S.codes + gi * t->n;
+            ec.codes = S.codes + gi * code_stride;
             ec.cut_off = plan.size();
             ec.m = (uint32_t)gcuts[j].size();
             ec.type = (uint32_t)t->cols[j].type;

@@ -140,8 +140,12 @@ def measured_peaks() -> dict:
 
 
 def scan_kernel_digest() -> str:
-    src = os.path.join(ROOT, "paper_1801_03644_gb300", "csrc", "scan_kernel.cuh")
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    """Digest of the scan kernel's source and of the file that configures its launches
+    (tile size, grid, the context's L2 fetch limit)."""
+    h = hashlib.sha256()
+    for name in ("scan_kernel.cuh", "mdrq.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1801_03644_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def dram_traffic_per_launch(workload: str, alg_bytes_per_launch: float):

@@ -95,6 +95,12 @@ typedef struct {
  *  stream         stream for the copies and checks.
  *  out            receives the handle; release it with mdrq_free.
  *
+ * Loading also limits the L2 cache's fetch granularity of the current CUDA context
+ * to 32 bytes (cudaLimitMaxL2FetchGranularity): the scan's early break reads isolated
+ * 32-byte sectors, and larger fetches would bring in the sectors it skips. The limit
+ * applies to every kernel of the context and ends with it; a caller who wants another
+ * value sets it again after loading.
+ *
  * Errors: MDRQ_E_INVAL (d = 0, n >= 2^32, a null pointer where n > 0, an unknown
  * type, a device column that is not 16-byte aligned, out == NULL); MDRQ_E_NAN (a
  * float32 column holds a NaN; nothing is kept); MDRQ_E_NOMEM; MDRQ_E_CUDA.

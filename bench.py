@@ -211,13 +211,48 @@ def verify_with_oracle(columns, queries, ids, off, which, nthreads: int) -> dict
             "seconds": time.perf_counter() - t0}
 
 
-def early_break_bytes(table, cols_dev, queries, n: int, granule: int = 32):
+def zone_candidates(table, cols_dev, n: int, tile: int = 4096, max_runs: int = 1024):
+    """For the tile pruning of zone maps: a function of a query plan that gives the row
+    mask of the tiles the scan visits. A tile is a candidate when, for every predicate
+    whose column's zone map is in use (``mdrq_zone_map_info``), the tile's [min, max]
+    meets the interval; more than ``max_runs`` runs of candidates are visited as one
+    span from the first to the last. The tiles' min and max are computed here from the
+    columns, independently of the library's zone maps."""
+    import torch
+    ntiles = (n + tile - 1) // tile
+    pad = ntiles * tile - n
+    used, tmin, tmax = {}, {}, {}
+    for j, x in enumerate(cols_dev):
+        used[j] = table.zone_map_info(j)["used"]
+        if used[j]:
+            xp = torch.cat([x, x[-1:].expand(pad)]) if pad else x
+            tmin[j] = xp.view(ntiles, tile).amin(dim=1)
+            tmax[j] = xp.view(ntiles, tile).amax(dim=1)
+
+    def visited(plan):
+        cand = torch.ones(ntiles, dtype=torch.bool, device=cols_dev[0].device)
+        for (j, lo, hi) in plan:
+            if used[j]:
+                lo_t = torch.tensor(lo, dtype=cols_dev[j].dtype, device=cand.device)
+                hi_t = torch.tensor(hi, dtype=cols_dev[j].dtype, device=cand.device)
+                cand &= (tmax[j] >= lo_t) & (tmin[j] <= hi_t)
+        starts = cand.clone()
+        starts[1:] &= ~cand[:-1]
+        if int(starts.sum()) > max_runs:
+            idx = torch.nonzero(cand).flatten()
+            cand[int(idx[0]):int(idx[-1]) + 1] = True
+        return cand.repeat_interleave(tile)[:n]
+    return visited
+
+
+def early_break_bytes(table, cols_dev, queries, n: int, granule: int = 32, visited=None):
     """Algorithmic bytes of the plain scan of ``queries`` with its early break (Sec.
     2.2.4) at DRAM-sector granularity: for each query, in the order the scan evaluates
     its predicates (``mdrq_explain_query``), 32 B for every 32-byte sector (8 rows) of
     the column that still holds a row satisfying all earlier predicates, plus 4 B per
     answer id (``granule``: the same count at a coarser fetch size, for comparison with
-    the DRAM traffic). Counted on the GPU with plain tensor operations, outside any timed
+    the DRAM traffic; ``visited``: a function of the plan giving the rows the scan
+    reaches at all, for tile pruning). Counted on the GPU with plain tensor operations, outside any timed
     region; it does not depend on the kernel (two lanes of 4 rows share a sector, and
     a lane whose rows have all failed issues no load)."""
     import torch
@@ -228,7 +263,7 @@ def early_break_bytes(table, cols_dev, queries, n: int, granule: int = 32):
         empty, plan = table.explain(q)
         if empty:
             continue
-        alive = None
+        alive = visited(plan) if visited is not None else None
         for (j, lo, hi) in plan:
             x = cols_dev[j]
             if alive is None:
@@ -878,15 +913,14 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
         dense_rule = ("4 B per row per constrained column over the rows of the tiles the zone "
                       "maps leave (%d rows per query) plus 4 B per id" % (zone_rows // max(1, nq)))
     avg_launch_s = timing["ms"] / 1e3 / launches
-    if zone_rows is None:
-        alg_per_launch = early_break_bytes(table, cols_dev, wl.queries, wl.n)
-        alg64_per_launch = early_break_bytes(table, cols_dev, wl.queries, wl.n, granule=64)
-        alg_rule = ("early-break bytes: per query, in the scan's predicate order, 32 B per 32-byte "
-                    "sector (8 rows) of each evaluated column that still holds a row satisfying "
-                    "the earlier predicates, plus 4 B per id")
-    else:
-        alg_per_launch, alg_rule = dense_per_launch, dense_rule
-        alg64_per_launch = None
+    vis = zone_candidates(table, cols_dev, wl.n) if zone_rows is not None else None
+    alg_per_launch = early_break_bytes(table, cols_dev, wl.queries, wl.n, visited=vis)
+    alg64_per_launch = early_break_bytes(table, cols_dev, wl.queries, wl.n, granule=64, visited=vis)
+    alg_rule = ("early-break bytes: per query, in the scan's predicate order, 32 B per 32-byte "
+                "sector (8 rows) of each evaluated column that still holds a row satisfying "
+                "the earlier predicates, plus 4 B per id")
+    if zone_rows is not None:
+        alg_rule += "; rows of the tiles the zone maps rule out are never reached"
     achieved = alg_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
     effective = dense_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
     traffic, ratio = dram_traffic_per_launch(args.workload, alg_per_launch)

@@ -60,3 +60,73 @@ def test_selectivity_summary_from_offsets():
     assert s["min"] == 0.0 and s["max"] == 1.0 and s["median"] == 0.02
     assert abs(s["mean"] - 1040 / 4000) < 1e-12
     assert bench.selectivity_summary(np.zeros(1, dtype=np.uint64), 1000) == {"queries": 0}
+
+
+def _bench_module():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_module", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    return bench
+
+
+class _PlanTable:
+    """Stands in for a table: the plan is the query itself, every zone map in use."""
+
+    def explain(self, q):
+        return (any(lo > hi for (_, lo, hi) in q), [] if any(lo > hi for (_, lo, hi) in q) else list(q))
+
+    def zone_map_info(self, j):
+        return {"used": True, "mean_width": 0.0}
+
+
+def _brute_early_break(cols, queries, n, granule, tile=None, max_runs=1024):
+    """The same count written out row by row (and tile by tile) with numpy."""
+    import numpy as np
+    rows = granule // 4
+    total = 0
+    for q in queries:
+        if any(lo > hi for (_, lo, hi) in q):
+            continue
+        alive = np.ones(n, dtype=bool)
+        if tile is not None:
+            nt = (n + tile - 1) // tile
+            cand = np.ones(nt, dtype=bool)
+            for (j, lo, hi) in q:
+                for t in range(nt):
+                    seg = cols[j][t * tile:(t + 1) * tile]
+                    cand[t] &= seg.max() >= lo and seg.min() <= hi
+            starts = cand & ~np.concatenate([[False], cand[:-1]])
+            if starts.sum() > max_runs:
+                idx = np.flatnonzero(cand)
+                cand[idx[0]:idx[-1] + 1] = True
+            alive = np.repeat(cand, tile)[:n]
+        for (j, lo, hi) in q:
+            sectors = sum(alive[s:s + rows].any() for s in range(0, n, rows))
+            total += granule * sectors
+            alive &= (cols[j] >= lo) & (cols[j] <= hi)
+        total += 4 * int(alive.sum())
+    return total
+
+
+def test_early_break_byte_count_matches_a_row_by_row_count():
+    """bench.py's roofline bytes: sectors that still hold a live row when their column
+    is reached, per query in plan order, plus the ids; with tile pruning, only rows of
+    candidate tiles are ever live."""
+    import numpy as np
+    import torch
+    bench = _bench_module()
+    rng = np.random.default_rng(3)
+    n = 9_001
+    cols = [np.sort(rng.random(n).astype(np.float32)), rng.random(n).astype(np.float32),
+            rng.integers(-5, 5, size=n).astype(np.int32)]
+    queries = [[(0, 0.2, 0.4), (1, 0.1, 0.9)], [(2, -1, 1)], [(1, 0.3, 0.31), (2, 0, 4), (0, 0.0, 0.99)],
+               [(0, 0.5, 0.4)], [(0, 0.05, 0.06), (2, -5, -5)]]
+    dev = [torch.from_numpy(c) for c in cols]
+    t = _PlanTable()
+    for granule in (32, 64):
+        assert bench.early_break_bytes(t, dev, queries, n, granule=granule) == \
+            _brute_early_break(cols, queries, n, granule)
+        vis = bench.zone_candidates(t, dev, n, tile=512)
+        assert bench.early_break_bytes(t, dev, queries, n, granule=granule, visited=vis) == \
+            _brute_early_break(cols, queries, n, granule, tile=512)

@@ -373,7 +373,7 @@ def timed_steps(torch, stream, step, steps, barrier):
     return e0.elapsed_time(e1), last
 
 
-def learned_leg(args, table, enc, step, nq, total_ids, world, barrier, stream, ids, ids_ref, off_ref):
+def learned_leg(args, table, enc, step, nq, total_ids, world, barrier, stream, ids, ids_ref, off_ref, cells=None):
     """Learned range narrower (PLA, the MLP-rooted two-stage model, and no model: the
     whole key column searched) and zone-map tile pruning on a Z-sorted table: queries/s
     and speedup over the plain scan of the same batch with zone maps off (every tile
@@ -402,7 +402,7 @@ def learned_leg(args, table, enc, step, nq, total_ids, world, barrier, stream, i
                                  "speedup_vs_plain": zval / base, "rows_visited_per_query": zrows / nq,
                                  "tiles_visited": ztiles, "answers_identical_to_plain": same_z}}
     for name, model in (("pla", mdrq.MODEL_PLA), ("mlp", mdrq.MODEL_MLP), ("none", mdrq.MODEL_NONE)):
-        info = table.learn([0, 1, 2, 3], model)
+        info = table.learn([0, 1, 2, 3], model, cells=cells)
         lvalue, lms, same_l = timed(mdrq.BATCH_LEARNED, mdrq.ZONES_AUTO)
         rows, widen = table.learn_window_rows()
         ranges, probes = table.learn_search_info()
@@ -455,7 +455,8 @@ def learned_workload_leg(args, world, barrier):
     ids_ref = ids[:total].clone()
     nq = len(wl.queries)
     res = {"workload": wl.name, "recipe": wl.recipe, "unit": UNIT, "answer_ids_per_step": total}
-    res.update(learned_leg(args, table, enc, step, nq, total, world, barrier, stream, ids, ids_ref, off_ref))
+    res.update(learned_leg(args, table, enc, step, nq, total, world, barrier, stream, ids, ids_ref, off_ref,
+                           cells=wl.key_bounds))
     table.close()
     del ids
     if not args.no_verify:
@@ -841,7 +842,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     # ---- learned range narrower: on this table when it is Z-sorted, else on its own
     learned = None
     if args.workload == "zorder_learned":
-        learned = learned_leg(args, table, enc, step, nq, total_ids, world, barrier, stream, ids, ids_ref, off_ref)
+        learned = learned_leg(args, table, enc, step, nq, total_ids, world, barrier, stream, ids, ids_ref, off_ref,
+                              cells=wl.key_bounds)
 
     # ---- end to end: host query descriptors in, host answers out (pinned)
     e2e = None

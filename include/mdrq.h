@@ -263,8 +263,11 @@ int mdrq_set_batch_mode(mdrq_table *t, int mode);
  * 2.2); this narrows the full scan of Sec. 2.2.4 to the rows a query can match.
  *
  * The table's rows must already be sorted by the 32-bit Z-order (Morton) key of the
- * float32 columns dims[0 .. ndims) (1 <= ndims <= 4): with cell(x) = clamp(floor(x *
- * 256), 0, 255) in float32, key bit 4b + j is bit b of cell(x_dims[j]). The cells of a
+ * float32 columns dims[0 .. ndims) (1 <= ndims <= 4): key bit 4b + j is bit b of
+ * cell(x_dims[j]), where cell(x) is the number of the column's 255 cell bounds at or
+ * below x when mdrq_set_key_cells gave it bounds (for instance the column's quantiles,
+ * so that every cell holds about as many rows), and clamp(floor(x * 256), 0, 255) in
+ * float32 otherwise. The cells of a
  * query box then form key ranges, each one run of rows of the sorted table. Per batch
  * the GPU splits every query's box into at most 1024 such ranges (the key-bit tree
  * expanded level by level, largest runs first; the ranges left at the budget cover
@@ -291,6 +294,14 @@ int mdrq_set_batch_mode(mdrq_table *t, int mode);
 #define MDRQ_MODEL_PLA 1
 #define MDRQ_MODEL_MLP 2
 #define MDRQ_MODEL_NONE 3
+
+/* mdrq_set_key_cells — the cells of key dimension `dim` for later mdrq_learn calls:
+ * bounds[0 .. 255) ascending (no NaN) split the values into 256 cells, cell(x) = the
+ * number of bounds <= x; nbounds = 0 returns the column to equal-width cells. A model
+ * keeps the cells it was trained with. The paper has no counterpart (its index
+ * structures partition space by their own rules). Errors: MDRQ_E_INVAL (t NULL, dim >=
+ * d, nbounds other than 0 or 255, bounds NULL, NaN or not ascending). */
+int mdrq_set_key_cells(mdrq_table *t, uint32_t dim, const float *bounds, uint32_t nbounds);
 int mdrq_learn(mdrq_table *t, const uint32_t *dims, uint32_t ndims, int model, void *stream);
 
 /* mdrq_learn_info — the model's largest position error over all keys (n for

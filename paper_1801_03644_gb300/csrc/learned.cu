@@ -45,6 +45,7 @@
 namespace mdrq {
 
 constexpr uint32_t kPlaSegments = 4096;
+constexpr uint32_t kKeyCellBounds = 255;   // bounds of 256 cells per key dimension
 constexpr uint32_t kMlpLeaves = 1u << 18;  // second stage of the MLP-rooted model
 constexpr int kMlpHidden = 32;
 constexpr int kMlpParams = kMlpHidden + kMlpHidden + kMlpHidden * kMlpHidden + kMlpHidden + kMlpHidden + 1;
@@ -66,6 +67,8 @@ struct LearnedModel {
     uint32_t segments = 0;
     unsigned long long key_min = 0;          // MLP input: (key - key_min) * key_inv
     float key_inv = 0.0f;
+    std::vector<float> cells[4];             // each key dimension's cell bounds (empty: equal width)
+    float *cells_dev = nullptr;              // the same, kKeyCellBounds per dimension (device)
     unsigned long long *knot_key = nullptr;  // segments + 1 (last = max key + 1)
     unsigned long long *knot_pos = nullptr;  // segments + 1
     float *slope = nullptr;                  // segments
@@ -87,14 +90,25 @@ struct LearnedModel {
 
 // ---------------------------------------------------------------- keys
 
-__device__ __forceinline__ uint32_t zcell(float x)
+// Cell of a value on one key dimension: with bounds (255 ascending values), the number
+// of bounds at or below x; without, clamp(floor(x * 256), 0, 255) in float32. Either is
+// monotone in x, which is all the key's ordering argument needs.
+__host__ __device__ __forceinline__ uint32_t zcell(float x, const float *bounds)
 {
+    if (bounds) {
+        uint32_t c = 0;
+        for (uint32_t step = 128; step; step >>= 1)
+            if (c + step <= kKeyCellBounds && bounds[c + step - 1] <= x)
+                c += step;
+        return c;
+    }
     const float c = floorf(x * 256.0f);
     return c < 0.0f ? 0u : (c > 255.0f ? 255u : (uint32_t)c);
 }
 
 struct KeyCols {
     const float *col[4];
+    const float *bounds[4];  // device cell bounds of each key dimension, or null
     uint32_t ndims;
 };
 
@@ -103,7 +117,7 @@ __global__ void mdrq_zkey_kernel(KeyCols kc, uint64_t n, uint32_t *keys)
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t k = 0;
         for (uint32_t j = 0; j < kc.ndims; ++j) {
-            const uint32_t c = zcell(kc.col[j][i]);
+            const uint32_t c = zcell(kc.col[j][i], kc.bounds[j]);
             for (int b = 0; b < 8; ++b)
                 k |= ((c >> b) & 1u) << (4 * b + j);
         }
@@ -920,10 +934,9 @@ ModelView view_of(const LearnedModel &m, uint64_t n)
     return v;
 }
 
-uint32_t host_cell(float x)
+uint32_t host_cell(float x, const std::vector<float> &bounds)
 {
-    const float c = std::floor(x * 256.0f);
-    return c < 0.0f ? 0u : (c > 255.0f ? 255u : (uint32_t)c);
+    return zcell(x, bounds.empty() ? nullptr : bounds.data());
 }
 
 
@@ -939,6 +952,7 @@ void learned_free(mdrq_table *t)
     cudaFree(m.knot_pos);
     cudaFree(m.slope);
     cudaFree(m.mlp);
+    cudaFree(m.cells_dev);
     cudaFree(m.slots);
     cudaFree(m.windows);
     cudaFree(m.qaux);
@@ -974,8 +988,26 @@ int learn(mdrq_table *t, const uint32_t *dims, uint32_t ndims, int kind, cudaStr
             (st = cuda_status(cudaMalloc(&m->totals, 16))))
             break;
         KeyCols kc;
-        for (int j = 0; j < 4; ++j)
+        bool any_cells = false;
+        for (uint32_t j = 0; j < ndims; ++j) {
+            m->cells[j] = t->cols[dims[j]].key_cells;
+            any_cells = any_cells || !m->cells[j].empty();
+        }
+        if (any_cells) {
+            if ((st = cuda_status(cudaMalloc(&m->cells_dev, 4ull * kKeyCellBounds * 4))))
+                break;
+            for (uint32_t j = 0; j < ndims; ++j)
+                if (!m->cells[j].empty() &&
+                    (st = cuda_status(cudaMemcpyAsync(m->cells_dev + j * kKeyCellBounds, m->cells[j].data(),
+                                                      kKeyCellBounds * 4, cudaMemcpyHostToDevice, s))))
+                    break;
+            if (st)
+                break;
+        }
+        for (int j = 0; j < 4; ++j) {
             kc.col[j] = j < (int)ndims ? static_cast<const float *>(t->cols[dims[j]].ptr) : nullptr;
+            kc.bounds[j] = j < (int)ndims && !m->cells[j].empty() ? m->cells_dev + j * kKeyCellBounds : nullptr;
+        }
         kc.ndims = ndims;
         const uint32_t grid = (uint32_t)std::min<uint64_t>((n + 255) / 256, (uint64_t)t->sm_count * 16);
         mdrq_zkey_kernel<<<grid, 256, 0, s>>>(kc, n, m->keys);
@@ -1124,8 +1156,8 @@ int learned_batch(mdrq_table *t, const std::vector<EncodedQuery> &enc, const std
                     float lo, hi;
                     std::memcpy(&lo, &e.preds[p].lo, 4);
                     std::memcpy(&hi, &e.preds[p].hi, 4);
-                    cl = host_cell(lo);
-                    ch = host_cell(hi);
+                    cl = host_cell(lo, m->cells[j]);
+                    ch = host_cell(hi, m->cells[j]);
                 }
             }
             clo |= cl << (8 * j);
@@ -1225,6 +1257,21 @@ int learned_export(const mdrq_table *t, mdrq_model_desc *desc, uint64_t *knot_ke
     }
     if (mlp && m.kind == MDRQ_MODEL_MLP)
         MDRQ_TRY_STATUS(cudaMemcpy(mlp, m.mlp, kMlpParams * 4ull, cudaMemcpyDeviceToHost));
+    return MDRQ_OK;
+}
+
+int set_key_cells(mdrq_table *t, uint32_t dim, const float *bounds, uint32_t nbounds)
+{
+    if (!t || dim >= t->d || (nbounds != 0 && (nbounds != kKeyCellBounds || !bounds)))
+        return MDRQ_E_INVAL;
+    if (nbounds == 0) {
+        t->cols[dim].key_cells.clear();
+        return MDRQ_OK;
+    }
+    for (uint32_t i = 0; i < nbounds; ++i)
+        if (std::isnan(bounds[i]) || (i > 0 && !(bounds[i - 1] <= bounds[i])))
+            return MDRQ_E_INVAL;
+    t->cols[dim].key_cells.assign(bounds, bounds + nbounds);
     return MDRQ_OK;
 }
 

@@ -1123,6 +1123,11 @@ int mdrq_learn_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *widenings)
     return learned_window_rows(t, rows, widenings);
 }
 
+int mdrq_set_key_cells(mdrq_table *t, uint32_t dim, const float *bounds, uint32_t nbounds)
+{
+    return set_key_cells(t, dim, bounds, nbounds);
+}
+
 int mdrq_learn_search_info(mdrq_table *t, uint64_t *ranges, uint64_t *probes)
 {
     return learned_search_info(t, ranges, probes);

@@ -22,6 +22,8 @@ struct ColumnInfo {
     uint2 *zone = nullptr;                // zone map (device, owned): min / max bits per 4096 rows
     double zone_width = 1.0;              // mean zone width / column range
     bool zone_keep = false;               // MDRQ_ZONES_AUTO reads this column's map
+    std::vector<float> key_cells;         // learned narrower: 255 ascending cell bounds, or
+                                          // empty for equal-width cells (mdrq_set_key_cells)
 };
 
 // a2: one query after encoding
@@ -202,6 +204,7 @@ int learned_info(const mdrq_table *t, uint64_t *max_error, uint32_t *segments, d
 void learned_free(mdrq_table *t);
 int learned_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *widenings);
 int learned_search_info(mdrq_table *t, uint64_t *ranges, uint64_t *probes);
+int set_key_cells(mdrq_table *t, uint32_t dim, const float *bounds, uint32_t nbounds);
 int learned_export(const mdrq_table *t, mdrq_model_desc *desc, uint64_t *knot_key, uint64_t *knot_pos, float *slope,
                    float *mlp, uint32_t capacity);
 

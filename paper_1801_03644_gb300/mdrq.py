@@ -62,7 +62,8 @@ EXPORTS = ["mdrq_load_columns", "mdrq_query", "mdrq_query_batch", "mdrq_free",
            "mdrq_set_shared_config", "mdrq_set_shared_bits_budget", "mdrq_autotune",
            "mdrq_set_zone_maps", "mdrq_zone_map_info", "mdrq_zone_scan_info",
            "mdrq_server_submit_batch", "mdrq_server_wait_many", "mdrq_explain_query",
-           "mdrq_learn_search_info", "mdrq_learn_export", "mdrq_set_host_answers", "mdrq_set_shared_codes"]
+           "mdrq_learn_search_info", "mdrq_learn_export", "mdrq_set_host_answers", "mdrq_set_shared_codes",
+           "mdrq_set_key_cells"]
 
 FAULT_SKIP_TILES, FAULT_NOMEM = 1, 2
 BATCH_AUTO, BATCH_PLAIN, BATCH_SHARED, BATCH_LEARNED = 0, 1, 2, 3
@@ -111,6 +112,8 @@ def lib():
         L.mdrq_learn_info.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u32), ctypes.POINTER(ctypes.c_double)]
         L.mdrq_learn_window_rows.restype = ctypes.c_int
         L.mdrq_learn_window_rows.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]
+        L.mdrq_set_key_cells.restype = ctypes.c_int
+        L.mdrq_set_key_cells.argtypes = [vp, u32, ctypes.POINTER(ctypes.c_float), u32]
         L.mdrq_set_shared_codes.restype = ctypes.c_int
         L.mdrq_set_shared_codes.argtypes = [vp, ctypes.c_int]
         L.mdrq_set_host_answers.restype = ctypes.c_int
@@ -495,9 +498,21 @@ class Table:
             raise MDRQError(st, "mdrq_prepare_batch")
         return Prepared(self, h.value, out, nq, off.copy())
 
-    def learn(self, dims, model: int = MODEL_PLA, stream=None):
+    def learn(self, dims, model: int = MODEL_PLA, stream=None, cells=None):
         """``mdrq_learn``: a learned range narrower over the Z-order key of ``dims`` (the
-        rows must be sorted by that key). Returns ``learn_info()``."""
+        rows must be sorted by that key). ``cells``: per key dimension 255 ascending
+        float32 cell bounds (``mdrq_set_key_cells``), or None for equal-width cells.
+        Returns ``learn_info()``."""
+        for k, j in enumerate(dims):
+            b = None if cells is None else cells[k]
+            if b is None:
+                st = lib().mdrq_set_key_cells(self._h, int(j), None, 0)
+            else:
+                b = np.ascontiguousarray(b, dtype=np.float32)
+                st = lib().mdrq_set_key_cells(self._h, int(j), b.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                              b.size)
+            if st != OK:
+                raise MDRQError(st, "mdrq_set_key_cells")
         arr = (ctypes.c_uint32 * max(1, len(dims)))(*[int(j) for j in dims])
         st = lib().mdrq_learn(self._h, arr, len(dims), int(model), _stream_handle(stream))
         if st != OK:

@@ -36,6 +36,7 @@ class Workload:
     columns: list          # d 1-D numpy arrays (float32 / int32), length n
     queries: list          # list of queries; a query is a list of (dim, lo, hi)
     recipe: str            # one line: how the inputs were drawn
+    key_bounds: list = None  # Z-sorted tables: per key column the 255 cell bounds, or None
 
     @property
     def n(self) -> int:
@@ -248,18 +249,34 @@ def skewed_mixed_types(n: int = 50_000_000, nq: int = 256, sel_range=(1e-6, 0.5)
                     % (n, nq, sel_range[0], sel_range[1], 100 * empty_fraction))
 
 
-def zorder_cell(v: np.ndarray) -> np.ndarray:
-    """8-bit cell of a value for the Z-order layout: clamp(floor(v * 256), 0, 255)."""
-    c = np.floor(np.asarray(v, dtype=np.float32) * np.float32(256.0))
+def zorder_cell(v: np.ndarray, bounds=None) -> np.ndarray:
+    """8-bit cell of a value for the Z-order layout: with ``bounds`` (255 ascending
+    float32 values) the number of bounds <= v, else clamp(floor(v * 256), 0, 255)."""
+    v = np.asarray(v, dtype=np.float32)
+    if bounds is not None:
+        return np.searchsorted(np.asarray(bounds, dtype=np.float32), v, side="right").astype(np.uint32)
+    c = np.floor(v * np.float32(256.0))
     return np.clip(c, 0, 255).astype(np.uint32)
 
 
-def zorder_key(columns: list) -> np.ndarray:
-    """32-bit Morton key over up to 4 columns of values in [0, 1): bit 4b + j of the key
-    is bit b of column j's 8-bit cell (dimension 0 least significant in each nibble)."""
+def quantile_cell_bounds(column: np.ndarray, rng: np.random.Generator, sample: int = 1 << 20) -> np.ndarray:
+    """255 cell bounds at the 1/256 .. 255/256 quantiles of a sample of the column, so
+    that each of the 256 cells holds about as many rows (float32, ascending)."""
+    n = column.shape[0]
+    s = np.sort(column[rng.integers(0, n, size=min(sample, max(1, n)))] if n else column)
+    if s.size == 0:
+        return np.linspace(0, 1, 257, dtype=np.float32)[1:-1]
+    idx = (np.arange(1, 256) * s.size) // 256
+    return s[np.minimum(idx, s.size - 1)].astype(np.float32)
+
+
+def zorder_key(columns: list, bounds=None) -> np.ndarray:
+    """32-bit Morton key over up to 4 columns: bit 4b + j of the key is bit b of column
+    j's 8-bit cell (dimension 0 least significant in each nibble); ``bounds``: per
+    column the cell bounds of ``zorder_cell``, or None for equal-width cells."""
     key = np.zeros(columns[0].shape[0], dtype=np.uint32)
     for j, c in enumerate(columns):
-        cell = zorder_cell(c)
+        cell = zorder_cell(c, None if bounds is None else bounds[j])
         for b in range(8):
             key |= ((cell >> np.uint32(b)) & np.uint32(1)) << np.uint32(4 * b + j)
     return key
@@ -269,8 +286,11 @@ def zorder_learned(n: int = 200_000_000, nq: int = 4096, sel_range=(1e-4, 0.05),
                    chunk: int = 1 << 24) -> Workload:
     """n x 4 float32: dims 0 and 2 uniform on [0,1); dims 1 and 3 lognormal(0, 1)
     normalised to [0,1) by (y - min) / (max - min) and clipped to [0, 0.99999994]. Rows
-    are sorted (stably) by the 32-bit Z-order key of the 4 dims. Complete-match queries,
-    target selectivity log-uniform in ``sel_range``, s^(1/4) per dimension by quantile."""
+    are sorted (stably) by the 32-bit Z-order key of the 4 dims over quantile cells
+    (each dimension's 256 cells cut at the quantiles of a 2^20-row sample, so that every
+    cell holds about n / 256 rows; ``key_bounds`` of the result). Complete-match
+    queries, target selectivity log-uniform in ``sel_range``, s^(1/4) per dimension by
+    quantile."""
     rng = rng_for(4, 0)
     cols = []
     for j in range(4):
@@ -287,7 +307,9 @@ def zorder_learned(n: int = 200_000_000, nq: int = 4096, sel_range=(1e-4, 0.05),
             del y
             np.clip(x, np.float32(0.0), np.float32(ONE_BELOW), out=x)
             cols.append(x)
-    key = zorder_key(cols)
+    crng = rng_for(4, 3)
+    bounds = [quantile_cell_bounds(c, crng) for c in cols]
+    key = zorder_key(cols, bounds)
     order = np.argsort(key, kind="stable")
     del key
     cols = [c[order] for c in cols]
@@ -301,8 +323,8 @@ def zorder_learned(n: int = 200_000_000, nq: int = 4096, sel_range=(1e-4, 0.05),
         qs.append(target_selectivity_query(samples, dtypes, [0, 1, 2, 3], s, qrng))
     return Workload("zorder_%dx4_f32" % n, cols, qs,
                     "n=%d d=4 f32 (2 U[0,1), 2 normalised lognormal(0,1)), rows sorted by the "
-                    "32-bit Z-order key; %d complete-match queries, target sel log-uniform "
-                    "[%g, %g]" % (n, nq, sel_range[0], sel_range[1]))
+                    "32-bit Z-order key over quantile cells; %d complete-match queries, target sel "
+                    "log-uniform [%g, %g]" % (n, nq, sel_range[0], sel_range[1]), key_bounds=bounds)
 
 
 def serving_table(n: int = 20_000_000, nq: int = 20_000, sel_range=(1e-5, 0.1)) -> Workload:

@@ -128,7 +128,7 @@ def test_zorder_full(M):
         ids, off = _answer_batch(M, t, wl.queries)
         _verify_every_query(M, wl.columns, wl.queries, ids, off, seed=3)
         for model in (M.MODEL_PLA, M.MODEL_MLP):
-            t.learn([0, 1, 2, 3], model)
+            t.learn([0, 1, 2, 3], model, cells=wl.key_bounds)
             t.set_batch_mode(M.BATCH_LEARNED)
             ids2, off2 = _answer_batch(M, t, wl.queries)
             assert _same_answers(ids, off, ids2, off2), model

@@ -10,11 +10,11 @@ from test_gpu_parity import M, _device  # noqa: F401
 pytestmark = pytest.mark.gpu
 
 
-def _learned_answers(M, cols_np, queries, model, dims=(0, 1, 2, 3)):
+def _learned_answers(M, cols_np, queries, model, dims=(0, 1, 2, 3), cells=None):
     import torch
     cols = _device(cols_np)
     with M.Table(cols) as t:
-        info = t.learn(list(dims), model)
+        info = t.learn(list(dims), model, cells=cells)
         t.set_batch_mode(M.BATCH_LEARNED)
         ids, off = t.query_batch(queries)
         torch.cuda.synchronize()
@@ -31,7 +31,7 @@ MODELS = pytest.mark.parametrize("model", [1, 2, 3], ids=["pla", "mlp", "none"])
 @MODELS
 def test_learned_matches_oracle_and_plain(M, model):
     wl = W.zorder_learned(n=2_000_003, nq=160)
-    info, got, off, plain, off_p = _learned_answers(M, wl.columns, wl.queries, model)
+    info, got, off, plain, off_p = _learned_answers(M, wl.columns, wl.queries, model, cells=wl.key_bounds)
     if model == 3:
         assert info["max_error"] == wl.n and info["segments"] == 0
     else:
@@ -56,7 +56,7 @@ def test_learned_partial_and_odd_queries(M, model):
            [(0, 0.0, 0.0)], [(3, 0.3, 0.3)], [(0, 0.1, 0.9), (0, 0.2, 0.3)]]
     r = int(rng.integers(0, wl.n))
     qs.append([(j, float(wl.columns[j][r]), float(wl.columns[j][r])) for j in range(4)])
-    info, got, off, plain, off_p = _learned_answers(M, wl.columns, qs, model)
+    info, got, off, plain, off_p = _learned_answers(M, wl.columns, qs, model, cells=wl.key_bounds)
     assert np.array_equal(off, off_p) and np.array_equal(got, plain)
     for q, query in enumerate(qs):
         want = oracle.mdrq(wl.columns, query, nthreads=8)
@@ -66,7 +66,7 @@ def test_learned_partial_and_odd_queries(M, model):
 @pytest.mark.parametrize("n", [1, 5, 4096, 4097, 70_001])
 def test_learned_small_tables(M, n):
     wl = W.zorder_learned(n=n, nq=24)
-    info, got, off, plain, off_p = _learned_answers(M, wl.columns, wl.queries, 1)
+    info, got, off, plain, off_p = _learned_answers(M, wl.columns, wl.queries, 1, cells=wl.key_bounds)
     assert np.array_equal(off, off_p) and np.array_equal(got, plain)
     for q, query in enumerate(wl.queries):
         assert np.array_equal(got[int(off[q]):int(off[q + 1])], oracle.mdrq(wl.columns, query, 2))
@@ -187,10 +187,10 @@ def test_max_error_recomputed_from_the_parameters(M, model):
     """mdrq_learn_info's error is the largest |prediction - row| over every key of the
     table: recomputed here on the CPU from the exported parameters, exhaustively."""
     wl = W.zorder_learned(n=1_000_003, nq=4)
-    keys = W.zorder_key(wl.columns).astype(np.int64)
+    keys = W.zorder_key(wl.columns, wl.key_bounds).astype(np.int64)
     assert np.all(np.diff(keys) >= 0)
     with M.Table(_device(wl.columns)) as t:
-        info = t.learn([0, 1, 2, 3], model)
+        info = t.learn([0, 1, 2, 3], model, cells=wl.key_bounds)
         exp = t.learn_export()
     assert exp["kind"] == model and exp["max_error"] == info["max_error"]
     pred = _pla_predict(exp, keys) if model == 1 else _mlp_predict(exp, keys)
@@ -211,10 +211,35 @@ def test_models_search_fewer_keys_than_no_model(M):
         t.set_batch_mode(M.BATCH_LEARNED)
         probes = {}
         for model in (1, 2, 3):
-            t.learn([0, 1, 2, 3], model)
+            t.learn([0, 1, 2, 3], model, cells=wl.key_bounds)
             t.query_batch(wl.queries)
             torch.cuda.synchronize()
             probes[model] = t.learn_search_info()
     ranges = {m: r for m, (r, _) in probes.items()}
     assert ranges[1] == ranges[2] == ranges[3] > 0
     assert probes[1][1] < probes[3][1] and probes[2][1] < probes[3][1], probes
+
+
+def test_equal_width_and_quantile_cells_both_exact(M):
+    """The same rows sorted by the equal-width key and by the quantile-cell key: each
+    table learned with its own cells answers exactly; a table learned with cells it is
+    not sorted by is refused; bad cell bounds are refused."""
+    import ctypes
+    wl = W.zorder_learned(n=400_003, nq=48)
+    for sort_cells in (None, wl.key_bounds):
+        key = W.zorder_key(wl.columns, sort_cells)
+        o = np.argsort(key, kind="stable")
+        cols = [c[o] for c in wl.columns]
+        info, got, off, plain, off_p = _learned_answers(M, cols, wl.queries, 1, cells=sort_cells)
+        assert np.array_equal(off, off_p) and np.array_equal(got, plain)
+        for q, query in enumerate(wl.queries):
+            assert np.array_equal(got[int(off[q]):int(off[q + 1])], oracle.mdrq(cols, query, 4)), q
+    with M.Table(_device(wl.columns)) as t:  # sorted by the quantile key, not the equal-width one
+        with pytest.raises(M.MDRQError) as e:
+            t.learn([0, 1, 2, 3], 1)
+        assert e.value.status == M.E_INVAL
+        bad = np.array(wl.key_bounds[0][::-1])  # descending
+        assert M.lib().mdrq_set_key_cells(t.handle, 0, bad.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                          255) == M.E_INVAL
+        assert M.lib().mdrq_set_key_cells(t.handle, 0, None, 7) == M.E_INVAL
+        assert M.lib().mdrq_set_key_cells(t.handle, 9, None, 0) == M.E_INVAL

@@ -86,7 +86,7 @@ def test_zorder_table_learned_and_plain(M):
     want = [oracle.mdrq(wl.columns, q, nthreads=16) for q in wl.queries]
     with M.Table(_device(wl.columns)) as t:
         assert all(t.zone_map_info(j)["used"] for j in range(4))
-        t.learn([0, 1, 2, 3], M.MODEL_PLA)
+        t.learn([0, 1, 2, 3], M.MODEL_PLA, cells=wl.key_bounds)
         for mode in (M.BATCH_LEARNED, M.BATCH_PLAIN):
             t.set_batch_mode(mode)
             ids, off = t.query_batch(wl.queries)

@@ -119,7 +119,7 @@ def test_zorder_key_interleaves_cells():
 def test_zorder_table_is_sorted_and_normalised():
     wl = W.zorder_learned(n=60_000, nq=16)
     assert wl.d == 4 and all(c.dtype == np.float32 for c in wl.columns)
-    key = W.zorder_key(wl.columns)
+    key = W.zorder_key(wl.columns, wl.key_bounds)
     assert np.all(key[1:] >= key[:-1])  # rows in key order
     for c in wl.columns:
         assert c.min() >= 0.0 and c.max() <= W.ONE_BELOW

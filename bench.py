@@ -879,7 +879,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
 
         e2e_s, e2e_kernel, same_d = e2e_run(mdrq.HOST_AUTO)
         st_s, st_kernel, same_s = e2e_run(mdrq.HOST_STAGED)
+        di_s, di_kernel, same_di = e2e_run(mdrq.HOST_DIRECT)
         table.set_host_answers(mdrq.HOST_AUTO)
+        auto_copies = e2e_kernel["scan_launches"] > args.steps  # AUTO took the staged copies
         npreds = sum(len(q) for q in wl.queries)
         e2e = {"value": world * nq * args.steps / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": 16 * npreds + 16 * nq,
@@ -888,8 +890,11 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
                "scan_kernel_ms_per_step": e2e_kernel["ms"] / args.steps,
                "launches_per_step": e2e_kernel["scan_launches"] / args.steps,
                "answers_identical_to_plain": same_d,
-               "path": "mdrq_query_batch with host query descriptors and a pinned host answer "
-                       "buffer, which the scan writes itself over the CPU-GPU link; host wall clock",
+               "path": ("mdrq_query_batch with host query descriptors and a pinned host answer "
+                        "buffer (MDRQ_HOST_AUTO: %s); host wall clock" %
+                        ("the batch's plain output is staged, so the ids are staged in device memory "
+                         "and each launch's are copied out on a second stream while the next runs"
+                         if auto_copies else "the scan writes the ids itself over the CPU-GPU link")),
                "bytes": "h2d: the host descriptors passed to the call (16 B per predicate and per "
                         "query; the library stages them as one copy of 16 B per query and 32 B per "
                         "kept predicate); d2h: the offsets and every id",
@@ -900,7 +905,15 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
                           "d2h_gbs_one_copy_alone": d2h_gbs(torch),
                           "answers_identical_to_plain": same_s,
                           "path": "the same call with the ids staged in device memory and copied "
-                                  "out per launch on a second stream (mdrq_set_host_answers STAGED)"}}
+                                  "out per launch on a second stream (mdrq_set_host_answers STAGED)"},
+               "direct": {"value": world * nq * args.steps / di_s, "unit": UNIT,
+                          "wall_ms_per_step": 1e3 * di_s / args.steps,
+                          "scan_kernel_ms_per_step": di_kernel["ms"] / args.steps,
+                          "launches_per_step": di_kernel["scan_launches"] / args.steps,
+                          "answers_identical_to_plain": same_di,
+                          "path": "the same call with the ids written into the pinned buffer by the "
+                                  "kernels over the CPU-GPU link (mdrq_set_host_answers DIRECT; with "
+                                  "staged output the ordering pass writes them, after the scan)"}}
         del host_ids
 
     # ---- roofline of the scan kernel: bytes / event-timed launch duration
@@ -915,6 +928,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
         dense_rule = ("4 B per row per constrained column over the rows of the tiles the zone "
                       "maps leave (%d rows per query) plus 4 B per id" % (zone_rows // max(1, nq)))
     avg_launch_s = timing["ms"] / 1e3 / launches
+    # a staged plain launch counts four kernels: the scan and the ordering pass's three
+    staged_output = args.workload != "zorder_learned" and timing["kernel_launches"] == 4 * launches
     vis = zone_candidates(table, cols_dev, wl.n) if zone_rows is not None else None
     alg_per_launch = early_break_bytes(table, cols_dev, wl.queries, wl.n, visited=vis)
     alg64_per_launch = early_break_bytes(table, cols_dev, wl.queries, wl.n, granule=64, visited=vis)
@@ -931,9 +946,13 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
                 "traffic": traffic,
                 "peak_source": peaks["source"] + " (HBM copy bandwidth)",
                 "kernel": ("mdrq_scan_window_kernel (plain batch over the tiles the zone maps leave)"
-                           if args.workload == "zorder_learned" else "mdrq_scan_kernel"),
+                           if args.workload == "zorder_learned" else
+                           "mdrq_scan_staged_kernel (plain batch, staged output; the three kernels of "
+                           "the ordering pass run after it, inside the step but outside this timing)"
+                           if staged_output else "mdrq_scan_kernel"),
                 "alg_bytes_per_launch": alg_per_launch, "alg_bytes_rule": alg_rule,
                 "avg_launch_ms": avg_launch_s * 1e3,
+                "ordering_pass_ms_per_step": (ms / args.steps - avg_launch_s * 1e3) if staged_output else 0.0,
                 "scan_launches": timing["scan_launches"],
                 "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
                 "traffic_over_alg_bytes": ratio,

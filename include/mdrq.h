@@ -118,8 +118,9 @@ int mdrq_load_columns(const void *const *cols, const int32_t *types, uint32_t d,
  *  ids            output, `capacity` uint32 slots; device memory when
  *                 ids_on_device = 1, host memory when 0. Host answers in page-locked
  *                 memory (cudaHostAlloc / cudaHostRegister, a pinned torch tensor) are
- *                 written by the scan kernels themselves over the CPU-GPU link (see
- *                 mdrq_set_host_answers). Other host memory goes through a device
+ *                 written by the scan kernels themselves over the CPU-GPU link, unless
+ *                 the batch's output is staged (see mdrq_set_host_answers and
+ *                 mdrq_set_output_order). Other host memory goes through a device
  *                 staging buffer of `capacity` ids that the table keeps; a plain batch
  *                 that scans at least 2 GiB of columns then runs as several launches
  *                 (up to 16, of equal query counts, on average at least 1 GiB of
@@ -158,7 +159,10 @@ int mdrq_query_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t 
  *  MDRQ_HOST_AUTO    (default) written by the scan itself when the buffer is page-locked
  *                    and mapped into the device's address space (on a GPU that shares a
  *                    coherent link with the CPU, as on GB300, the stores cross that link
- *                    at the scan's pace), staged otherwise;
+ *                    at the scan's pace), staged otherwise. A plain batch whose output
+ *                    is staged (mdrq_set_output_order) is ordered by a pass after each
+ *                    scan launch, so its ids are always staged and copied, each
+ *                    launch's while the next one runs;
  *  MDRQ_HOST_STAGED  always through the device staging buffer and copies;
  *  MDRQ_HOST_DIRECT  always written by the scan; calls with a buffer that is not
  *                    page-locked fail with MDRQ_E_INVAL.
@@ -168,6 +172,34 @@ int mdrq_query_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t 
 #define MDRQ_HOST_STAGED 1
 #define MDRQ_HOST_DIRECT 2
 int mdrq_set_host_answers(mdrq_table *t, int mode);
+
+/*
+ * mdrq_set_output_order — how a plain scan launch puts the partial results of its
+ * partitions (one row tile of one query each) into ascending order; the paper
+ * concatenates its partitions' results in partition order (Sec. 3.1).
+ *  MDRQ_ORDER_AUTO      (default) staged for a launch of at least 8 tiles per resident
+ *                       thread block (on GB300 about 8,500 tiles, e.g. 100 queries of
+ *                       1M rows or one query of 35M rows), look-back below that;
+ *  MDRQ_ORDER_LOOKBACK  each tile finds its place in the answer while the scan runs
+ *                       (single-pass decoupled look-back over the tiles' counts);
+ *                       nothing beyond the scratch of mdrq_load_columns is allocated;
+ *  MDRQ_ORDER_STAGED    each tile writes its ids to a device staging buffer of
+ *                       `capacity` ids plus an 8-byte record per tile (both kept by the
+ *                       table and grown as needed), and an ordering pass of three
+ *                       kernels after the scan copies every tile's ids into place: the
+ *                       ids are written twice, but no tile of the scan waits on another.
+ *                       A launch whose staging buffers cannot be allocated uses the
+ *                       look-back instead.
+ * Answers are identical in every order. It applies to plain launches (batch mode
+ * PLAIN, AUTO when that scans plainly, single queries and prepared batches); the
+ * zone-pruned, learned, shared and allocation-free paths order their output their own
+ * way, and the serving loop's plain batches use the look-back.
+ * Errors: MDRQ_E_INVAL (t NULL, unknown mode).
+ */
+#define MDRQ_ORDER_AUTO 0
+#define MDRQ_ORDER_LOOKBACK 1
+#define MDRQ_ORDER_STAGED 2
+int mdrq_set_output_order(mdrq_table *t, int mode);
 
 /* mdrq_free — release a table and its device memory (not caller-owned columns). NULL is
  * a no-op. Synchronises the device work the table still has in flight. */

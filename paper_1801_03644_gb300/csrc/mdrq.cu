@@ -311,6 +311,9 @@ constexpr uint64_t tile_rows()
     return (uint64_t)kWarps * U * 128;
 }
 
+// MDRQ_ORDER_AUTO stages a plain launch's output from this many tiles per resident block
+constexpr uint64_t kStagedMinTilesPerBlock = 8;
+
 // With event timing on (mdrq_scan_timing): the next event pair of the table, its first
 // event recorded on s; *evp stays null when timing is off.
 int timing_begin(mdrq_table *t, cudaStream_t s, cudaEvent_t **evp)
@@ -359,6 +362,22 @@ int launch_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t scanned_column
     // every launch starts its tile claims from zero
     MDRQ_TRY(cudaMemsetAsync(t->ticket, 0, sizeof(unsigned long long), s));
 
+    // Output order (mdrq_set_output_order): staged when the launch has many tiles in
+    // flight behind each resident block, where the look-back's chain of inclusive
+    // prefixes paces the whole launch; look-back when the staging buffers cannot be
+    // had, and always under fault injection (whose failure is a look-back wait).
+    bool staged = false;
+    if (t->inject_skip_tiles == 0 && t->output_order != MDRQ_ORDER_LOOKBACK &&
+        (t->output_order == MDRQ_ORDER_STAGED || total_tiles >= kStagedMinTilesPerBlock * resident)) {
+        staged = grow_device(reinterpret_cast<void **>(&t->cat_ids), &t->cat_ids_cap,
+                             std::max<uint64_t>(16, capacity * 4)) == MDRQ_OK &&
+                 grow_device(reinterpret_cast<void **>(&t->cat_rec), &t->cat_rec_cap, total_tiles * 8) == MDRQ_OK;
+        if (!staged)
+            (void)cudaGetLastError();
+    }
+    if (staged)
+        MDRQ_TRY(cudaMemsetAsync(t->cat_bump, 0, sizeof(unsigned long long), s));
+
     ScanParams p;
     std::memset(&p, 0, sizeof(p));
     p.queries = t->dq_dev + q0;
@@ -390,21 +409,41 @@ int launch_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t scanned_column
         if (st != MDRQ_OK)
             return st;
     }
-    if (ui == 2)
+    if (staged) {
+        // the scan writes each tile's ids to a run of the staging buffer; concat_staged
+        // below puts them in order into ids
+        p.bump = t->cat_bump;
+        p.tile_rec = t->cat_rec;
+        p.ids = t->cat_ids;
+        p.capacity = t->cat_ids_cap / 4;
+        if (ui == 2)
+            mdrq_scan_staged_kernel<4><<<grid, kScanThreads, 0, s>>>(p);
+        else if (ui == 1)
+            mdrq_scan_staged_kernel<2><<<grid, kScanThreads, 0, s>>>(p);
+        else
+            mdrq_scan_staged_kernel<1><<<grid, kScanThreads, 0, s>>>(p);
+    } else if (ui == 2) {
         mdrq_scan_kernel<4><<<grid, kScanThreads, 0, s>>>(p);
-    else if (ui == 1)
+    } else if (ui == 1) {
         mdrq_scan_kernel<2><<<grid, kScanThreads, 0, s>>>(p);
-    else
+    } else {
         mdrq_scan_kernel<1><<<grid, kScanThreads, 0, s>>>(p);
+    }
     MDRQ_TRY(cudaGetLastError());
     if (evp)
         MDRQ_TRY(cudaEventRecord(evp[1], s));
+    if (staged) {
+        const int st = concat_staged(t, total_tiles, (uint32_t)tiles_per_query, (uint32_t)rows, t->dq_dev + q0,
+                                     base_in, ids, capacity, s);
+        if (st != MDRQ_OK)
+            return st;
+    }
     t->tag_next += laps;
     t->last_launches += 1;
     t->last_bytes += scanned_columns * 4ull * t->n;
     if (t->timing) {
         t->acc_scans += 1;
-        t->acc_kernels += 1;
+        t->acc_kernels += staged ? 4 : 1;  // the scan and the three ordering kernels
         t->acc_bytes += scanned_columns * 4ull * t->n;
     }
     return MDRQ_OK;
@@ -484,7 +523,7 @@ void reset_scratch(mdrq_table *t, cudaStream_t s)
 {
     cudaStreamSynchronize(s);
     (void)cudaGetLastError();
-    cudaMemset(t->scratch, 0, (size_t)(2 + ((size_t)1 << t->ring_bits)) * 8);
+    cudaMemset(t->scratch, 0, (size_t)(3 + ((size_t)1 << t->ring_bits)) * 8);
     cudaDeviceSynchronize();
     (void)cudaGetLastError();
     t->tag_next = 1;
@@ -685,6 +724,29 @@ int finish_batch(mdrq_table *t, const std::vector<uint32_t> &live, uint32_t nq, 
     return MDRQ_OK;
 }
 
+// Whether a batch's live queries go to plain launches with staged output (the mode
+// choice of enqueue_batch and the order rule of launch_scan, for a single launch).
+static bool batch_output_staged(const mdrq_table *t, const std::vector<EncodedQuery> &enc,
+                                const std::vector<uint32_t> &live)
+{
+    const size_t nlive = live.size();
+    if (nlive == 0 || t->n == 0 || t->batch_mode == MDRQ_BATCH_LEARNED || t->output_order == MDRQ_ORDER_LOOKBACK)
+        return false;
+    const bool shared = t->batch_mode == MDRQ_BATCH_SHARED ||
+                        (t->batch_mode == MDRQ_BATCH_AUTO && nlive >= kAutoSharedMinQueries &&
+                         (t->auto_mode >= 0 ? t->auto_mode == MDRQ_BATCH_SHARED : t->n >= kAutoSharedMinRows));
+    if (shared)
+        return false;
+    for (uint32_t q : live)
+        for (const DevPred &dp : enc[q].preds)
+            if (dp.zone)
+                return false;  // tile pruning: a windowed launch
+    if (t->output_order == MDRQ_ORDER_STAGED)
+        return true;
+    const uint64_t tiles = (uint64_t)nlive * ((t->n + tile_rows<4>() - 1) / tile_rows<4>());
+    return tiles >= kStagedMinTilesPerBlock * (uint64_t)t->sm_count * t->blocks_per_sm[2];
+}
+
 int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, uint64_t capacity,
               uint64_t *offsets, int ids_on_device, cudaStream_t s)
 {
@@ -706,7 +768,12 @@ int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, u
     uint32_t *out = ids;
     HostSink sink;
     uint32_t *mapped = nullptr;  // the caller's page-locked buffer as the device sees it
-    if (!ids_on_device && capacity > 0 && t->host_answers != MDRQ_HOST_STAGED) {
+    // AUTO: a batch whose plain output is staged is ordered by a pass after each scan;
+    // its ids go through device staging and copies that overlap the next launch rather
+    // than crossing the CPU-GPU link from the ordering pass, after the scan
+    const bool via_copies = t->host_answers == MDRQ_HOST_STAGED ||
+                            (t->host_answers == MDRQ_HOST_AUTO && batch_output_staged(t, enc, live));
+    if (!ids_on_device && capacity > 0 && !via_copies) {
         cudaPointerAttributes a;
         if (cudaPointerGetAttributes(&a, ids) == cudaSuccess && a.type == cudaMemoryTypeHost && a.devicePointer)
             mapped = static_cast<uint32_t *>(a.devicePointer);
@@ -763,16 +830,17 @@ int run_batch(mdrq_table *t, const mdrq_qdesc *qs, uint32_t nq, uint32_t *ids, u
     return total > capacity ? MDRQ_E_CAPACITY : MDRQ_OK;
 }
 
-// scratch: claim counter, error word and a ring of 2^16 look-back states (512 KiB),
-// and the pinned error word
+// scratch: claim counter, error word, a ring of 2^16 look-back states (512 KiB) and the
+// staged output's allocation counter; and the pinned error word
 int alloc_scratch(mdrq_table *t, cudaStream_t s)
 {
     t->ring_bits = 16;
-    const size_t scratch_words = 2 + ((size_t)1 << t->ring_bits);
+    const size_t scratch_words = 3 + ((size_t)1 << t->ring_bits);
     MDRQ_TRY(cudaMalloc(&t->scratch, scratch_words * 8));
     t->ticket = t->scratch;
     t->error = reinterpret_cast<int *>(t->scratch + 1);
     t->tile_state = t->scratch + 2;
+    t->cat_bump = t->scratch + 2 + ((size_t)1 << t->ring_bits);
     MDRQ_TRY(cudaMemsetAsync(t->scratch, 0, scratch_words * 8, s));
     MDRQ_TRY(cudaMallocHost((void **)&t->error_host, sizeof(int)));
     return MDRQ_OK;
@@ -800,6 +868,7 @@ int make_shadow(const mdrq_table *t, cudaStream_t s, mdrq_table **out)
     sh->shared_bits_budget = t->shared_bits_budget;
     sh->auto_mode = t->auto_mode;
     sh->zone_mode = t->zone_mode;
+    sh->output_order = t->output_order;
     const int st = alloc_scratch(sh, s);
     if (st != MDRQ_OK) {
         free_shadow(sh);
@@ -835,6 +904,7 @@ void destroy(mdrq_table *t)
     learned_free(t);
     cudaFree(t->ids_stage);
     cudaFree(t->tile_map);
+    concat_free(t);
     if (t->sink_copy)
         cudaStreamDestroy(t->sink_copy);
     if (t->sink_done)
@@ -1144,6 +1214,14 @@ int mdrq_set_host_answers(mdrq_table *t, int mode)
     if (!t || (mode != MDRQ_HOST_AUTO && mode != MDRQ_HOST_STAGED && mode != MDRQ_HOST_DIRECT))
         return MDRQ_E_INVAL;
     t->host_answers = mode;
+    return MDRQ_OK;
+}
+
+int mdrq_set_output_order(mdrq_table *t, int mode)
+{
+    if (!t || (mode != MDRQ_ORDER_AUTO && mode != MDRQ_ORDER_LOOKBACK && mode != MDRQ_ORDER_STAGED))
+        return MDRQ_E_INVAL;
+    t->output_order = mode;
     return MDRQ_OK;
 }
 

@@ -32,6 +32,12 @@
 //    finish does it); one output warp drains the stages in order, resolves each tile's
 //    offset by look-back and writes the ids. The filter warps never wait on another
 //    tile or on each other.
+//  * Staged output (STAGED, large plain launches): instead of the look-back, each tile
+//    takes the next free run of a staging buffer with one atomic add and records where
+//    its ids went and how many there are; a concatenation pass afterwards (concat.cu)
+//    turns the tile counts into positions and copies every tile's ids into place. That
+//    is the paper's concatenation of partition results (Sec. 3.1) with tiles as the
+//    partitions: no tile waits on another, at the price of writing the ids twice.
 //  * Every wait (on another tile's state or on a stage) is bounded; on expiry the
 //    kernel records an error bit and finishes, never traps.
 #pragma once
@@ -114,7 +120,11 @@ struct ScanParams {
     const unsigned long long *nwindows_dev;  // windowed launches: number of windows (device)
     const unsigned long long *total_tiles_dev;  // windowed launches: tile count (device)
     const uint32_t *tile_map;        // windowed launches: the window of every tile (device)
+    unsigned long long *bump;        // staged output: ids staged so far by this launch (device)
+    unsigned long long *tile_rec;    // staged output: per tile, staging position << 13 | id count
 };
+
+constexpr int kRecCountBits = 13;  // a tile record's count field (a tile holds <= 4096 rows)
 
 // Where tile t of a launch lies: its query, its first row, the end of the rows it may
 // read, and whether it is the query's last tile.
@@ -421,14 +431,16 @@ constexpr unsigned long long kStopTile = ~0ull;  // "no more tiles" marker
 // claimed about one tile before it is processed and tiles are finished close to claim
 // order, which keeps look-back waits short. Slot reuse is safe with kStages + 1 slots:
 // a warp can run at most kStages iterations ahead of the output warp.
-template <int U, bool WINDOWED = false>
+template <int U, bool WINDOWED = false, bool STAGED = false>
 __device__ __forceinline__ void scan_cta(const ScanParams &p)
 {
+    static_assert(!(STAGED && WINDOWED), "staged output is for plain launches");
     static_assert(U >= 1 && U <= 4, "8-bit packed counts hold at most 4 groups");
     constexpr int kWarpRows = U * 128;
     constexpr int kTileRows = kWarps * kWarpRows;
     constexpr uint32_t kFullMask = (1u << (U * 4)) - 1u;
     static_assert(kTileRows <= 65536, "row offsets are staged as 16-bit values");
+    static_assert(kTileRows < (1 << kRecCountBits), "a tile's id count fits its record");
 
     __shared__ uint16_t s_stage[kStages][kTileRows];  // warp w: [w*kWarpRows, ...)
     __shared__ uint32_t s_warp_total[kStages][kWarps];
@@ -492,14 +504,26 @@ __device__ __forceinline__ void scan_cta(const ScanParams &p)
                     wincl += x;
             }
             const uint32_t total = __shfl_sync(0xffffffffu, wincl, kWarps - 1);
-            const unsigned long long excl = t == 0 ? 0ull : tile_lookback(p, t, total, lane);
-            if (lane == 0 && tp.last)
-                p.offsets[p.queries[tp.q].orig + 1] = base + excl + total;
+            unsigned long long excl;
+            if (STAGED) {
+                // the next free run of the staging buffer; the tile's place in the
+                // answer is set afterwards from the counts of all tiles
+                unsigned long long pos = 0;
+                if (lane == 0) {
+                    pos = atomicAdd(p.bump, (unsigned long long)total);
+                    p.tile_rec[t] = (pos << kRecCountBits) | total;
+                }
+                excl = __shfl_sync(0xffffffffu, pos, 0);
+            } else {
+                excl = t == 0 ? 0ull : tile_lookback(p, t, total, lane);
+                if (lane == 0 && tp.last)
+                    p.offsets[p.queries[tp.q].orig + 1] = base + excl + total;
+            }
             const uint32_t row0 = (uint32_t)tp.row0;
 #pragma unroll 1
             for (int w = 0; w < kWarps; ++w) {
                 const uint32_t cnt = __shfl_sync(0xffffffffu, wt, w);
-                const unsigned long long out0 = base + excl + __shfl_sync(0xffffffffu, wincl - wt, w);
+                const unsigned long long out0 = (STAGED ? 0ull : base) + excl + __shfl_sync(0xffffffffu, wincl - wt, w);
                 const uint16_t *seg = &s_stage[b][w * kWarpRows];
                 for (uint32_t r = lane; r < cnt; r += 32) {
                     const unsigned long long pos = out0 + r;
@@ -607,7 +631,7 @@ __device__ __forceinline__ void scan_cta(const ScanParams &p)
             // a tile, publishes its aggregate at once (the launch's first tile: its prefix)
             if (atomicAdd(&s_done[b], 1u) == kWarps - 1) {
                 __threadfence_block();
-                if (t != kStopTile) {
+                if (!STAGED && t != kStopTile) {
                     uint32_t total = 0;
 #pragma unroll
                     for (int w = 0; w < kWarps; ++w)
@@ -631,6 +655,13 @@ template <int U>
 __global__ void __launch_bounds__(kScanThreads, 7) mdrq_scan_kernel(const __grid_constant__ ScanParams p)
 {
     scan_cta<U, false>(p);
+}
+
+// The same with staged output (tile records and a staging buffer; concat.cu orders it).
+template <int U>
+__global__ void __launch_bounds__(kScanThreads, 7) mdrq_scan_staged_kernel(const __grid_constant__ ScanParams p)
+{
+    scan_cta<U, false, true>(p);
 }
 
 

@@ -419,6 +419,8 @@ int mdrq_server_start(mdrq_table *t, uint64_t result_bytes, uint32_t max_batch, 
             rc = make_shadow(t, S->stream[k], &S->plain[k]);
             if (rc == MDRQ_OK) {
                 S->plain[k]->batch_mode = MDRQ_BATCH_PLAIN;
+                // small latency-bound batches: ordered in the scan, no staging memory
+                S->plain[k]->output_order = MDRQ_ORDER_LOOKBACK;
                 rc = cuda_status(cudaMalloc(&S->scratch_ids[k], S->scratch_cap * 4));
             }
         }

@@ -60,7 +60,8 @@ struct mdrq_table {
     std::vector<mdrq::ColumnInfo> cols;
     std::vector<void *> owned;  // device columns this table allocated
 
-    // scratch: [0] claim counter, [1] error word, [2..] ring of look-back states
+    // scratch: [0] claim counter, [1] error word, [2 .. 2 + ring) look-back states,
+    // [2 + ring] the staged output's allocation counter
     unsigned long long *scratch = nullptr;
     unsigned long long *ticket = nullptr;
     int *error = nullptr;
@@ -84,6 +85,15 @@ struct mdrq_table {
     size_t ids_stage_cap = 0;
     uint32_t *tile_map = nullptr;   // windowed launches: the window of every tile
     size_t tile_map_cap = 0;
+    // staged output of large plain launches (scan_kernel.cuh STAGED, concat.cu)
+    int output_order = MDRQ_ORDER_AUTO;  // mdrq_set_output_order
+    uint32_t *cat_ids = nullptr;          // staging runs of the tiles' ids
+    size_t cat_ids_cap = 0;               // bytes
+    unsigned long long *cat_rec = nullptr;  // per tile: staging position << 13 | id count
+    size_t cat_rec_cap = 0;
+    unsigned long long *cat_seg = nullptr;  // per segment of 2048 tiles: id count, then prefix
+    size_t cat_seg_cap = 0;
+    unsigned long long *cat_bump = nullptr;  // in scratch: ids staged so far by the launch
     cudaStream_t sink_copy = nullptr;  // copies of host answers out of the staging buffer
     cudaEvent_t sink_done = nullptr;
     unsigned long long *sink_end = nullptr;  // pinned
@@ -194,6 +204,14 @@ int zone_batch(mdrq_table *t, uint32_t q0, uint32_t nlive, uint64_t scanned_colu
                uint64_t capacity, const unsigned long long *base_in, cudaStream_t s);
 void zone_windows_free(mdrq_table *t);
 int zone_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *tiles);
+
+// concat.cu: order the staged output of a plain launch of ntiles tiles of tile_rows rows (t->cat_rec,
+// t->cat_ids) into ids (CSR from *base_in, or 0) and write the CSR end of every query
+// of the launch (queries: the launch's query table, tiles_per_query tiles each)
+int concat_staged(mdrq_table *t, uint64_t ntiles, uint32_t tiles_per_query, uint32_t tile_rows,
+                  const DevQuery *queries, const unsigned long long *base_in, uint32_t *ids, uint64_t capacity,
+                  cudaStream_t s);
+void concat_free(mdrq_table *t);
 
 // learned.cu
 int learn(mdrq_table *t, const uint32_t *dims, uint32_t ndims, int kind, cudaStream_t s);

@@ -63,6 +63,7 @@ EXPORTS = ["mdrq_load_columns", "mdrq_query", "mdrq_query_batch", "mdrq_free",
            "mdrq_set_zone_maps", "mdrq_zone_map_info", "mdrq_zone_scan_info",
            "mdrq_server_submit_batch", "mdrq_server_wait_many", "mdrq_explain_query",
            "mdrq_learn_search_info", "mdrq_learn_export", "mdrq_set_host_answers", "mdrq_set_shared_codes",
+           "mdrq_set_output_order",
            "mdrq_set_key_cells"]
 
 FAULT_SKIP_TILES, FAULT_NOMEM = 1, 2
@@ -70,6 +71,7 @@ BATCH_AUTO, BATCH_PLAIN, BATCH_SHARED, BATCH_LEARNED = 0, 1, 2, 3
 MODEL_PLA, MODEL_MLP, MODEL_NONE = 1, 2, 3
 ZONES_OFF, ZONES_AUTO, ZONES_ALL = 0, 1, 2
 HOST_AUTO, HOST_STAGED, HOST_DIRECT = 0, 1, 2
+ORDER_AUTO, ORDER_LOOKBACK, ORDER_STAGED = 0, 1, 2
 
 STATIC_MAX_ROWS = 1 << 28  # MDRQ_STATIC_MAX_ROWS
 
@@ -118,6 +120,8 @@ def lib():
         L.mdrq_set_shared_codes.argtypes = [vp, ctypes.c_int]
         L.mdrq_set_host_answers.restype = ctypes.c_int
         L.mdrq_set_host_answers.argtypes = [vp, ctypes.c_int]
+        L.mdrq_set_output_order.restype = ctypes.c_int
+        L.mdrq_set_output_order.argtypes = [vp, ctypes.c_int]
         L.mdrq_learn_export.restype = ctypes.c_int
         L.mdrq_learn_export.argtypes = [vp, ctypes.POINTER(ModelDesc), ctypes.POINTER(u64), ctypes.POINTER(u64),
                                         ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), u32]
@@ -425,6 +429,12 @@ class Table:
         st = lib().mdrq_set_host_answers(self._h, int(mode))
         if st != OK:
             raise MDRQError(st, "mdrq_set_host_answers")
+
+    def set_output_order(self, mode: int):
+        """``mdrq_set_output_order``: ORDER_AUTO, ORDER_LOOKBACK or ORDER_STAGED."""
+        st = lib().mdrq_set_output_order(self._h, int(mode))
+        if st != OK:
+            raise MDRQError(st, "mdrq_set_output_order")
 
     def set_zone_maps(self, mode: int):
         """``mdrq_set_zone_maps``: ZONES_OFF, ZONES_AUTO or ZONES_ALL."""

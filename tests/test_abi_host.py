@@ -180,4 +180,5 @@ def test_every_handle_call_rejects_null(L):
     assert L.mdrq_learn_export(None, ctypes.byref(desc), None, None, None, None, 0) == E
     assert L.mdrq_set_host_answers(None, mdrq.HOST_AUTO) == E
     assert L.mdrq_set_shared_codes(None, 1) == E
+    assert L.mdrq_set_output_order(None, mdrq.ORDER_AUTO) == E
     assert L.mdrq_set_key_cells(None, 0, None, 0) == E

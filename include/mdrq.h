@@ -177,23 +177,31 @@ int mdrq_set_host_answers(mdrq_table *t, int mode);
  * mdrq_set_output_order — how a plain scan launch puts the partial results of its
  * partitions (one row tile of one query each) into ascending order; the paper
  * concatenates its partitions' results in partition order (Sec. 3.1).
- *  MDRQ_ORDER_AUTO      (default) staged for a launch of at least 8 tiles per resident
- *                       thread block (on GB300 about 8,500 tiles, e.g. 100 queries of
- *                       1M rows or one query of 35M rows), look-back below that;
+ *  MDRQ_ORDER_AUTO      (default) staged for a plain launch of at least 8 tiles per
+ *                       resident thread block (on GB300 about 8,500 tiles, e.g. 100
+ *                       queries of 1M rows or one query of 35M rows), look-back below
+ *                       that and for windowed launches;
  *  MDRQ_ORDER_LOOKBACK  each tile finds its place in the answer while the scan runs
  *                       (single-pass decoupled look-back over the tiles' counts);
  *                       nothing beyond the scratch of mdrq_load_columns is allocated;
  *  MDRQ_ORDER_STAGED    each tile writes its ids to a device staging buffer of
- *                       `capacity` ids plus an 8-byte record per tile (both kept by the
- *                       table and grown as needed), and an ordering pass of three
+ *                       `capacity` ids plus 3 per tile (a tile's run is padded to a
+ *                       multiple of 4 ids) and an 8-byte record per tile (both kept by
+ *                       the table and grown as needed), and an ordering pass of three
  *                       kernels after the scan copies every tile's ids into place: the
  *                       ids are written twice, but no tile of the scan waits on another.
  *                       A launch whose staging buffers cannot be allocated uses the
  *                       look-back instead.
- * Answers are identical in every order. It applies to plain launches (batch mode
- * PLAIN, AUTO when that scans plainly, single queries and prepared batches); the
- * zone-pruned, learned, shared and allocation-free paths order their output their own
- * way, and the serving loop's plain batches use the look-back.
+ * Answers are identical in every order. It applies to the plain scan's launches (batch
+ * mode PLAIN, AUTO when that scans plainly, single queries, prepared batches) and to
+ * the windowed launches of tile pruning (mdrq_set_zone_maps) and of the learned
+ * narrower (MDRQ_BATCH_LEARNED), which are staged only under MDRQ_ORDER_STAGED: they
+ * read few rows per id they write, so the second write of the ids costs more than the
+ * look-back saves. A staged windowed launch sizes its tile records by its upper bound
+ * of tiles (every tile of every query plus one per window), since its tile count is
+ * known only on the device. The shared and allocation-free
+ * paths order their output their own way, and the serving loop's plain batches use
+ * the look-back.
  * Errors: MDRQ_E_INVAL (t NULL, unknown mode).
  */
 #define MDRQ_ORDER_AUTO 0

@@ -5,7 +5,8 @@
 // ascending order. Here a partition is a row tile of one query; the scan wrote each
 // tile's ids (ascending within the tile) to a run of a staging buffer in whatever order
 // the tiles finished, and recorded per tile rec[t] = staging position << 13 | id count.
-// Because the tiles of a launch are numbered query-major and ascending in rows, the
+// Because the tiles of a launch are numbered query-major and ascending in rows (a
+// windowed launch's tiles follow its windows, which run in query and row order), the
 // answer is the concatenation of the tiles' runs in tile order:
 //   dst(t) = base + sum of the counts of tiles 0 .. t-1,
 //   offsets[orig(q) + 1] = dst(last tile of q) + its count  (the CSR end of query q).
@@ -34,6 +35,9 @@ constexpr int kCatPerThread = 8;
 constexpr int kCatSeg = kCatThreads * kCatPerThread;  // 2048 tiles per segment
 constexpr unsigned long long kRecCountMask = (1ull << kRecCountBits) - 1;
 constexpr uint32_t kSmallRun = 8;  // runs this short are copied by one lane
+
+__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
 
 // sum over the block (every thread gets it)
 __device__ __forceinline__ unsigned long long block_sum(unsigned long long v, unsigned long long *s_w)
@@ -80,10 +84,14 @@ __device__ __forceinline__ unsigned long long block_excl(unsigned long long v, u
     return before + incl - v;
 }
 
-__global__ void __launch_bounds__(kCatThreads)
-    mdrq_concat_count_kernel(const unsigned long long *rec, uint64_t ntiles, unsigned long long *seg_sum)
+// ntiles_dev: the launch's tile count on the device (windowed launches), else null
+__global__ void __launch_bounds__(kCatThreads) mdrq_concat_count_kernel(const unsigned long long *rec, uint64_t ntiles,
+                                                                        const unsigned long long *ntiles_dev,
+                                                                        unsigned long long *seg_sum)
 {
     __shared__ unsigned long long s_w[kCatThreads / 32];
+    if (ntiles_dev)
+        ntiles = umin64(ntiles, *ntiles_dev);
     const uint64_t s0 = (uint64_t)blockIdx.x * kCatSeg;
     unsigned long long c = 0;
 #pragma unroll
@@ -117,7 +125,10 @@ __global__ void __launch_bounds__(kCatThreads) mdrq_concat_scan_kernel(unsigned 
 
 struct ConcatParams {
     const unsigned long long *rec;       // per tile: staging position << 13 | id count
-    uint64_t ntiles;
+    uint64_t ntiles;                     // tiles (windowed: an upper bound)
+    const unsigned long long *ntiles_dev;  // windowed: the tile count (device), else null
+    const uint32_t *tile_map;            // windowed: the window of every tile, else null
+    const DevWindow *windows;            // windowed: the launch's windows
     const unsigned long long *seg_base;  // exclusive prefix of the segments' id counts
     uint32_t tiles_per_query;
     uint32_t tile_rows;
@@ -143,14 +154,42 @@ __device__ __forceinline__ bool pred_holds(uint32_t x, const DevPred &pr)
     return (int)pr.lo <= v && v <= (int)pr.hi;
 }
 
-// One warp writes the ids of tile t (query q, local tile rt) from dst on, recomputing
-// them: 32 rows per step, each row tested against every predicate of the query.
-__device__ void rescan_tile(const ConcatParams &cp, uint64_t q, uint32_t rt, unsigned long long dst, int lane)
+// Where tile t lies: its query (an index into cp.queries), whether it is the query's
+// last tile, and the rows [*r0, *r1) it covers.
+struct TileSpot {
+    uint64_t q;
+    bool last;
+    uint64_t r0, r1;
+};
+
+__device__ __forceinline__ TileSpot tile_spot(const ConcatParams &cp, uint64_t t)
 {
-    const DevQuery dq = cp.queries[q];
-    const uint64_t row0 = (uint64_t)rt * cp.tile_rows;
-    const uint64_t row_end = min(row0 + cp.tile_rows, cp.n);
-    for (uint64_t r0 = row0; r0 < row_end; r0 += 32) {
+    TileSpot ts;
+    if (cp.tile_map) {
+        const DevWindow w = cp.windows[cp.tile_map[t]];
+        const uint64_t rt = t - w.tile_start;
+        const uint64_t a = w.row_begin + rt * cp.tile_rows;
+        ts.q = w.query;
+        ts.last = w.last && rt == w.tiles - 1;
+        ts.r0 = umax64(a, w.row_first);
+        ts.r1 = umin64(a + cp.tile_rows, w.row_end);
+    } else {
+        ts.q = t / cp.tiles_per_query;
+        const uint64_t rt = t - ts.q * cp.tiles_per_query;
+        ts.last = rt == cp.tiles_per_query - 1;
+        ts.r0 = rt * cp.tile_rows;
+        ts.r1 = umin64(ts.r0 + cp.tile_rows, cp.n);
+    }
+    return ts;
+}
+
+// One warp writes the ids of one tile from dst on, recomputing them: 32 rows per step,
+// each row tested against every predicate of the tile's query.
+__device__ void rescan_tile(const ConcatParams &cp, const TileSpot &ts, unsigned long long dst, int lane)
+{
+    const DevQuery dq = cp.queries[ts.q];
+    const uint64_t row_end = ts.r1;
+    for (uint64_t r0 = ts.r0; r0 < row_end; r0 += 32) {
         const uint64_t row = r0 + lane;
         bool ok = row < row_end;
         for (uint32_t i = 0; i < dq.npred && __any_sync(0xffffffffu, ok); ++i) {
@@ -170,8 +209,10 @@ __device__ void rescan_tile(const ConcatParams &cp, uint64_t q, uint32_t rt, uns
 __global__ void __launch_bounds__(kCatThreads) mdrq_concat_kernel(const __grid_constant__ ConcatParams cp)
 {
     const unsigned long long *__restrict__ rec = cp.rec;
-    const uint64_t ntiles = cp.ntiles;
+    const uint64_t ntiles = cp.ntiles_dev ? umin64(cp.ntiles, *cp.ntiles_dev) : cp.ntiles;
     const uint32_t tiles_per_query = cp.tiles_per_query;
+    if ((uint64_t)blockIdx.x * kCatSeg >= ntiles)
+        return;  // (windowed launches: the grid covers the upper bound)
     const uint32_t *__restrict__ stage = cp.stage;
     const uint64_t stage_cap = cp.stage_cap;
     uint32_t *__restrict__ ids = cp.ids;
@@ -198,7 +239,7 @@ __global__ void __launch_bounds__(kCatThreads) mdrq_concat_kernel(const __grid_c
     unsigned long long seg_total;
     uint32_t r = (uint32_t)block_excl(mine, s_w, &seg_total);
     const unsigned long long base = (cp.base_in ? *cp.base_in : 0ull) + cp.seg_base[blockIdx.x];
-    if (j0 < nt) {
+    if (j0 < nt && !cp.tile_map) {
         const uint64_t t0 = s0 + j0;
         uint64_t q = t0 / tiles_per_query;
         uint32_t rt = (uint32_t)(t0 - q * tiles_per_query);
@@ -213,6 +254,17 @@ __global__ void __launch_bounds__(kCatThreads) mdrq_concat_kernel(const __grid_c
                 ++q;
             }
         }
+    } else if (j0 < nt) {
+#pragma unroll
+        for (int k = 0; k < kCatPerThread; ++k) {
+            s_rel[j0 + k] = r;
+            if (j0 + k < nt) {
+                const TileSpot ts = tile_spot(cp, s0 + j0 + k);
+                if (ts.last)
+                    cp.offsets[cp.queries[ts.q].orig + 1] = base + r + c[k];
+            }
+            r += c[k];
+        }
     }
     __syncthreads();
 
@@ -225,52 +277,57 @@ __global__ void __launch_bounds__(kCatThreads) mdrq_concat_kernel(const __grid_c
         const uint32_t cnt = (uint32_t)(rc & kRecCountMask);
         const uint64_t pos = rc >> kRecCountBits;
         const unsigned long long dst = base + s_rel[j];
-        // a run that did not fit the staging buffer whole: recompute it (rare)
-        const bool lost = cnt > 0 && pos + cnt > stage_cap && dst < capacity;
+        // runs start on 16-byte boundaries and take a multiple of 4 ids; one that did not
+        // fit the staging buffer whole is recomputed (rare)
+        const bool staged = pos + ((cnt + 3u) & ~3u) <= stage_cap;
+        const bool lost = cnt > 0 && !staged && dst < capacity;
         uint32_t lost_mask = __ballot_sync(0xffffffffu, lost);
         while (lost_mask) {
             const int l = __ffs(lost_mask) - 1;
             lost_mask &= lost_mask - 1;
-            const uint64_t tl = s0 + g * 32 + l;
-            const uint64_t ql = tl / tiles_per_query;
-            rescan_tile(cp, ql, (uint32_t)(tl - ql * tiles_per_query), __shfl_sync(0xffffffffu, dst, l), lane);
+            rescan_tile(cp, tile_spot(cp, s0 + g * 32 + l), __shfl_sync(0xffffffffu, dst, l), lane);
         }
-        if (cnt <= kSmallRun && !lost) {
-            uint32_t v[kSmallRun];
+        if (cnt > 0 && cnt <= kSmallRun && staged) {
+            // one or two 16-byte loads
+            const uint4 a = ld_stream_v4(stage + pos);
+            const uint4 b = cnt > 4 ? ld_stream_v4(stage + pos + 4) : make_uint4(0, 0, 0, 0);
+            const uint32_t v[kSmallRun] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 #pragma unroll
             for (uint32_t i = 0; i < kSmallRun; ++i)
-                if (i < cnt && pos + i < stage_cap)
-                    v[i] = ld_stream_u32(stage + pos + i);
-#pragma unroll
-            for (uint32_t i = 0; i < kSmallRun; ++i)
-                if (i < cnt && pos + i < stage_cap && dst + i < capacity)
+                if (i < cnt && dst + i < capacity)
                     ids[dst + i] = v[i];
         }
-        uint32_t big = __ballot_sync(0xffffffffu, cnt > kSmallRun && !lost);
+        uint32_t big = __ballot_sync(0xffffffffu, cnt > kSmallRun && staged);
         while (big) {
             const int l = __ffs(big) - 1;
             big &= big - 1;
             const uint32_t bc = __shfl_sync(0xffffffffu, cnt, l);
             const uint64_t bp = __shfl_sync(0xffffffffu, pos, l);
             const unsigned long long bd = __shfl_sync(0xffffffffu, dst, l);
-            for (uint32_t i = lane; i < bc; i += 128) {
-                uint32_t v[4];
+            // lane l: ids 4l .. 4l + 3 of every 128, four 16-byte loads in flight
+            for (uint32_t i = 4 * lane; i < bc; i += 512) {
+                uint4 v[4];
 #pragma unroll
                 for (uint32_t u = 0; u < 4; ++u)
-                    if (i + 32 * u < bc && bp + i + 32 * u < stage_cap)
-                        v[u] = ld_stream_u32(stage + bp + i + 32 * u);
+                    if (i + 128 * u < bc)
+                        v[u] = ld_stream_v4(stage + bp + i + 128 * u);
 #pragma unroll
-                for (uint32_t u = 0; u < 4; ++u)
-                    if (i + 32 * u < bc && bp + i + 32 * u < stage_cap && bd + i + 32 * u < capacity)
-                        ids[bd + i + 32 * u] = v[u];
+                for (uint32_t u = 0; u < 4; ++u) {
+                    const uint32_t k = i + 128 * u;
+                    const uint32_t e[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                    for (uint32_t x = 0; x < 4; ++x)
+                        if (k + x < bc && bd + k + x < capacity)
+                            ids[bd + k + x] = e[x];
+                }
             }
         }
     }
 }
 
-int concat_staged(mdrq_table *t, uint64_t ntiles, uint32_t tiles_per_query, uint32_t tile_rows,
-                  const DevQuery *queries, const unsigned long long *base_in, uint32_t *ids, uint64_t capacity,
-                  cudaStream_t s)
+int concat_staged(mdrq_table *t, uint64_t ntiles, const unsigned long long *ntiles_dev, uint32_t tiles_per_query,
+                  uint32_t tile_rows, const DevQuery *queries, const uint32_t *tile_map, const DevWindow *windows,
+                  const unsigned long long *base_in, uint32_t *ids, uint64_t capacity, cudaStream_t s)
 {
     const uint64_t nseg = (ntiles + kCatSeg - 1) / kCatSeg;
     if (nseg == 0)
@@ -278,11 +335,14 @@ int concat_staged(mdrq_table *t, uint64_t ntiles, uint32_t tiles_per_query, uint
     const int st = grow_device(reinterpret_cast<void **>(&t->cat_seg), &t->cat_seg_cap, (nseg + 1) * 8);
     if (st != MDRQ_OK)
         return st;
-    mdrq_concat_count_kernel<<<(unsigned)nseg, kCatThreads, 0, s>>>(t->cat_rec, ntiles, t->cat_seg);
+    mdrq_concat_count_kernel<<<(unsigned)nseg, kCatThreads, 0, s>>>(t->cat_rec, ntiles, ntiles_dev, t->cat_seg);
     mdrq_concat_scan_kernel<<<1, kCatThreads, 0, s>>>(t->cat_seg, nseg);
     ConcatParams cp;
     cp.rec = t->cat_rec;
     cp.ntiles = ntiles;
+    cp.ntiles_dev = ntiles_dev;
+    cp.tile_map = tile_map;
+    cp.windows = windows;
     cp.seg_base = t->cat_seg;
     cp.tiles_per_query = tiles_per_query;
     cp.tile_rows = tile_rows;

@@ -44,6 +44,13 @@ __global__ void __launch_bounds__(kScanThreads, 7) mdrq_scan_window_kernel(const
     scan_cta<4, true>(p);
 }
 
+// The same with staged output (concat.cu orders it by the launch's tile map).
+__global__ void __launch_bounds__(kScanThreads, 7)
+    mdrq_scan_window_staged_kernel(const __grid_constant__ ScanParams p)
+{
+    scan_cta<4, true, true>(p);
+}
+
 // NaN count, minimum and maximum of a column. out[0] += NaNs; out[1] / out[2] hold the
 // minimum / maximum as order-preserving keys (see key_of).
 __device__ __forceinline__ unsigned long long key_of(uint32_t bits, uint32_t type)
@@ -369,8 +376,9 @@ int launch_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t scanned_column
     bool staged = false;
     if (t->inject_skip_tiles == 0 && t->output_order != MDRQ_ORDER_LOOKBACK &&
         (t->output_order == MDRQ_ORDER_STAGED || total_tiles >= kStagedMinTilesPerBlock * resident)) {
+        // (each tile's run is padded to a multiple of 4 ids)
         staged = grow_device(reinterpret_cast<void **>(&t->cat_ids), &t->cat_ids_cap,
-                             std::max<uint64_t>(16, capacity * 4)) == MDRQ_OK &&
+                             std::max<uint64_t>(16, (capacity + 3 * total_tiles) * 4)) == MDRQ_OK &&
                  grow_device(reinterpret_cast<void **>(&t->cat_rec), &t->cat_rec_cap, total_tiles * 8) == MDRQ_OK;
         if (!staged)
             (void)cudaGetLastError();
@@ -433,8 +441,8 @@ int launch_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t scanned_column
     if (evp)
         MDRQ_TRY(cudaEventRecord(evp[1], s));
     if (staged) {
-        const int st = concat_staged(t, total_tiles, (uint32_t)tiles_per_query, (uint32_t)rows, t->dq_dev + q0,
-                                     base_in, ids, capacity, s);
+        const int st = concat_staged(t, total_tiles, nullptr, (uint32_t)tiles_per_query, (uint32_t)rows,
+                                     t->dq_dev + q0, nullptr, nullptr, base_in, ids, capacity, s);
         if (st != MDRQ_OK)
             return st;
     }
@@ -477,6 +485,20 @@ int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t max_win
     }
     mdrq_tile_map_kernel<<<(uint32_t)t->sm_count * 8, 256, 0, s>>>(windows, nwindows, t->tile_map);
     MDRQ_TRY(cudaMemsetAsync(t->ticket, 0, sizeof(unsigned long long), s));
+    // Output order: staged only on request. A windowed launch reads few rows per id it
+    // writes (the Z-sorted bench: 26.6 GB of ids for about 300 GB of column sectors), so
+    // writing the ids a second time cost more than the look-back did (tile pruning 55.3
+    // against 49.4 ms, learned windows 53.8 against 48.4 ms).
+    bool staged = false;
+    if (t->inject_skip_tiles == 0 && t->output_order == MDRQ_ORDER_STAGED) {
+        staged = grow_device(reinterpret_cast<void **>(&t->cat_ids), &t->cat_ids_cap,
+                             std::max<uint64_t>(16, (capacity + 3 * max_tiles) * 4)) == MDRQ_OK &&
+                 grow_device(reinterpret_cast<void **>(&t->cat_rec), &t->cat_rec_cap, max_tiles * 8) == MDRQ_OK;
+        if (!staged)
+            (void)cudaGetLastError();
+    }
+    if (staged)
+        MDRQ_TRY(cudaMemsetAsync(t->cat_bump, 0, sizeof(unsigned long long), s));
     ScanParams p;
     std::memset(&p, 0, sizeof(p));
     p.queries = t->dq_dev + q0;
@@ -503,16 +525,30 @@ int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t max_win
         if (st != MDRQ_OK)
             return st;
     }
-    mdrq_scan_window_kernel<<<grid, kScanThreads, 0, s>>>(p);
+    if (staged) {
+        p.bump = t->cat_bump;
+        p.tile_rec = t->cat_rec;
+        p.ids = t->cat_ids;
+        p.capacity = t->cat_ids_cap / 4;
+        mdrq_scan_window_staged_kernel<<<grid, kScanThreads, 0, s>>>(p);
+    } else {
+        mdrq_scan_window_kernel<<<grid, kScanThreads, 0, s>>>(p);
+    }
     MDRQ_TRY(cudaGetLastError());
     if (evp)
         MDRQ_TRY(cudaEventRecord(evp[1], s));
+    if (staged) {
+        const int st = concat_staged(t, max_tiles, total_tiles, 0, (uint32_t)tile_rows<4>(), t->dq_dev + q0,
+                                     t->tile_map, windows, base_in, ids, capacity, s);
+        if (st != MDRQ_OK)
+            return st;
+    }
     t->tag_next += laps;
     t->last_launches += 1;
     t->last_bytes += alg_bytes;
     if (t->timing) {
         t->acc_scans += 1;
-        t->acc_kernels += 2 + helper_kernels;  // the tile map and the scan
+        t->acc_kernels += 2 + helper_kernels + (staged ? 3 : 0);  // tile map, scan, ordering pass
         t->acc_bytes += alg_bytes;
     }
     return MDRQ_OK;

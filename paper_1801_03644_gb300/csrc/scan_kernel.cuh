@@ -32,7 +32,7 @@
 //    finish does it); one output warp drains the stages in order, resolves each tile's
 //    offset by look-back and writes the ids. The filter warps never wait on another
 //    tile or on each other.
-//  * Staged output (STAGED, large plain launches): instead of the look-back, each tile
+//  * Staged output (STAGED, large launches): instead of the look-back, each tile
 //    takes the next free run of a staging buffer with one atomic add and records where
 //    its ids went and how many there are; a concatenation pass afterwards (concat.cu)
 //    turns the tile counts into positions and copies every tile's ids into place. That
@@ -434,7 +434,6 @@ constexpr unsigned long long kStopTile = ~0ull;  // "no more tiles" marker
 template <int U, bool WINDOWED = false, bool STAGED = false>
 __device__ __forceinline__ void scan_cta(const ScanParams &p)
 {
-    static_assert(!(STAGED && WINDOWED), "staged output is for plain launches");
     static_assert(U >= 1 && U <= 4, "8-bit packed counts hold at most 4 groups");
     constexpr int kWarpRows = U * 128;
     constexpr int kTileRows = kWarps * kWarpRows;
@@ -510,7 +509,8 @@ __device__ __forceinline__ void scan_cta(const ScanParams &p)
                 // answer is set afterwards from the counts of all tiles
                 unsigned long long pos = 0;
                 if (lane == 0) {
-                    pos = atomicAdd(p.bump, (unsigned long long)total);
+                    // runs start on 16-byte boundaries, for the ordering pass's loads
+                    pos = atomicAdd(p.bump, (unsigned long long)((total + 3u) & ~3u));
                     p.tile_rec[t] = (pos << kRecCountBits) | total;
                 }
                 excl = __shfl_sync(0xffffffffu, pos, 0);

@@ -205,12 +205,14 @@ int zone_batch(mdrq_table *t, uint32_t q0, uint32_t nlive, uint64_t scanned_colu
 void zone_windows_free(mdrq_table *t);
 int zone_window_rows(mdrq_table *t, uint64_t *rows, uint64_t *tiles);
 
-// concat.cu: order the staged output of a plain launch of ntiles tiles of tile_rows rows (t->cat_rec,
-// t->cat_ids) into ids (CSR from *base_in, or 0) and write the CSR end of every query
-// of the launch (queries: the launch's query table, tiles_per_query tiles each)
-int concat_staged(mdrq_table *t, uint64_t ntiles, uint32_t tiles_per_query, uint32_t tile_rows,
-                  const DevQuery *queries, const unsigned long long *base_in, uint32_t *ids, uint64_t capacity,
-                  cudaStream_t s);
+// concat.cu: order the staged output of a launch (t->cat_rec, t->cat_ids) into ids (CSR
+// from *base_in, or 0) and write the CSR end of every query of the launch (queries: the
+// launch's query table). Plain launch: ntiles tiles of tile_rows rows, tiles_per_query
+// per query; ntiles_dev, tile_map and windows null. Windowed launch: at most ntiles
+// tiles, the count in *ntiles_dev, placed by tile_map and windows (device).
+int concat_staged(mdrq_table *t, uint64_t ntiles, const unsigned long long *ntiles_dev, uint32_t tiles_per_query,
+                  uint32_t tile_rows, const DevQuery *queries, const uint32_t *tile_map, const DevWindow *windows,
+                  const unsigned long long *base_in, uint32_t *ids, uint64_t capacity, cudaStream_t s);
 void concat_free(mdrq_table *t);
 
 // learned.cu

@@ -1,7 +1,8 @@
-"""Output orders of the plain scan (mdrq_set_output_order): look-back and staged give the
+"""Output orders of the scan (mdrq_set_output_order): look-back and staged give the
 oracle's answers id for id, on ragged sizes, skewed and mixed-type tables, short answer
 buffers (tiles that miss the staging buffer are recomputed), host answers split over
-several launches, prepared batches and single queries (needs a GB300)."""
+several launches, prepared batches, single queries, and the windowed launches of tile
+pruning and the learned narrower (needs a GB300)."""
 import numpy as np
 import pytest
 
@@ -134,6 +135,54 @@ def test_single_query_staged(M):
             t.set_output_order(mode)
             out = torch.empty(want.size, dtype=torch.int32, device="cuda")
             assert np.array_equal(M.as_uint32_numpy(t.query(q, out=out)), want)
+
+
+@ORDERS
+@pytest.mark.parametrize("batch", ["zones", "learned_pla", "learned_none"])
+def test_windowed_orders(M, order_mode, batch):
+    """Windowed launches (tile pruning on the Z-sorted table; the learned narrower's
+    windows): look-back and staged answers equal the oracle's."""
+    import torch
+    wl = W.zorder_learned(n=2_000_003, nq=96)
+    want = [oracle.mdrq(wl.columns, q, nthreads=16) for q in wl.queries]
+    with M.Table(_device(wl.columns)) as t:
+        t.set_output_order(order_mode)
+        if batch == "zones":
+            t.set_zone_maps(M.ZONES_ALL)
+            t.set_batch_mode(M.BATCH_PLAIN)
+        else:
+            t.learn([0, 1, 2, 3], M.MODEL_PLA if batch == "learned_pla" else M.MODEL_NONE, cells=wl.key_bounds)
+            t.set_batch_mode(M.BATCH_LEARNED)
+        ids, off = t.query_batch(wl.queries)
+        torch.cuda.synchronize()
+        got = M.as_uint32_numpy(ids)
+        for q, w in enumerate(want):
+            assert np.array_equal(got[int(off[q]):int(off[q + 1])], w), (batch, q)
+
+
+@pytest.mark.parametrize("batch", ["zones", "learned"])
+def test_windowed_short_buffer_staged(M, batch):
+    """A staged windowed batch into a buffer of a third of its answer: the prefix is the
+    oracle's, nothing past capacity is written, the total is exact."""
+    import torch
+    wl = W.zorder_learned(n=1_000_003, nq=48)
+    cat = np.concatenate([oracle.mdrq(wl.columns, q, nthreads=16) for q in wl.queries])
+    cap = cat.size // 3
+    with M.Table(_device(wl.columns)) as t:
+        t.set_output_order(M.ORDER_STAGED)
+        if batch == "zones":
+            t.set_zone_maps(M.ZONES_ALL)
+            t.set_batch_mode(M.BATCH_PLAIN)
+        else:
+            t.learn([0, 1, 2, 3], M.MODEL_PLA, cells=wl.key_bounds)
+            t.set_batch_mode(M.BATCH_LEARNED)
+        enc = t.encode_batch(wl.queries)
+        buf = torch.full((cap + 256,), -1, dtype=torch.int32, device="cuda")
+        st, off = t.query_batch_raw(enc, buf.data_ptr(), cap, True)
+        assert st == M.E_CAPACITY and int(off[-1]) == cat.size
+        got = M.as_uint32_numpy(buf)
+        assert np.array_equal(got[:cap], cat[:cap])
+        assert np.all(buf[cap:].cpu().numpy() == -1)
 
 
 def test_bad_order_mode_rejected(M):

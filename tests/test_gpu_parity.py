@@ -261,9 +261,11 @@ def test_repeat_calls_reuse_scratch(M):
 def test_host_answers_pinned_and_pageable(M, mode, host):
     """Host answers: staged (a plain batch's launches copied out one by one while the
     next runs; the batch scans more than 2 GiB of columns, so it is split into several
-    launches) or written by the scan itself into page-locked memory (auto, direct). The
-    result and the capacity rule are those of the device path, for a page-locked and a
-    pageable buffer, with the capacity cut inside the batch."""
+    launches) or written by the kernels themselves into page-locked memory (direct).
+    Auto takes the staged copies here, since the plain batch's output is staged
+    (mdrq_set_output_order AUTO: 64 queries of 733 tiles). The result and the capacity
+    rule are those of the device path, for a page-locked and a pageable buffer, with the
+    capacity cut inside the batch."""
     import torch
     wl = W.mixed_clustered(n=3_000_017, nq=64)
     want = [oracle.mdrq(wl.columns, q, 8) for q in wl.queries]
@@ -279,7 +281,7 @@ def test_host_answers_pinned_and_pageable(M, mode, host):
         if mode == 1:
             launches, scanned = t.last_scan_stats()
             assert scanned >= 2 << 30
-            assert (launches >= 2) if host == 1 else (launches == 1), launches
+            assert (launches >= 2) if host in (0, 1) else (launches == 1), launches
         got = pinned.numpy().view(np.uint32)
         assert np.array_equal(got[:total], cat)
         assert np.all(pinned.numpy()[total:] == -1)

@@ -859,7 +859,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
 
         def e2e_run(host_mode):
             table.set_host_answers(host_mode)
-            step_host()
+            for _ in range(max(1, args.warmup)):
+                step_host()
             barrier()
             torch.cuda.synchronize()
             table.scan_timing(True)

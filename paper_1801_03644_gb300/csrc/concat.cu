@@ -304,22 +304,19 @@ __global__ void __launch_bounds__(kCatThreads) mdrq_concat_kernel(const __grid_c
             const uint32_t bc = __shfl_sync(0xffffffffu, cnt, l);
             const uint64_t bp = __shfl_sync(0xffffffffu, pos, l);
             const unsigned long long bd = __shfl_sync(0xffffffffu, dst, l);
-            // lane l: ids 4l .. 4l + 3 of every 128, four 16-byte loads in flight
-            for (uint32_t i = 4 * lane; i < bc; i += 512) {
-                uint4 v[4];
+            // lane l: ids l, l + 32, ... of every 512: each load and each store instruction
+            // covers 128 contiguous bytes (stores that cross the CPU-GPU link to a pinned
+            // host buffer stay whole), 16 loads in flight per lane
+            for (uint32_t i = lane; i < bc; i += 512) {
+                uint32_t v[16];
 #pragma unroll
-                for (uint32_t u = 0; u < 4; ++u)
-                    if (i + 128 * u < bc)
-                        v[u] = ld_stream_v4(stage + bp + i + 128 * u);
+                for (uint32_t u = 0; u < 16; ++u)
+                    if (i + 32 * u < bc)
+                        v[u] = ld_stream_u32(stage + bp + i + 32 * u);
 #pragma unroll
-                for (uint32_t u = 0; u < 4; ++u) {
-                    const uint32_t k = i + 128 * u;
-                    const uint32_t e[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-#pragma unroll
-                    for (uint32_t x = 0; x < 4; ++x)
-                        if (k + x < bc && bd + k + x < capacity)
-                            ids[bd + k + x] = e[x];
-                }
+                for (uint32_t u = 0; u < 16; ++u)
+                    if (i + 32 * u < bc && bd + i + 32 * u < capacity)
+                        ids[bd + i + 32 * u] = v[u];
             }
         }
     }

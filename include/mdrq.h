@@ -473,10 +473,15 @@ int mdrq_server_stop(mdrq_server *s);
  *                         queries and every query queued behind it end with
  *                         MDRQ_E_NOMEM, mdrq_server_submit refuses new queries with it,
  *                         and mdrq_server_stop returns it.
+ *  MDRQ_FAULT_STAGE_NOMEM the next scan launch that would stage its output (see
+ *                         mdrq_set_output_order) finds its staging buffers unavailable,
+ *                         as if their allocation had failed, and orders its output by
+ *                         look-back instead: the call succeeds with the same answer.
  * Errors: MDRQ_E_INVAL (t NULL, unknown kind, SKIP_TILES with arg = 0).
  */
 #define MDRQ_FAULT_SKIP_TILES 1
 #define MDRQ_FAULT_NOMEM 2
+#define MDRQ_FAULT_STAGE_NOMEM 3
 int mdrq_inject_fault(mdrq_table *t, int kind, uint64_t arg);
 
 /*

@@ -377,7 +377,8 @@ int launch_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t scanned_column
     if (t->inject_skip_tiles == 0 && t->output_order != MDRQ_ORDER_LOOKBACK &&
         (t->output_order == MDRQ_ORDER_STAGED || total_tiles >= kStagedMinTilesPerBlock * resident)) {
         // (each tile's run is padded to a multiple of 4 ids)
-        staged = grow_device(reinterpret_cast<void **>(&t->cat_ids), &t->cat_ids_cap,
+        staged = !__atomic_exchange_n(&t->inject_stage_nomem, 0, __ATOMIC_ACQ_REL) &&
+                 grow_device(reinterpret_cast<void **>(&t->cat_ids), &t->cat_ids_cap,
                              std::max<uint64_t>(16, (capacity + 3 * total_tiles) * 4)) == MDRQ_OK &&
                  grow_device(reinterpret_cast<void **>(&t->cat_rec), &t->cat_rec_cap, total_tiles * 8) == MDRQ_OK;
         if (!staged)
@@ -491,7 +492,8 @@ int launch_window_scan(mdrq_table *t, uint32_t q0, uint32_t nq, uint64_t max_win
     // against 49.4 ms, learned windows 53.8 against 48.4 ms).
     bool staged = false;
     if (t->inject_skip_tiles == 0 && t->output_order == MDRQ_ORDER_STAGED) {
-        staged = grow_device(reinterpret_cast<void **>(&t->cat_ids), &t->cat_ids_cap,
+        staged = !__atomic_exchange_n(&t->inject_stage_nomem, 0, __ATOMIC_ACQ_REL) &&
+                 grow_device(reinterpret_cast<void **>(&t->cat_ids), &t->cat_ids_cap,
                              std::max<uint64_t>(16, (capacity + 3 * max_tiles) * 4)) == MDRQ_OK &&
                  grow_device(reinterpret_cast<void **>(&t->cat_rec), &t->cat_rec_cap, max_tiles * 8) == MDRQ_OK;
         if (!staged)
@@ -1293,6 +1295,9 @@ int mdrq_inject_fault(mdrq_table *t, int kind, uint64_t arg)
         return MDRQ_OK;
     case MDRQ_FAULT_NOMEM:
         __atomic_store_n(&t->inject_nomem, 1, __ATOMIC_RELEASE);
+        return MDRQ_OK;
+    case MDRQ_FAULT_STAGE_NOMEM:
+        __atomic_store_n(&t->inject_stage_nomem, 1, __ATOMIC_RELEASE);
         return MDRQ_OK;
     default:
         return MDRQ_E_INVAL;

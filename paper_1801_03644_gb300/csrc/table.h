@@ -134,6 +134,7 @@ struct mdrq_table {
     // host-side fault injection for failure-detection tests (mdrq_inject_fault)
     uint64_t inject_skip_tiles = 0;  // next scan launch never claims its first tiles
     int inject_nomem = 0;            // next query call fails its scratch allocation
+    int inject_stage_nomem = 0;      // next staged launch finds its staging buffers missing
 };
 
 

@@ -66,7 +66,7 @@ EXPORTS = ["mdrq_load_columns", "mdrq_query", "mdrq_query_batch", "mdrq_free",
            "mdrq_set_output_order",
            "mdrq_set_key_cells"]
 
-FAULT_SKIP_TILES, FAULT_NOMEM = 1, 2
+FAULT_SKIP_TILES, FAULT_NOMEM, FAULT_STAGE_NOMEM = 1, 2, 3
 BATCH_AUTO, BATCH_PLAIN, BATCH_SHARED, BATCH_LEARNED = 0, 1, 2, 3
 MODEL_PLA, MODEL_MLP, MODEL_NONE = 1, 2, 3
 ZONES_OFF, ZONES_AUTO, ZONES_ALL = 0, 1, 2

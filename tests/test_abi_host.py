@@ -173,6 +173,7 @@ def test_every_handle_call_rejects_null(L):
     assert L.mdrq_scan_timing(None, 1) == E
     assert L.mdrq_scan_timing_read(None, ctypes.byref(ms), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), 0) == E
     assert L.mdrq_inject_fault(None, mdrq.FAULT_NOMEM, 0) == E
+    assert L.mdrq_inject_fault(None, mdrq.FAULT_STAGE_NOMEM, 0) == E
     k, empty = u32(0), i32(0)
     assert L.mdrq_explain_query(None, p, 1, p, 1, ctypes.byref(k), ctypes.byref(empty)) == E
     assert L.mdrq_learn_search_info(None, ctypes.byref(a), ctypes.byref(b)) == E

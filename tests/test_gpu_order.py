@@ -185,6 +185,33 @@ def test_windowed_short_buffer_staged(M, batch):
         assert np.all(buf[cap:].cpu().numpy() == -1)
 
 
+def test_staging_unavailable_falls_back_to_lookback(M):
+    """A staged launch whose staging buffers cannot be had (a host-side fault: the
+    allocation reported as failed) orders its output by look-back instead: one kernel
+    instead of the scan and the three ordering kernels, the same answers."""
+    import torch
+    wl = W.mixed_clustered(n=1_000_003, nq=40)
+    want = [oracle.mdrq(wl.columns, q, 16) for q in wl.queries]
+    with M.Table(_device(wl.columns)) as t:
+        t.set_batch_mode(M.BATCH_PLAIN)
+        t.set_output_order(M.ORDER_STAGED)
+        t.scan_timing(True)
+        for fault, kernels_per_scan in ((True, 1), (False, 4)):
+            t.scan_timing_read(reset=True)
+            if fault:
+                t.inject_fault(M.FAULT_STAGE_NOMEM)
+            out = torch.empty(sum(w.size for w in want), dtype=torch.int32, device="cuda")
+            ids, off = t.query_batch(wl.queries, out=out)  # one call: the buffer fits
+            torch.cuda.synchronize()
+            tm = t.scan_timing_read(reset=True)
+            assert tm["scan_launches"] >= 1
+            assert tm["kernel_launches"] == kernels_per_scan * tm["scan_launches"], (fault, tm)
+            got = M.as_uint32_numpy(ids)
+            for q, w in enumerate(want):
+                assert np.array_equal(got[int(off[q]):int(off[q + 1])], w), (fault, q)
+        t.scan_timing(False)
+
+
 def test_bad_order_mode_rejected(M):
     wl = W.uniform_small(n=1000, nq=1)
     with M.Table(wl.columns) as t:

@@ -120,7 +120,8 @@ struct SharedParams {
     unsigned long long *offsets;    // offsets[orig + 1] <- CSR end of that query
     uint32_t *ids;
     uint64_t capacity;
-    uint4 *masks;                   // [chunk][row]: the row's query bits (CACHED passes)
+    uint4 *masks;                   // [chunk][32-row step][lane]: the step's rows of queries
+                                    // 32g + lane, g = 0..3 (CACHED passes; rows padded to 32)
 };
 
 // e(x) = number of cut points <= x, by a fixed-step binary search (uniform across lanes)
@@ -322,8 +323,10 @@ __device__ __forceinline__ void flush_counts(uint32_t (&plane)[kSharedG][kCountP
 
 // Pass 1 (WRITE = false): per live query and unit, the number of matching rows.
 // Pass 2 (WRITE = true): the ids, at qbase[q] + counts[q][unit] (exclusive prefix).
-// CACHED: pass 1 also stores every row's 128 query bits of the chunk (16 bytes per row
-// and chunk) and pass 2 reads them instead of evaluating the columns again.
+// CACHED: pass 1 also stores the chunk's row bits (16 bytes per row and chunk), transposed
+// per 32-row step so that lane l holds the step's rows of queries l, 32 + l, 64 + l and
+// 96 + l; it counts them with popcounts, and pass 2 reads them instead of evaluating the
+// columns again and without transposing them.
 // CODED: the chunk columns are the batch's 16-bit codes (mdrq_shared_encode_kernel),
 // each chunk's elementary interval a table lookup.
 template <bool WRITE, bool CACHED, bool CODED>
@@ -331,6 +334,7 @@ template <bool WRITE, bool CACHED, bool CODED>
 __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(SharedParams p)
 {
     constexpr bool kLoadMasks = WRITE && CACHED;
+    const uint64_t n_pad = (p.n + 31) & ~31ull;  // rows of the stored row bits
     // columns whose next-step values are loaded ahead: fewer for 2-byte codes, whose
     // lookups are short, than for values, whose searches are long (measured)
     constexpr int kPre = CODED ? 4 : kPrefetchCols;
@@ -412,7 +416,8 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
             const bool valid = r < r_end;
             uint32_t mask[kSharedG];
             if (kLoadMasks) {
-                const uint4 m4 = valid ? __ldcs(p.masks + (uint64_t)c * p.n + r) : make_uint4(0u, 0u, 0u, 0u);
+                // stored transposed by pass 1: lane l gets the step's rows of query 32g + l
+                const uint4 m4 = __ldcs(p.masks + (uint64_t)c * n_pad + r0 + lane);
                 mask[0] = m4.x;
                 mask[1] = m4.y;
                 mask[2] = m4.z;
@@ -465,8 +470,14 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
                         }
                     }
                 }
-                if (CACHED && valid)
-                    __stcs(p.masks + (uint64_t)c * p.n + r, make_uint4(mask[0], mask[1], mask[2], mask[3]));
+                if (CACHED) {
+                    // stored transposed (lane l: the step's rows of query 32g + l), so that
+                    // pass 2 needs no transpose; pass 1 counts them with a popcount
+#pragma unroll
+                    for (int g = 0; g < kSharedG; ++g)
+                        mask[g] = __any_sync(0xffffffffu, mask[g]) ? warp_transpose32(mask[g], lane) : 0u;
+                    __stcs(p.masks + (uint64_t)c * n_pad + r0 + lane, make_uint4(mask[0], mask[1], mask[2], mask[3]));
+                }
             }
             if (kLoadMasks) {
                 // the step's (row, query) bit matrix, transposed (lane l: the rows of
@@ -474,7 +485,7 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
                 // the block's ids are written query by query by the whole warp
 #pragma unroll
                 for (int g = 0; g < kSharedG; ++g) {
-                    const uint32_t tr = __any_sync(0xffffffffu, mask[g]) ? warp_transpose32(mask[g], lane) : 0u;
+                    const uint32_t tr = mask[g];  // transposed already (pass 1)
                     tb[(g * 32 + lane) * kBlockStride + sb] = tr;
                     seen[g] |= tr;
                 }
@@ -559,6 +570,11 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
                             off[g] += __popc(b);
                     }
                 }
+            } else if (CACHED) {
+                // count the stored, transposed bits: lane l counts query 32g + l
+#pragma unroll
+                for (int g = 0; g < kSharedG; ++g)
+                    cnt[g] += (uint32_t)__popc(mask[g]);
             } else {
                 // count: add this lane's bits into per-lane bit-sliced counters (plane j
                 // holds bit j of 32 counters); flush them before they can overflow
@@ -579,7 +595,8 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
             }
         }
         if (!WRITE) {
-            flush_counts(plane, cnt, lane);
+            if (!CACHED)
+                flush_counts(plane, cnt, lane);
 #pragma unroll
             for (int g = 0; g < kSharedG; ++g) {
                 const uint32_t qi = g * 32 + lane;
@@ -1191,8 +1208,9 @@ int shared_scan_count(mdrq_table *t, SharedScanState &S, const std::vector<Encod
         S.smem_attr = true;
         S.grid_scan = t->sm_count * 2;
     }
-    // row masks kept between the passes when they fit: 16 bytes per row and chunk
-    const uint64_t mask_bytes = (uint64_t)chunks.size() * t->n * sizeof(uint4);
+    // row masks kept between the passes when they fit: 16 bytes per row (rows padded to
+    // a multiple of 32) and chunk
+    const uint64_t mask_bytes = (uint64_t)chunks.size() * ((t->n + 31) & ~31ull) * sizeof(uint4);
     const uint64_t budget_bytes = t->shared_bits_budget == ~0ull ? kMaskBudgetBytes : t->shared_bits_budget;
     bool cached = mask_bytes <= budget_bytes && S.masks_cap >= mask_bytes;
     if (!cached && mask_bytes <= budget_bytes) {

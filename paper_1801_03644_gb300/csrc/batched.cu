@@ -69,6 +69,7 @@ constexpr uint32_t kBlockSteps = 16;     // cached write pass: 32-row steps per 
 constexpr uint32_t kBlockStride = kBlockSteps + 1;  // words per query in the block buffer (padded)
 constexpr uint32_t kLanesPerWord = 32 / kBlockSteps;  // lanes sharing one step's word in a flush
 constexpr uint32_t kLaneBits = kBlockSteps == 32 ? 0xffffffffu : (1u << kBlockSteps) - 1u;
+constexpr uint32_t kLaneRun = 16;  // cached write pass: a query's block ids its own lane writes
 constexpr size_t kBlockBufferBytes = (size_t)kSharedWarps * kSharedG * 32 * kBlockStride * 4;
 constexpr uint32_t kCodedMaxCuts = 16383;        // coded columns: most cut points of one column
 constexpr int kBallotQueries = 2;                // write pass: up to this many matching queries
@@ -491,12 +492,37 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
                 }
                 if (++sb == kBlockSteps || r0 + 32 >= r_end) {
                     __syncwarp();
-                    // lane i takes rows [Bi, Bi + B) of the block (B = kBlockSteps): bits
-                    // B (i % (32 / B)) .. of step i / (32 / B)
 #pragma unroll
                     for (int g = 0; g < kSharedG; ++g) {
-                        uint32_t qs = __ballot_sync(0xffffffffu, seen[g] != 0u);
+                        // lane l's own query 32g + l: its ids in the block
+                        const uint32_t *wq = tb + (g * 32 + lane) * kBlockStride;
+                        uint32_t mine = 0;
+                        if (seen[g])
+                            for (uint32_t w = 0; w < sb; ++w)
+                                mine += __popc(wq[w]);
                         seen[g] = 0u;
+                        const unsigned long long qb = off[g];
+                        // a query with few ids in the block: its own lane writes them, the
+                        // warp's 32 queries at once
+                        if (mine != 0u && mine <= kLaneRun && qb != kSkipQuery) {
+                            unsigned long long pos = qb;
+                            for (uint32_t w = 0; w < sb; ++w) {
+                                uint32_t x = wq[w];
+                                while (x) {
+                                    const int e = __ffs(x) - 1;
+                                    x &= x - 1;
+                                    if (pos < p.capacity)
+                                        p.ids[pos] = (uint32_t)(block_row0 + 32 * w + e);
+                                    ++pos;
+                                }
+                            }
+                        }
+                        if (qb != kSkipQuery)
+                            off[g] = qb + mine;
+                        // more ids: the whole warp, one query at a time; lane i takes rows
+                        // [Bi, Bi + B) of the block (B = kBlockSteps): bits B (i % (32 / B))
+                        // .. of step i / (32 / B)
+                        uint32_t qs = __ballot_sync(0xffffffffu, mine > kLaneRun);
                         while (qs) {
                             const int q = __ffs(qs) - 1;
                             qs &= qs - 1;
@@ -511,8 +537,7 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
                                 if (lane >= o)
                                     incl += x;
                             }
-                            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-                            const unsigned long long base = __shfl_sync(0xffffffffu, off[g], q);
+                            const unsigned long long base = __shfl_sync(0xffffffffu, qb, q);
                             if (base != kSkipQuery) {
                                 unsigned long long pos = base + incl - c8;
                                 while (bits) {
@@ -522,8 +547,6 @@ __global__ void __launch_bounds__(kSharedThreads, 4) mdrq_shared_pass_kernel(Sha
                                         p.ids[pos] = (uint32_t)(block_row0 + kBlockSteps * lane + e);
                                     ++pos;
                                 }
-                                if (lane == q)
-                                    off[g] += total;
                             }
                         }
                     }
